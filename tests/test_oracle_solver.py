@@ -1,0 +1,248 @@
+"""Pins of the oracle's discretisation and GSIS driver (CPU only)."""
+import numpy as np
+import pytest
+
+from workloads import shock_1d_case, cylinder_case, cartesian_1d, cylinder_ogrid, sphere_ogrid
+from workloads.meshes import BC_FARFIELD, BC_WALL, BC_PERIODIC, BC_NONE
+from oracle import model as M
+from oracle import kinetic as K
+from oracle.mesh import Topology
+from oracle.macro import MacroGeometry, hllc, euler_flux_dot, residual, lsq_grad
+from oracle.gsis import OracleSolver, residual_eps, prim_to_U
+
+
+# ----------------------------------------------------------------------------- geometry
+@pytest.mark.parametrize("mesh", [
+    cartesian_1d(7, -1.0, 2.0, [1, 1, 0, 0, 1], [1, 1, 0, 0, 1]),
+    cylinder_ogrid(6, 8, 0.5, 5.0, 0.05, 2.0, [1, 1, 0, 0, 1]),
+    sphere_ogrid(4, 6, 8, 0.5, 5.0, 0.1, 2.0, [1, 1, 0, 0, 1]),
+])
+def test_cells_are_closed(mesh):
+    """Outward area vectors of every cell sum to zero (geometric conservation)."""
+    topo = Topology(mesh)
+    for c in range(topo.ncell):
+        s = sum(sd.S_out for sd in topo.sides[c])
+        scale = max(np.linalg.norm(sd.S_out) for sd in topo.sides[c])
+        assert np.linalg.norm(s) < 1e-13 * scale
+        assert topo.vol[c] > 0
+
+
+def test_cylinder_volume_is_polygon_area():
+    """Cells are straight-sided quadrilaterals of unit depth: the total volume
+    is the annulus between two regular n-gons, n/2 (r_o^2 - r_i^2) sin(2 pi/n)."""
+    n = 16
+    mesh = cylinder_ogrid(10, n, 0.5, 5.0, 0.02, 2.0, [1, 1, 0, 0, 1])
+    exact = 0.5 * n * (5.0 ** 2 - 0.5 ** 2) * np.sin(2 * np.pi / n)
+    assert abs(mesh.volumes.sum() / exact - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("mesh", [
+    cylinder_ogrid(6, 8, 0.5, 5.0, 0.05, 2.0, [1, 1, 0, 0, 1]),
+    sphere_ogrid(4, 6, 8, 0.5, 5.0, 0.1, 2.0, [1, 1, 0, 0, 1]),
+])
+def test_lsq_gradient_exact_for_linear_fields(mesh):
+    topo = Topology(mesh)
+    geo = MacroGeometry(topo)
+    a = np.array([0.3, -1.2, 0.7])[:mesh.dim]
+    lin = lambda x: 2.0 + x[..., :mesh.dim] @ a
+    phi = lin(topo.centers)
+    bv = np.zeros((topo.ncell, 6))
+    for c in range(topo.ncell):
+        for si, sd in enumerate(topo.sides[c]):
+            bv[c, si] = lin(sd.xf)
+    g = lsq_grad(geo, phi, bv)
+    assert np.max(np.abs(g[:, :mesh.dim] - a[None, :])) < 1e-11
+
+
+# ----------------------------------------------------------------------------- macro fluxes
+def test_hllc_consistency_and_upwinding():
+    rng = np.random.default_rng(1)
+    F = 20
+    r = rng.uniform(0.5, 2, F); u = rng.uniform(-1, 1, (F, 3)); p = rng.uniform(0.5, 2, F)
+    n = rng.normal(size=(F, 3)); n /= np.linalg.norm(n, axis=1)[:, None]
+    U = np.concatenate([r[:, None], r[:, None] * u, (1.5 * p + 0.5 * r * np.sum(u * u, 1))[:, None]], 1)
+    assert np.allclose(hllc(r, u, p, r, u, p, n), euler_flux_dot(U, n), rtol=1e-13, atol=1e-13)
+    # supersonic left-to-right: the flux is the left state's flux
+    u2 = 5.0 * n
+    U2 = np.concatenate([r[:, None], r[:, None] * u2, (1.5 * p + 0.5 * r * 25.0)[:, None]], 1)
+    assert np.allclose(hllc(r, u2, p, r * 2, u2 * 0.9, p * 3, n), euler_flux_dot(U2, n), rtol=1e-13)
+
+
+def test_macro_residual_vanishes_for_uniform_stream_on_ogrid():
+    W = [1.0, 2.0, 0.5, 0.0, 1.0]
+    mesh = cylinder_ogrid(5, 8, 0.5, 5.0, 0.1, 2.0, W)
+    mesh.bc_type[0] = BC_FARFIELD
+    mesh.bc_state[0] = W
+    topo = Topology(mesh)
+    geo = MacroGeometry(topo)
+    Wc = np.tile(W, (topo.ncell, 1))
+    R, _, _ = residual(geo, mesh.bc_state, prim_to_U(Wc), np.zeros((topo.ncell, 3, 3)),
+                       np.zeros((topo.ncell, 3)), 0.01, 0.81)
+    assert np.max(np.abs(R)) < 1e-13
+
+
+# ----------------------------------------------------------------------------- kinetic step
+def _tiny_1d(n=6, Kn=1.0, nv=(10, 4, 4), delta=1.0):
+    c = shock_1d_case(Ma=2.0, n_cells=n, half_width=n / 4.0, nv=nv, delta=delta)
+    c.Kn = Kn
+    return c
+
+
+def test_first_order_sweep_equals_dense_implicit_solve(monkeypatch):
+    """With slopes switched off the scheme is the first-order implicit upwind
+    system (1/tau + sum_out xi.S/V) f_c - sum_in |xi.S|/V f_nb = g/tau + inflow;
+    in 1D one symmetric Gauss-Seidel pass solves it exactly.  Compare with a
+    dense Gaussian elimination per velocity."""
+    case = _tiny_1d()
+    s = OracleSolver(case); s.initialise()
+    inp = s.kinetic_inputs()
+    monkeypatch.setattr(K, "slope", lambda *a: 0.0)
+    f = s.f.copy()
+    K.sweep(s.topo, s.vg, f, s.dvm, inp)
+    N, vg, topo = s.N, s.vg, s.topo
+    for v in range(vg.nv):
+        A = np.zeros((N, N)); b = np.zeros(N)
+        for c in range(N):
+            A[c, c] += 1.0 / inp.tau[c]
+            b[c] += inp.gt[c][v] / inp.tau[c]
+            for sd in topo.sides[c]:
+                if sd.nbr < 0 and sd.bc == BC_NONE:
+                    continue
+                xn = vg.xi[v] @ sd.S_out / topo.vol[c]
+                if xn > 0:
+                    A[c, c] += xn
+                elif sd.nbr >= 0:
+                    A[c, sd.nbr] += xn
+                else:
+                    b[c] -= xn * inp.ff[sd.bc_side][v]
+        ref = np.linalg.solve(A, b)
+        assert np.max(np.abs(f[:, v] - ref)) <= 1e-13 * max(1e-300, np.max(np.abs(ref)))
+
+
+def test_second_order_sweeps_converge_to_discrete_steady_state():
+    """Repeated kinetic steps (frozen g~, tau) converge to the solution of the
+    second-order steady scheme: for every cell and velocity
+    (1/V) sum_F xi.S_F f_F = (g~ - f)/tau with f_F the upwind MUSCL-minmod
+    face value (written out here independently of the oracle)."""
+    case = _tiny_1d(n=8, Kn=0.3)
+    s = OracleSolver(case); s.initialise()
+    inp = s.kinetic_inputs()
+    for _ in range(60):
+        K.sweep(s.topo, s.vg, s.f, s.dvm, inp)
+    f, vg, topo = s.f, s.vg, s.topo
+    N = s.N
+
+    def mm(a, b):
+        return np.where(a * b > 0, np.sign(a) * np.minimum(np.abs(a), np.abs(b)), 0.0)
+
+    slopes = np.zeros_like(f)
+    for c in range(1, N - 1):
+        slopes[c] = mm(f[c] - f[c - 1], f[c + 1] - f[c])
+    xi = vg.xi[:, 0]
+    ff_lo, ff_hi = inp.ff[0], inp.ff[1]
+    res = 0.0
+    for c in range(N):
+        dx = topo.vol[c]
+        # face c+1/2 and c-1/2 values
+        right = np.where(xi > 0, f[c] + 0.5 * slopes[c], (f[c + 1] - 0.5 * slopes[c + 1]) if c + 1 < N else ff_hi)
+        left = np.where(xi > 0, (f[c - 1] + 0.5 * slopes[c - 1]) if c > 0 else ff_lo, f[c] - 0.5 * slopes[c])
+        r = xi * (right - left) / dx - (inp.gt[c] - f[c]) / inp.tau[c]
+        res = max(res, np.max(np.abs(r)) / np.max(np.abs(inp.gt[c] / inp.tau[c])))
+    assert res < 1e-11
+
+
+def test_free_molecular_closed_form():
+    """tau -> infinity (Kn = 1e4): the steady 1D solution between two
+    far-field Maxwellians is M1 for xi_x > 0 and M2 for xi_x < 0 everywhere."""
+    case = _tiny_1d(n=6, Kn=1e4)
+    s = OracleSolver(case); s.initialise()
+    inp = s.kinetic_inputs()
+    for _ in range(8):
+        K.sweep(s.topo, s.vg, s.f, s.dvm, inp)
+    xi = s.vg.xi[:, 0]
+    expect = np.where(xi > 0, inp.ff[0], inp.ff[1])
+    assert np.max(np.abs(s.f - expect[None, :])) < 1e-3 * np.max(expect)   # O(1/Kn) collision term
+    # density of the half-range mix, summed independently half by half
+    w = s.vg.w
+    rho_closed = w * (np.sum(inp.ff[0][xi > 0]) + np.sum(inp.ff[1][xi < 0]))
+    assert abs(M.moments(s.f[3], s.vg)[0] / rho_closed - 1) < 1e-3
+
+
+def test_wall_density_gives_zero_mass_flux():
+    vg = M.VelocityGrid((12, 10, 6), (-6, -6, -6), (6, 6, 6))
+    f = M.maxwellian(1.3, [0.4, -0.2, 0], 1.5, vg.xi)
+    S = np.array([-0.3, -0.9, 0.0])
+    Mw = M.maxwellian(1.0, np.zeros(3), 2.0, vg.xi)
+    rw = K.wall_density(f, S, Mw, vg)
+    xn = vg.xi @ S
+    face = np.where(xn > 0, f, rw * Mw)
+    assert abs(np.sum(xn * face)) < 1e-14 * np.sum(np.abs(xn * face))
+
+
+# ----------------------------------------------------------------------------- whole iteration
+def test_uniform_stream_is_gsis_fixed_point_1d():
+    W1 = np.array([1.0, 1.5, 0.0, 0.0, 1.0])
+    case = shock_1d_case(n_cells=10, half_width=3.0, nv=(32, 20, 20), vmax=12.0, macro_steps=20)
+    case.mesh = cartesian_1d(10, -3, 3, W1, W1)
+    case.W0 = np.tile(W1, (10, 1))
+    s = OracleSolver(case).run(3)
+    assert np.max(np.abs(s.W - case.W0)) < 1e-12
+    assert max(s.eps_history) < 1e-12
+
+
+def test_uniform_stream_is_gsis_fixed_point_ogrid():
+    """A uniform stream through an O-grid annulus with far-field boundaries on
+    both radial sides (2D faces, periodic wrap, MUSCL, HLLC, viscous terms)."""
+    W = np.array([1.0, 1.2, -0.4, 0.0, 1.0])
+    case = cylinder_case(n_r=4, n_theta=6, nv=(24, 24, 6), Kn=0.5, adaptive=False, macro_steps=10,
+                         vbox=((-9, 9), (-9, 9), (-6, 6)))
+    case.mesh.bc_type[0] = BC_FARFIELD
+    case.mesh.bc_state[0] = W
+    case.mesh.bc_state[1] = W
+    case.W0 = np.tile(W, (case.mesh.ncell, 1))
+    s = OracleSolver(case).run(2)
+    assert np.max(np.abs(s.W - case.W0)) < 1e-11
+
+
+def test_residual_eps_definition():
+    """Convergence criterion of Sec. 4 on a hand-computed two-cell example."""
+    Wp = np.array([[1.0, 1.0, 0.0, 0.0, 2.0], [2.0, 0.0, 1.0, 0.0, 1.0]])
+    Wn = Wp.copy(); Wn[0, 0] = 1.1; Wn[1, 4] = 1.3
+    vol = np.array([1.0, 3.0])
+    e_rho = np.sqrt(0.01 * 1.0 / (1.0 * 1 + 4.0 * 3))
+    e_T = np.sqrt(0.09 * 3.0 / (4.0 * 1 + 1.0 * 3))
+    assert abs(residual_eps(Wn, Wp, vol) - max(e_rho, e_T)) < 1e-15
+
+
+def test_kn_gll_linear_density():
+    """Eq. Kn_Gll for rho = 1 + 0.01 x, uniform u and T: interior cells give
+    lambda |d rho/dx| / rho with lambda = mu(T)/p sqrt(pi T/2)."""
+    W1 = [1.0, 1.0, 0, 0, 1.0]
+    case = shock_1d_case(n_cells=12, half_width=3.0, nv=(8, 4, 4))
+    x = case.mesh.flat(case.mesh.centers)[:, 0]
+    case.mesh.bc_state[0] = [1 + 0.01 * -3.0, 1.0, 0, 0, 1.0]
+    case.mesh.bc_state[1] = [1 + 0.01 * 3.0, 1.0, 0, 0, 1.0]
+    case.W0 = np.stack([1 + 0.01 * x, np.ones_like(x), 0 * x, 0 * x, np.ones_like(x)], 1)
+    s = OracleSolver(case)
+    kn = s.kn_gll_field(case.W0)
+    mu0 = M.mu0_from_kn(case.Kn)
+    lam = mu0 / (1 + 0.01 * x) * np.sqrt(np.pi / 2)
+    assert np.allclose(kn, lam * 0.01 / (1 + 0.01 * x), rtol=1e-12)
+
+
+def test_no_dvm_cells_is_pure_navier_stokes():
+    """Kn_ref above every Kn_Gll: no DVM cell, HoT = 0, so each GSIS iteration
+    is exactly one block of NS pseudo-steps (continuum limit of the coupling)."""
+    from oracle.macro import macro_solve
+    from oracle.gsis import U_to_prim
+    case = shock_1d_case(n_cells=16, half_width=4.0, nv=(8, 4, 4), macro_steps=15)
+    case.adaptive = True; case.Kn_ref = 1e30; case.presolve_max_blocks = 0
+    s = OracleSolver(case).run(2)
+    assert not s.dvm.any()
+    s2 = OracleSolver(case)
+    z = np.zeros((s2.N, 3, 3)); zq = np.zeros((s2.N, 3))
+    U = prim_to_U(case.W0)
+    for _ in range(2):
+        U = macro_solve(s2.geo, s2.bc_state, U, z, zq, s2.mu0, s2.omega, case.cfl, case.k_sub, case.macro_steps,
+                        case.dt, U.copy())
+    assert np.max(np.abs(U_to_prim(U) - s.W)) < 1e-14
