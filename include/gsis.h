@@ -1,0 +1,203 @@
+/*
+ * gsis.h -- C ABI of the GB300 (sm_103a) adaptive GSIS kinetic hot path.
+ *
+ * The library implements one iteration of the adaptive general synthetic
+ * iterative scheme of Zhang, Zeng & Wu (arXiv 2501.02245) for a monatomic gas
+ * (the d_r = 0 reduction of the model of Sec. 2, i.e. the Shakhov model with
+ * Pr = 2/3) on a structured finite-volume mesh and a uniform discrete velocity
+ * grid, restricted to a compacted list of kinetic (DVM) cells:
+ *
+ *   reference distribution  (Sec. 2, Eq. general_model and the g_0t formula)
+ *   implicit upwind kinetic step           (Sec. 3.1, first equation)
+ *   velocity moments + high-order terms    (Eq. getmoment, Eq. full_constitutive)
+ *   macroscopic synthetic solve            (Eq. macro with Eq. NSF_constitutive)
+ *   VDF correction                         (Eq. updatef)
+ *   convergence criterion                  (Sec. 4, Eq. convergence_critertion)
+ *   adaptation + Grad-13 reconstruction    (Sec. 3.2, Eq. Kn_Gll, Eq. G13_VDF;
+ *                                           Sec. 3.4 Steps 1-3)
+ *
+ * Conventions
+ *  - Every function returns gsis_status; no C++ exception crosses the ABI.
+ *  - Non-dimensional units: R = 1, free-stream rho = T = 1; p = rho T.
+ *  - Host pointers passed in are read during the call and copied; the caller
+ *    keeps ownership.  The library owns all device memory it allocates,
+ *    through the gsis_allocator callbacks when given, else cudaMalloc.
+ *  - All device work of a context runs on the cuda stream given to gsis_init
+ *    (NULL = the legacy default stream).  Calls on one context are not
+ *    thread-safe; distinct contexts are independent.
+ *  - On GSIS_ERR_ARG the context state is unchanged.  After GSIS_ERR_CUDA,
+ *    GSIS_ERR_NONFINITE or GSIS_ERR_INTERNAL the context only accepts
+ *    gsis_free, gsis_last_error and gsis_moments.
+ */
+#ifndef GSIS_H
+#define GSIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSIS_OK = 0,
+    GSIS_ERR_ARG = 1,          /* invalid argument or descriptor             */
+    GSIS_ERR_STATE = 2,        /* call not allowed in the current state      */
+    GSIS_ERR_OOM = 3,          /* allocation failed (callback returned NULL) */
+    GSIS_ERR_CUDA = 4,         /* a CUDA runtime call failed                 */
+    GSIS_ERR_NONFINITE = 5,    /* non-finite or non-positive rho/T detected  */
+    GSIS_ERR_TIMEOUT = 6,      /* a bounded device wait ran out              */
+    GSIS_ERR_UNSUPPORTED = 7,  /* valid but not implemented combination      */
+    GSIS_ERR_INTERNAL = 8      /* device-side consistency check failed       */
+} gsis_status;
+
+/* VDF storage types (arithmetic: FP64 for GSIS_F64, FP32 otherwise; moments,
+ * conservation correction and the synthetic solve are FP64 always). */
+enum { GSIS_F64 = 0, GSIS_F32 = 1, GSIS_BF16 = 2, GSIS_F16 = 3 };
+
+/* Boundary side types. */
+enum { GSIS_BC_NONE = 0, GSIS_BC_FARFIELD = 1, GSIS_BC_WALL = 2, GSIS_BC_PERIODIC = 3 };
+
+/* Fields returned by gsis_moments, one bit each; values are written per cell
+ * in this order for the bits that are set. */
+enum {
+    GSIS_FIELD_RHO = 1 << 0, GSIS_FIELD_UX = 1 << 1, GSIS_FIELD_UY = 1 << 2, GSIS_FIELD_UZ = 1 << 3,
+    GSIS_FIELD_T = 1 << 4,
+    GSIS_FIELD_HOT_SXX = 1 << 5, GSIS_FIELD_HOT_SYY = 1 << 6, GSIS_FIELD_HOT_SZZ = 1 << 7,
+    GSIS_FIELD_HOT_SXY = 1 << 8, GSIS_FIELD_HOT_SXZ = 1 << 9, GSIS_FIELD_HOT_SYZ = 1 << 10,
+    GSIS_FIELD_HOT_QX = 1 << 11, GSIS_FIELD_HOT_QY = 1 << 12, GSIS_FIELD_HOT_QZ = 1 << 13,
+    GSIS_FIELD_KN_GLL = 1 << 14, GSIS_FIELD_DVM = 1 << 15,
+    GSIS_NFIELDS = 16
+};
+
+/* Device-memory callbacks (for example a framework's caching allocator).
+ * alloc must return memory aligned to at least 256 bytes, or NULL on failure
+ * (reported as GSIS_ERR_OOM).  free(NULL) is never called. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void  (*free)(void* p, void* stream, void* user);
+    void* user;
+} gsis_allocator;
+
+/* Run parameters. */
+typedef struct {
+    double Kn;            /* free-stream Knudsen number; mu(T0) from the Kn definition of Sec. 2 */
+    double omega;         /* viscosity index: mu = mu(T0) (T/T0)^omega (Sec. 2)                  */
+    int    adaptive;      /* 1: Sec. 3.4 Steps 1-3 (NS presolve, Kn_Gll region); 0: all cells DVM */
+    double Kn_ref;        /* reference Knudsen number of the DVM-region rule (Sec. 3.2)           */
+    int    adapt_every;   /* the region is re-identified once, after this many GSIS iterations    */
+    int    wall_layers;   /* cell layers next to a wall that are always DVM                        */
+    int    vdf_dtype;     /* GSIS_F64 / GSIS_F32 / GSIS_BF16 / GSIS_F16                            */
+    int    macro_steps;   /* pseudo-time steps of the synthetic solve per GSIS iteration           */
+    double cfl;           /* pseudo-time CFL number of the synthetic solve                         */
+    int    k_sub;         /* Jacobi sweeps of the data-parallel relaxation per pseudo-step         */
+    double dt;            /* time step of Eq. macro; 0 = steady form (dt -> infinity)              */
+    double tol;           /* convergence tolerance on epsilon (Sec. 4), also for the NS presolve   */
+    int    presolve_max_blocks; /* NS presolve: at most this many blocks of macro_steps steps      */
+    unsigned long long spin_limit; /* iteration limit of any bounded device wait (0 = default)    */
+} gsis_params;
+
+/* Structured mesh: cells (i, j, k), flat index c = i + ni*(j + nj*k).
+ * centers [ncell][3], volumes [ncell]; for direction d the faces normal to it:
+ * S[d] and xf[d] of shape [nk'][nj'][ni'][3] with one extra face along d
+ * (area vector pointing along +d, magnitude = area; face centre).  In a
+ * periodic direction the face between the last and the first cell is face 0.
+ * bc_type/bc_state per side (i-lo, i-hi, j-lo, j-hi, k-lo, k-hi); bc_state is
+ * (rho, ux, uy, uz, T) for a far field, T at index 4 is the wall temperature
+ * for a wall.  W0 [ncell][5] is the initial (rho, ux, uy, uz, T).
+ * Errors: GSIS_ERR_ARG for non-positive sizes or volumes, a periodic
+ * direction with fewer than 3 cells, inconsistent periodic sides, non-finite
+ * input or non-positive rho/T; GSIS_ERR_STATE after the first gsis_iterate. */
+typedef struct {
+    int ni, nj, nk;
+    int dim;                    /* spatial directions carrying gradients (1, 2 or 3) */
+    const double* centers;
+    const double* volumes;
+    const double* S[3];
+    const double* xf[3];
+    int    bc_type[6];
+    double bc_state[6][5];
+    const double* W0;
+} gsis_mesh_desc;
+
+/* Uniform midpoint velocity grid (Sec. 4.2: uniform discretisation of a
+ * truncated box): n[d] nodes on [lo[d], hi[d]], node k at lo+(k+1/2)(hi-lo)/n,
+ * weight prod_d (hi-lo)/n; flat index v = ix + nx*(iy + ny*iz). */
+typedef struct {
+    int    n[3];
+    double lo[3];
+    double hi[3];
+} gsis_vgrid_desc;
+
+/* Per-call report of gsis_iterate. Phase times are CUDA-event times on the
+ * context stream, summed over the iterations of the call (milliseconds). */
+enum { GSIS_PH_ADAPT = 0, GSIS_PH_CELLEQ = 1, GSIS_PH_SWEEP = 2, GSIS_PH_MOMENTS = 3,
+       GSIS_PH_MACRO = 4, GSIS_PH_CORRECT = 5, GSIS_PH_RESID = 6, GSIS_PH_PRESOLVE = 7, GSIS_NPHASE = 8 };
+typedef struct {
+    int     iterations;          /* GSIS iterations run by this call                    */
+    int     total_iterations;    /* since gsis_init                                     */
+    double  eps;                 /* epsilon of the last iteration (Sec. 4)              */
+    int     converged;           /* eps < tol                                           */
+    long long n_dvm;             /* kinetic cells                                       */
+    long long n_v;               /* discrete velocities                                 */
+    long long vdf_bytes;         /* bytes of the compacted VDF array                    */
+    int     presolve_blocks;     /* NS presolve blocks run (adaptive only)              */
+    double  phase_ms[GSIS_NPHASE];
+    long long sweep_launches;    /* sweep kernel launches in this call                  */
+    long long kernel_launches;   /* all kernel launches in this call                    */
+} gsis_report;
+
+typedef struct gsis_ctx gsis_ctx;
+
+/* Create a context.  params is copied.  alloc may be NULL (cudaMalloc/cudaFree).
+ * cuda_stream is a cudaStream_t (NULL = default stream).
+ * Errors: GSIS_ERR_ARG (NULL out/params, Kn <= 0, macro_steps < 0, k_sub < 0,
+ * cfl <= 0, dt < 0, unknown vdf_dtype), GSIS_ERR_CUDA (no device). */
+gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, void* cuda_stream,
+                      gsis_ctx** out);
+
+/* Upload the mesh (copied to the device). Must precede gsis_iterate. */
+gsis_status gsis_set_mesh(gsis_ctx* ctx, const gsis_mesh_desc* mesh);
+
+/* Set the velocity grid. Must precede gsis_iterate; GSIS_ERR_STATE afterwards.
+ * Errors: GSIS_ERR_ARG for n[d] < 1 or hi[d] <= lo[d]. */
+gsis_status gsis_set_velocity_grid(gsis_ctx* ctx, const gsis_vgrid_desc* vgrid);
+
+/* Run up to max_iter GSIS iterations (Sec. 3.1 steps; Sec. 3.4 drives the
+ * adaptive start on the first call).  max_iter = 0 performs only the start
+ * (presolve, region, initial VDF).  Stops early when eps < tol.  Synchronises
+ * the stream once per iteration to read eps (8 bytes device->host).
+ * report may be NULL.  Errors: GSIS_ERR_STATE (mesh or grid missing),
+ * GSIS_ERR_NONFINITE, GSIS_ERR_CUDA, GSIS_ERR_OOM. */
+gsis_status gsis_iterate(gsis_ctx* ctx, int max_iter, gsis_report* report);
+
+/* Write the selected per-cell fields (GSIS_FIELD_* bits, in bit order) of the
+ * current state: [ncell][popcount(mask)] doubles to dst (host memory when
+ * dst_is_device = 0, device memory on the context's device otherwise).  HoT
+ * fields are those of the last kinetic step (zero in NS cells). */
+gsis_status gsis_moments(gsis_ctx* ctx, unsigned field_mask, double* dst, int dst_is_device);
+
+/* Copy the compacted VDF of the DVM cells to host memory as FP64:
+ * dst [n_dvm][n_v] in the order of the cell list returned through cells
+ * (flat cell indices, n_dvm entries, may be NULL). */
+gsis_status gsis_get_vdf(gsis_ctx* ctx, double* dst, int* cells, long long capacity);
+
+/* Test hook: force the DVM region to the given per-cell flags (uint8, ncell)
+ * instead of the Kn_Gll rule, for the start and for the re-identification.
+ * Used to compare with a reference whose threshold decisions are taken
+ * elsewhere.  Must be called before the first gsis_iterate. */
+gsis_status gsis_debug_set_region(gsis_ctx* ctx, const uint8_t* flags);
+
+/* Human-readable description of the last error on this context (never NULL). */
+const char* gsis_last_error(const gsis_ctx* ctx);
+
+/* Release every resource of the context. NULL-safe; the pointer is invalid afterwards. */
+void gsis_free(gsis_ctx* ctx);
+
+/* Library version string. */
+const char* gsis_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSIS_H */

@@ -1,0 +1,365 @@
+// Distribution records: reference distributions of the kinetic model, their
+// conservation correction, Grad-13 interface distributions and boundary
+// Maxwellians, all in the separable form
+//     D(xi) = A e_x(ix) e_y(iy) e_z(iz) * P(c),   c = xi - u,
+//     e_d = exp(-c_d^2 / (2T)),  P = p0 + p.c + c.P2.c + (r.c) c^2,
+// so that one exp per 1D node (not per 3D node) is evaluated.
+//
+//  * Shakhov reference g_0t of Sec. 2 (Eq. general_model with d_r = 0):
+//      p0 = 1, p = -5T s q, r = s q, s = 1/(15 p T^2)
+//  * Grad-13 distribution of Eq. G13_VDF:
+//      p0 = 1, p = -q/(rho T^2), P2 = sigma/(2 rho T^2), r = q/(5 rho T^3)
+//  * conservation correction (the Lagrange-multiplier form of Gamba and
+//    Tharkabhushanam, J. Comput. Phys. 228 (2009), Maxwellian weighted):
+//      D <- D + M (a0 + a.xi + a4 |xi|^2) with the 5x5 system
+//      sum_v w psi phi^T M a = U - sum_v w psi D,  psi = (1, xi, |xi|^2/2),
+//      phi = (1, xi, |xi|^2),
+//    whose sums are assembled exactly from 1D sums C_d[k] = sum_i e_d c_d^k.
+#include "gsis_device.cuh"
+
+namespace gsis {
+
+struct Term { double c; int a, b, d; };
+
+__device__ static int psi_terms(int row, const double* u, Term* t, double scale) {
+    // psi_row in powers of c (c = xi - u); scale = 1 for psi, 2 for phi_4 only
+    switch (row) {
+        case 0: t[0] = {1.0, 0, 0, 0}; return 1;
+        case 1: t[0] = {1.0, 1, 0, 0}; t[1] = {u[0], 0, 0, 0}; return 2;
+        case 2: t[0] = {1.0, 0, 1, 0}; t[1] = {u[1], 0, 0, 0}; return 2;
+        case 3: t[0] = {1.0, 0, 0, 1}; t[1] = {u[2], 0, 0, 0}; return 2;
+        default: {
+            double h = 0.5 * scale;
+            t[0] = {h, 2, 0, 0}; t[1] = {h, 0, 2, 0}; t[2] = {h, 0, 0, 2};
+            t[3] = {scale * u[0], 1, 0, 0}; t[4] = {scale * u[1], 0, 1, 0}; t[5] = {scale * u[2], 0, 0, 1};
+            t[6] = {h * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]), 0, 0, 0};
+            return 7;
+        }
+    }
+}
+
+__device__ static int base_terms(const RecSpec& s, Term* t) {
+    int n = 0;
+    t[n++] = {s.p0, 0, 0, 0};
+    t[n++] = {s.p[0], 1, 0, 0}; t[n++] = {s.p[1], 0, 1, 0}; t[n++] = {s.p[2], 0, 0, 1};
+    t[n++] = {s.P2[0], 2, 0, 0}; t[n++] = {s.P2[1], 0, 2, 0}; t[n++] = {s.P2[2], 0, 0, 2};
+    t[n++] = {2.0 * s.P2[3], 1, 1, 0}; t[n++] = {2.0 * s.P2[4], 1, 0, 1}; t[n++] = {2.0 * s.P2[5], 0, 1, 1};
+    t[n++] = {s.r[0], 3, 0, 0}; t[n++] = {s.r[0], 1, 2, 0}; t[n++] = {s.r[0], 1, 0, 2};
+    t[n++] = {s.r[1], 2, 1, 0}; t[n++] = {s.r[1], 0, 3, 0}; t[n++] = {s.r[1], 0, 1, 2};
+    t[n++] = {s.r[2], 2, 0, 1}; t[n++] = {s.r[2], 0, 2, 1}; t[n++] = {s.r[2], 0, 0, 3};
+    return n;
+}
+
+__device__ static double poly_moment(const Term* t1, int n1, const Term* t2, int n2, const double (*Cs)[6]) {
+    double s = 0.0;
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n2; ++j)
+            s += t1[i].c * t2[j].c * (Cs[0][t1[i].a + t2[j].a] * Cs[1][t1[i].b + t2[j].b] * Cs[2][t1[i].d + t2[j].d]);
+    return s;
+}
+
+// Solve A x = b (5x5) by Gaussian elimination with partial pivoting.
+__device__ static void solve5(double A[5][5], double b[5], double x[5]) {
+    for (int col = 0; col < 5; ++col) {
+        int piv = col;
+        double best = fabs(A[col][col]);
+        for (int r = col + 1; r < 5; ++r)
+            if (fabs(A[r][col]) > best) { best = fabs(A[r][col]); piv = r; }
+        if (piv != col) {
+            for (int k = 0; k < 5; ++k) { double t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
+            double t = b[col]; b[col] = b[piv]; b[piv] = t;
+        }
+        for (int r = col + 1; r < 5; ++r) {
+            double m = A[r][col] / A[col][col];
+            for (int k = col; k < 5; ++k) A[r][k] -= m * A[col][k];
+            b[r] -= m * b[col];
+        }
+    }
+    for (int r = 4; r >= 0; --r) {
+        double s = b[r];
+        for (int k = r + 1; k < 5; ++k) s -= A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+}
+
+// One warp per record.
+__global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Records out, VGridDev vg) {
+    const int lane = threadIdx.x & 31;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nrec) return;
+    const RecSpec s = specs[r];
+    const int NT = vg.NT, nx = vg.nx, ny = vg.ny;
+    double* tab = out.tab + (long long)r * NTAB * NT;
+    double* scal = out.scal + (long long)r * RS;
+    const double T = s.T;
+    const double A = s.rho * pow(2.0 * PI * T, -1.5);
+    double part[3][6];
+    for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < 6; ++k) part[d][k] = 0.0;
+    for (int idx = lane; idx < NT; idx += 32) {
+        const int d = idx < nx ? 0 : (idx < nx + ny ? 1 : 2);
+        const double c = vg.xi[idx] - s.u[d];
+        const double e = exp(-(c * c) / (2.0 * T));
+        tab[idx] = e;
+        tab[2 * NT + idx] = c;
+        tab[3 * NT + idx] = c * c;
+        double pw = e;
+        for (int k = 0; k < 6; ++k) {
+            for (int dd = 0; dd < 3; ++dd)
+                if (dd == d) part[dd][k] += pw;
+            pw *= c;
+        }
+    }
+    double Cs[3][6];
+    for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < 6; ++k) Cs[d][k] = warp_sum(part[d][k]);
+
+    double coef[12];   // p0', p'(3), P2'(diag 3), alpha(5)
+    if (lane == 0) {
+        double pp[3] = {s.p[0], s.p[1], s.p[2]};
+        double p2d[3] = {s.P2[0], s.P2[1], s.P2[2]};
+        double p0 = s.p0;
+        double alpha[5] = {0, 0, 0, 0, 0};
+        if (s.correct) {
+            Term tp[7], tq[7], tb[19];
+            const int nb = base_terms(s, tb);
+            const double wa = vg.w * A;
+            double Am[5][5], rhs[5];
+            for (int a = 0; a < 5; ++a) {
+                const int na = psi_terms(a, s.u, tp, 1.0);
+                rhs[a] = s.U[a] - wa * poly_moment(tp, na, tb, nb, Cs);
+                for (int b = 0; b < 5; ++b) {
+                    const int nbb = psi_terms(b, s.u, tq, b == 4 ? 2.0 : 1.0);
+                    Am[a][b] = wa * poly_moment(tp, na, tq, nbb, Cs);
+                }
+            }
+            solve5(Am, rhs, alpha);
+            const double ua = alpha[1] * s.u[0] + alpha[2] * s.u[1] + alpha[3] * s.u[2];
+            const double u2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+            p0 = s.p0 + alpha[0] + ua + alpha[4] * u2;
+            for (int d = 0; d < 3; ++d) {
+                pp[d] = s.p[d] + alpha[1 + d] + 2.0 * alpha[4] * s.u[d];
+                p2d[d] = s.P2[d] + alpha[4];
+            }
+        }
+        coef[0] = p0;
+        for (int d = 0; d < 3; ++d) { coef[1 + d] = pp[d]; coef[4 + d] = p2d[d]; }
+        for (int k = 0; k < 5; ++k) coef[7 + k] = alpha[k];
+        scal[RS_P0] = p0;
+        scal[RS_P2XY] = s.P2[3];
+        scal[RS_P2XZ] = s.P2[4];
+        scal[RS_P2YZ] = s.P2[5];
+        scal[RS_OFFD] = (s.P2[3] != 0.0 || s.P2[4] != 0.0 || s.P2[5] != 0.0) ? 1.0 : 0.0;
+        scal[RS_UX] = s.u[0];
+        scal[RS_UY] = s.u[1];
+        scal[RS_UZ] = s.u[2];
+        for (int k = 0; k < 5; ++k) scal[RS_ALPHA0 + k] = alpha[k];
+    }
+    for (int k = 0; k < 7; ++k) coef[k] = __shfl_sync(0xffffffffu, coef[k], 0);
+    for (int idx = lane; idx < NT; idx += 32) {
+        const int d = idx < nx ? 0 : (idx < nx + ny ? 1 : 2);
+        const double c = tab[2 * NT + idx];
+        tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * (c * c);
+        tab[4 * NT + idx] = s.r[d] * c;
+        if (d == 0) tab[idx] *= A;
+    }
+}
+
+void launch_build_records(gsis_ctx* c, const Records& out, int nrec, const RecSpec* d_specs) {
+    if (nrec <= 0) return;
+    const int threads = 128;
+    const int blocks = (nrec * 32 + threads - 1) / threads;
+    k_build_records<<<blocks, threads, 0, c->stream>>>(d_specs, nrec, out, c->vg);
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------- spec builders
+__device__ static void cons_of(double rho, const double* u, double T, double* U) {
+    U[0] = rho;
+    U[1] = rho * u[0]; U[2] = rho * u[1]; U[3] = rho * u[2];
+    U[4] = rho * (1.5 * T + 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+}
+
+__device__ static void spec_maxwellian(RecSpec& s, double rho, const double* u, double T, int correct) {
+    s.rho = rho; s.T = T;
+    for (int d = 0; d < 3; ++d) { s.u[d] = u[d]; s.p[d] = 0.0; s.r[d] = 0.0; }
+    for (int k = 0; k < 6; ++k) s.P2[k] = 0.0;
+    s.p0 = 1.0;
+    cons_of(rho, u, T, s.U);
+    s.correct = correct;
+}
+
+// Shakhov reference state of each DVM cell from W^n and the heat flux of f^n
+// about u^n (third moment stored by the moments pass), tau = mu(T)/p, and the
+// diffuse-wall densities from the lagged outgoing half-range fluxes.
+__global__ void k_cell_eq(int Nd, const int* __restrict__ dvm_cell, const double* __restrict__ W,
+                          const double* __restrict__ mom, const int* __restrict__ side_bc,
+                          const double* __restrict__ wall_den, double mu0, double omega,
+                          RecSpec* specs, double* tau, double* rho_w) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nd) return;
+    const int c = dvm_cell[k];
+    const double rho = W[c * 5], T = W[c * 5 + 4];
+    const double u[3] = {W[c * 5 + 1], W[c * 5 + 2], W[c * 5 + 3]};
+    const double* m = mom + (long long)k * MOMN;
+    const double q[3] = {0.5 * m[10], 0.5 * m[11], 0.5 * m[12]};
+    const double p = rho * T;
+    const double sc = 1.0 / (15.0 * p * T * T);
+    RecSpec s;
+    spec_maxwellian(s, rho, u, T, 1);
+    for (int d = 0; d < 3; ++d) { s.p[d] = -5.0 * T * sc * q[d]; s.r[d] = sc * q[d]; }
+    specs[k] = s;
+    tau[k] = viscosity(T, mu0, omega) / p;
+    for (int sd = 0; sd < 6; ++sd) {
+        double v = 0.0;
+        if (side_bc[c * 6 + sd] == GSIS_BC_WALL) v = m[13 + sd] / wall_den[c * 6 + sd];
+        rho_w[(long long)k * 6 + sd] = v;
+    }
+}
+
+void launch_cell_eq(gsis_ctx* c) {
+    const int Nd = (int)c->Nd;
+    if (Nd == 0) return;
+    k_cell_eq<<<(Nd + 127) / 128, 128, 0, c->stream>>>(Nd, c->dvm_cell, c->W, c->mom, c->m.side_bc, c->wall_den,
+                                                        c->mu0, c->p.omega, c->specs, c->tau, c->rho_w);
+    c->launches++;
+    launch_build_records(c, c->recG, Nd, c->specs);
+}
+
+// Boundary records: far field -> conservation-corrected Maxwellian of the
+// boundary state; wall -> unit-density Maxwellian at rest at T_w (emission
+// shape, scaled by rho_w in the sweep).
+__global__ void k_bc_specs(RecSpec* specs, const int* bc_type, const double* bc_state) {
+    const int s = threadIdx.x;
+    if (s >= 6) return;
+    const double* st = bc_state + s * 5;
+    RecSpec r;
+    if (bc_type[s] == GSIS_BC_FARFIELD) {
+        spec_maxwellian(r, st[0], st + 1, st[4], 1);
+    } else if (bc_type[s] == GSIS_BC_WALL) {
+        const double z[3] = {0.0, 0.0, 0.0};
+        spec_maxwellian(r, 1.0, z, st[4], 0);
+    } else {
+        const double z[3] = {0.0, 0.0, 0.0};
+        spec_maxwellian(r, 1.0, z, 1.0, 0);
+    }
+    specs[s] = r;
+}
+
+void launch_bc_records(gsis_ctx* c) {
+    k_bc_specs<<<1, 32, 0, c->stream>>>(c->specs, c->d_bc_type, c->d_bc_state);
+    c->launches++;
+    launch_build_records(c, c->recBC, 6, c->specs);
+}
+
+// Denominator of the diffuse-wall density: sum over incoming velocities
+// (xi . S_out <= 0) of w |xi . S_out| M_w, one block per (cell, wall side).
+__global__ void k_wall_den(int N, const int* __restrict__ side_bc, const double* __restrict__ Sout,
+                           Records bc, VGridDev vg, double* wall_den) {
+    const int c = blockIdx.x;
+    __shared__ double sm[32];
+    for (int s = 0; s < 6; ++s) {
+        if (side_bc[c * 6 + s] != GSIS_BC_WALL) continue;
+        const double* S = Sout + ((long long)c * 6 + s) * 3;
+        const double* sc = rec_scal(bc, s);
+        const double* tb = rec_tab(bc, s, vg.NT);
+        double acc[1] = {0.0};
+        for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
+            int ix, iy, iz;
+            vsplit(v, vg.nx, vg.ny, ix, iy, iz);
+            const double xn = vg.xi[ix] * S[0] + vg.xi[vg.nx + iy] * S[1] + vg.xi[vg.nx + vg.ny + iz] * S[2];
+            if (!(xn > 0.0)) acc[0] += -xn * eval_rec(sc, tb, vg.NT, vg.nx, vg.ny, ix, iy, iz);
+        }
+        block_sum<1>(acc, sm);
+        if (threadIdx.x == 0) wall_den[c * 6 + s] = acc[0] * vg.w;
+    }
+}
+
+void launch_wall_den(gsis_ctx* c) {
+    k_wall_den<<<c->m.N, 256, 0, c->stream>>>(c->m.N, c->m.side_bc, c->m.Sout, c->recBC, c->vg, c->wall_den);
+    c->launches++;
+}
+
+// Grad-13 interface distributions (Eq. G13_VDF) of NS cells next to DVM
+// cells, from W^n and the NSF stress / heat flux at W^n, conservation-corrected.
+__device__ static void spec_grad13(RecSpec& s, const double* Wc, const double* nsf9) {
+    const double rho = Wc[0], T = Wc[4];
+    const double u[3] = {Wc[1], Wc[2], Wc[3]};
+    spec_maxwellian(s, rho, u, T, 1);
+    const double rT2 = rho * T * T;
+    for (int d = 0; d < 3; ++d) {
+        const double q = nsf9[6 + d];
+        s.p[d] = -q / rT2;
+        s.r[d] = q / (5.0 * rT2 * T);
+    }
+    for (int k = 0; k < 6; ++k) s.P2[k] = nsf9[k] / (2.0 * rT2);
+}
+
+__global__ void k_ghost_specs(int ng, const int* __restrict__ ghost_cell, const double* __restrict__ W,
+                              const double* __restrict__ nsf, RecSpec* specs) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int c = ghost_cell[g];
+    RecSpec s;
+    spec_grad13(s, W + c * 5, nsf + (long long)c * HOTN);
+    specs[g] = s;
+}
+
+void launch_ghost_records(gsis_ctx* c) {
+    if (c->n_ghost == 0) return;
+    k_ghost_specs<<<(c->n_ghost + 127) / 128, 128, 0, c->stream>>>(c->n_ghost, c->ghost_cell, c->W, c->nsf, c->specs);
+    c->launches++;
+    launch_build_records(c, c->recGhost, c->n_ghost, c->specs);
+}
+
+// M~(W^{n+1}) and M~(W^{n+1/2}) for Eq. updatef.
+__global__ void k_corr_specs(int Nd, const int* __restrict__ dvm_cell, const double* __restrict__ Wa,
+                             RecSpec* specs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nd) return;
+    const double* w = Wa + dvm_cell[k] * 5;
+    const double u[3] = {w[1], w[2], w[3]};
+    RecSpec s;
+    spec_maxwellian(s, w[0], u, w[4], 1);
+    specs[k] = s;
+}
+
+void launch_correction_records(gsis_ctx* c) {
+    const int Nd = (int)c->Nd;
+    if (Nd == 0) return;
+    k_corr_specs<<<(Nd + 127) / 128, 128, 0, c->stream>>>(Nd, c->dvm_cell, c->W, c->specs);
+    c->launches++;
+    launch_build_records(c, c->recNew, Nd, c->specs);
+    k_corr_specs<<<(Nd + 127) / 128, 128, 0, c->stream>>>(Nd, c->dvm_cell, c->Wh, c->specs);
+    c->launches++;
+    launch_build_records(c, c->recHalf, Nd, c->specs);
+}
+
+// Seed distributions for cells entering the DVM region: Grad-13 from W and
+// its NSF stress / heat flux (adaptive start, Sec. 3.2) or the corrected
+// Maxwellian M~(W) (all-kinetic start), into recNew slots of the new list.
+__global__ void k_seed_specs(int ne, const int* __restrict__ enter, const int* __restrict__ dvm_cell,
+                             const double* __restrict__ W, const double* __restrict__ nsf, int grad13,
+                             RecSpec* specs) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int c = dvm_cell[enter[e]];
+    RecSpec s;
+    if (grad13) {
+        spec_grad13(s, W + c * 5, nsf + (long long)c * HOTN);
+    } else {
+        const double u[3] = {W[c * 5 + 1], W[c * 5 + 2], W[c * 5 + 3]};
+        spec_maxwellian(s, W[c * 5], u, W[c * 5 + 4], 1);
+    }
+    specs[e] = s;
+}
+
+void launch_seed_records(gsis_ctx* c, int ne, int grad13) {
+    if (ne == 0) return;
+    k_seed_specs<<<(ne + 127) / 128, 128, 0, c->stream>>>(ne, c->enter_list, c->dvm_cell, c->W, c->nsf, grad13,
+                                                           c->specs);
+    c->launches++;
+    launch_build_records(c, c->recNew, ne, c->specs);
+}
+
+}  // namespace gsis

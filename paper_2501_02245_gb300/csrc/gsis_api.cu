@@ -1,0 +1,658 @@
+// C ABI of the GSIS library: context, argument checking, mesh set-up, and the
+// orchestration of one GSIS iteration (Sec. 3.1 steps; Sec. 3.4 for the
+// adaptive start).  Every numerical step runs in the kernels of the other
+// translation units; this file only moves descriptors and launches them.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include "gsis_device.cuh"
+
+using namespace gsis;
+
+namespace gsis {
+
+gsis_status set_err(gsis_ctx* c, gsis_status s, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (s == GSIS_ERR_CUDA || s == GSIS_ERR_NONFINITE || s == GSIS_ERR_INTERNAL) c->broken = true;
+    }
+    return s;
+}
+
+bool cuda_ok(gsis_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    set_err(c, GSIS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return false;
+}
+
+void* dev_alloc(gsis_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (c->have_alloc) {
+        p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+    } else {
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (p) c->allocations.push_back(p);
+    return p;
+}
+
+void dev_free(gsis_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+    if (it == c->allocations.end()) return;
+    c->allocations.erase(it);
+    if (c->have_alloc) c->alloc.free(p, (void*)c->stream, c->alloc.user);
+    else cudaFree(p);
+}
+
+size_t vdf_elem_bytes(int dtype) {
+    switch (dtype) {
+        case GSIS_F64: return 8;
+        case GSIS_F32: return 4;
+        default: return 2;
+    }
+}
+
+}  // namespace gsis
+
+namespace {
+
+template <typename T>
+T* upload(gsis_ctx* c, const std::vector<T>& h) {
+    T* d = (T*)dev_alloc(c, h.size() * sizeof(T));
+    if (!d) return nullptr;
+    if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return nullptr;
+    return d;
+}
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Solve the dim x dim normal equations G x = b (Gaussian elimination, partial pivoting).
+bool solve_small(int n, double G[3][3], double b[3], double x[3]) {
+    double A[3][4];
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) A[i][j] = G[i][j];
+        A[i][n] = b[i];
+    }
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int k = 0; k <= n; ++k) std::swap(A[col][k], A[piv][k]);
+        for (int r = col + 1; r < n; ++r) {
+            const double m = A[r][col] / A[col][col];
+            for (int k = col; k <= n; ++k) A[r][k] -= m * A[col][k];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = A[r][n];
+        for (int k = r + 1; k < n; ++k) s -= A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+    return true;
+}
+
+void phase_begin(gsis_ctx* c, int ph) {
+    if (c->events) cudaEventRecord(c->ev[2 * ph], c->stream);
+}
+void phase_end(gsis_ctx* c, int ph) {
+    if (c->events) cudaEventRecord(c->ev[2 * ph + 1], c->stream);
+}
+void phase_collect(gsis_ctx* c, const bool* used) {
+    if (!c->events) return;
+    for (int ph = 0; ph < GSIS_NPHASE; ++ph) {
+        if (!used[ph]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[2 * ph], c->ev[2 * ph + 1]) == cudaSuccess) c->phase_ms[ph] += ms;
+    }
+}
+
+gsis_status check_ctx(gsis_ctx* c) {
+    if (!c) return GSIS_ERR_ARG;
+    if (c->broken) return set_err(c, GSIS_ERR_STATE, "context is unusable after an earlier error: " + c->err);
+    return GSIS_OK;
+}
+
+// ---------------------------------------------------------------------------- start-up (Sec. 3.4 Steps 1-2)
+gsis_status presolve(gsis_ctx* c) {
+    const int N = c->m.N;
+    cudaMemsetAsync(c->hot, 0, (size_t)N * HOTN * sizeof(double), c->stream);
+    launch_prim_to_cons(c, c->W, c->U);
+    cudaMemcpyAsync(c->Wm, c->W, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    c->presolve_blocks = 0;
+    for (int b = 0; b < c->p.presolve_max_blocks; ++b) {
+        cudaMemcpyAsync(c->Wp, c->Wm, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+        macro_block(c, c->p.macro_steps, false, false);
+        launch_eps(c, c->Wm, c->Wp);
+        cudaMemcpyAsync(c->h_eps, c->eps_buf, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "presolve")) return GSIS_ERR_CUDA;
+        c->presolve_blocks = b + 1;
+        if (c->h_eps[1] != 0.0) return set_err(c, GSIS_ERR_NONFINITE, "non-finite state in the NS presolve");
+        if (c->h_eps[0] < c->p.tol) break;
+    }
+    cudaMemcpyAsync(c->W, c->Wm, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    return GSIS_OK;
+}
+
+gsis_status start(gsis_ctx* c) {
+    const int N = c->m.N;
+    if (!cuda_ok(c, cudaMemcpyAsync(c->W, c->host_W0.data(), (size_t)N * 5 * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream), "upload W0"))
+        return GSIS_ERR_CUDA;
+    cudaMemsetAsync(c->hot, 0, (size_t)N * HOTN * sizeof(double), c->stream);
+    launch_bc_records(c);
+    launch_wall_den(c);
+    phase_begin(c, GSIS_PH_PRESOLVE);
+    if (c->p.adaptive && c->p.presolve_max_blocks > 0) {
+        gsis_status s = presolve(c);
+        if (s != GSIS_OK) return s;
+    }
+    phase_end(c, GSIS_PH_PRESOLVE);
+    if (c->have_forced) {
+        cudaMemcpyAsync(c->flag, c->forced_flags.data(), N, cudaMemcpyHostToDevice, c->stream);
+    } else if (c->p.adaptive) {
+        launch_kn_gll(c, c->W);
+    } else {
+        cudaMemsetAsync(c->flag, 1, N, c->stream);
+    }
+    {
+        std::vector<int> m1(N, -1);
+        cudaMemcpyAsync(c->cell2dvm, m1.data(), N * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    if (build_region(c) < 0) return c->broken ? GSIS_ERR_CUDA : GSIS_ERR_OOM;
+    launch_moments(c, c->W, 0, c->mom);
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "start")) return GSIS_ERR_CUDA;
+    c->started = true;
+    return GSIS_OK;
+}
+
+// ---------------------------------------------------------------------------- one GSIS iteration
+gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
+    const int N = c->m.N;
+    if (c->p.adaptive && c->iteration == c->p.adapt_every && !c->have_forced) {
+        used[GSIS_PH_ADAPT] = true;
+        phase_begin(c, GSIS_PH_ADAPT);
+        launch_kn_gll(c, c->W);
+        if (build_region(c) < 0) return c->broken ? GSIS_ERR_CUDA : GSIS_ERR_OOM;
+        launch_moments(c, c->W, 0, c->mom);
+        phase_end(c, GSIS_PH_ADAPT);
+    }
+    // 1. reference distributions, tau, interface ghosts, wall densities
+    used[GSIS_PH_CELLEQ] = true;
+    phase_begin(c, GSIS_PH_CELLEQ);
+    if (c->n_ghost > 0) {
+        launch_nsf(c, c->W, c->nsf);
+        launch_ghost_records(c);
+    }
+    launch_cell_eq(c);
+    phase_end(c, GSIS_PH_CELLEQ);
+    // 2. kinetic step: forward and backward Gauss-Seidel passes
+    used[GSIS_PH_SWEEP] = true;
+    phase_begin(c, GSIS_PH_SWEEP);
+    launch_sweep(c, 0);
+    launch_sweep(c, 1);
+    phase_end(c, GSIS_PH_SWEEP);
+    // 3. moments of f^{n+1/2}, W^{n+1/2}, HoT
+    used[GSIS_PH_MOMENTS] = true;
+    phase_begin(c, GSIS_PH_MOMENTS);
+    launch_moments(c, c->W, 0, c->momh);
+    launch_half_state(c);
+    launch_nsf(c, c->Wh, c->nsf);
+    launch_hot(c);
+    phase_end(c, GSIS_PH_MOMENTS);
+    // 4. synthetic solve over all cells from W^{n+1/2}
+    used[GSIS_PH_MACRO] = true;
+    phase_begin(c, GSIS_PH_MACRO);
+    launch_prim_to_cons(c, c->Wh, c->U);
+    launch_prim_to_cons(c, c->W, c->Un);
+    cudaMemcpyAsync(c->Wm, c->Wh, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0);
+    phase_end(c, GSIS_PH_MACRO);
+    // 6. residual between W^{n+1} (Wm) and W^n (W)
+    used[GSIS_PH_RESID] = true;
+    phase_begin(c, GSIS_PH_RESID);
+    launch_eps(c, c->Wm, c->W);
+    cudaMemcpyAsync(c->h_eps, c->eps_buf, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    phase_end(c, GSIS_PH_RESID);
+    std::swap(c->W, c->Wm);   // W = W^{n+1}
+    // 5. Eq. updatef in DVM cells, and moments of f^{n+1} about u^{n+1}
+    used[GSIS_PH_CORRECT] = true;
+    phase_begin(c, GSIS_PH_CORRECT);
+    launch_correction_records(c);
+    launch_moments(c, c->W, 1, c->mom);
+    phase_end(c, GSIS_PH_CORRECT);
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "GSIS iteration")) return GSIS_ERR_CUDA;
+    if (!cuda_ok(c, cudaGetLastError(), "kernel launch")) return GSIS_ERR_CUDA;
+    if (c->h_eps[1] != 0.0)
+        return set_err(c, GSIS_ERR_NONFINITE, "non-finite or non-positive density/temperature after iteration " +
+                                                  std::to_string(c->iteration));
+    *eps_out = c->h_eps[0];
+    c->iteration++;
+    return GSIS_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* gsis_version(void) { return "gsis-gb300 0.1 (sm_103a)"; }
+
+gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, void* cuda_stream, gsis_ctx** out) {
+    if (!out || !params) return GSIS_ERR_ARG;
+    *out = nullptr;
+    const gsis_params& p = *params;
+    if (!(p.Kn > 0.0) || !std::isfinite(p.Kn) || !(p.omega >= 0.0) || p.macro_steps < 0 || p.k_sub < 0 ||
+        !(p.cfl > 0.0) || !(p.dt >= 0.0) || p.vdf_dtype < GSIS_F64 || p.vdf_dtype > GSIS_F16 ||
+        p.presolve_max_blocks < 0 || p.wall_layers < 0 || p.adapt_every < 0 || !(p.tol >= 0.0))
+        return GSIS_ERR_ARG;
+    if (alloc && (!alloc->alloc || !alloc->free)) return GSIS_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GSIS_ERR_CUDA;
+    }
+    gsis_ctx* c = new (std::nothrow) gsis_ctx();
+    if (!c) return GSIS_ERR_OOM;
+    c->p = p;
+    if (c->p.spin_limit == 0) c->p.spin_limit = 1ull << 26;
+    if (alloc) { c->alloc = *alloc; c->have_alloc = true; }
+    c->stream = (cudaStream_t)cuda_stream;
+    c->device = dev;
+    c->mu0 = p.Kn * 1.0 * 1.0 / std::sqrt(PI / 2.0);   // Kn = mu(T0)/(p0 L) sqrt(pi R T0 / 2), p0 = L = T0 = 1
+    for (int i = 0; i < GSIS_NPHASE; ++i) c->phase_ms[i] = 0.0;
+    bool ev_ok = true;
+    for (int i = 0; i < 2 * GSIS_NPHASE; ++i) ev_ok = ev_ok && cudaEventCreate(&c->ev[i]) == cudaSuccess;
+    c->events = ev_ok;
+    if (cudaMallocHost(&c->h_eps, 4 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_count, 4 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        gsis_free(c);
+        return GSIS_ERR_CUDA;
+    }
+    *out = c;
+    return GSIS_OK;
+}
+
+gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!md) return set_err(c, GSIS_ERR_ARG, "NULL mesh descriptor");
+    if (c->started) return set_err(c, GSIS_ERR_STATE, "mesh cannot change after the first iterate");
+    const int ni = md->ni, nj = md->nj, nk = md->nk;
+    if (ni < 1 || nj < 1 || nk < 1 || md->dim < 1 || md->dim > 3)
+        return set_err(c, GSIS_ERR_ARG, "mesh sizes must be >= 1 and dim in 1..3");
+    if ((long long)ni * nj * nk > (1ll << 30)) return set_err(c, GSIS_ERR_ARG, "too many cells");
+    if (!md->centers || !md->volumes || !md->W0 || !md->S[0] || !md->S[1] || !md->S[2] || !md->xf[0] ||
+        !md->xf[1] || !md->xf[2])
+        return set_err(c, GSIS_ERR_ARG, "NULL mesh array");
+    const int n3[3] = {ni, nj, nk};
+    bool per[3];
+    for (int d = 0; d < 3; ++d) {
+        const int lo = md->bc_type[2 * d], hi = md->bc_type[2 * d + 1];
+        for (int s : {lo, hi})
+            if (s < GSIS_BC_NONE || s > GSIS_BC_PERIODIC) return set_err(c, GSIS_ERR_ARG, "unknown boundary type");
+        if ((lo == GSIS_BC_PERIODIC) != (hi == GSIS_BC_PERIODIC))
+            return set_err(c, GSIS_ERR_ARG, "periodic sides must come in pairs");
+        per[d] = lo == GSIS_BC_PERIODIC;
+        if (per[d] && n3[d] < 3) return set_err(c, GSIS_ERR_ARG, "a periodic direction needs at least 3 cells");
+    }
+    for (int s = 0; s < 6; ++s) {
+        if (md->bc_type[s] == GSIS_BC_FARFIELD &&
+            (!(md->bc_state[s][0] > 0.0) || !(md->bc_state[s][4] > 0.0) || !finite_all(md->bc_state[s], 5)))
+            return set_err(c, GSIS_ERR_ARG, "far-field state must be finite with rho, T > 0");
+        if (md->bc_type[s] == GSIS_BC_WALL && !(md->bc_state[s][4] > 0.0))
+            return set_err(c, GSIS_ERR_ARG, "wall temperature must be > 0");
+    }
+    const int N = ni * nj * nk;
+    if (!finite_all(md->centers, (size_t)N * 3) || !finite_all(md->W0, (size_t)N * 5))
+        return set_err(c, GSIS_ERR_ARG, "non-finite mesh centres or initial state");
+    for (int q = 0; q < N; ++q) {
+        if (!(md->volumes[q] > 0.0)) return set_err(c, GSIS_ERR_ARG, "cell volumes must be > 0");
+        if (!(md->W0[q * 5] > 0.0) || !(md->W0[q * 5 + 4] > 0.0))
+            return set_err(c, GSIS_ERR_ARG, "initial rho and T must be > 0");
+    }
+    const size_t nf[3] = {(size_t)(ni + 1) * nj * nk, (size_t)ni * (nj + 1) * nk, (size_t)ni * nj * (nk + 1)};
+    for (int d = 0; d < 3; ++d)
+        if (!finite_all(md->S[d], nf[d] * 3) || !finite_all(md->xf[d], nf[d] * 3))
+            return set_err(c, GSIS_ERR_ARG, "non-finite face geometry");
+
+    // connectivity, outward area vectors, face centres
+    std::vector<int> nbr((size_t)N * 6), side_bc((size_t)N * 6), hyper(N);
+    std::vector<double> Sout((size_t)N * 18), xf((size_t)N * 18), lsq((size_t)N * 18, 0.0);
+    auto face_index = [&](int d, int i, int j, int k, int fi) -> size_t {
+        if (d == 0) return ((size_t)k * nj + j) * (ni + 1) + fi;
+        if (d == 1) return ((size_t)k * (nj + 1) + fi) * ni + i;
+        return ((size_t)fi * nj + j) * ni + i;
+    };
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nj; ++j)
+            for (int i = 0; i < ni; ++i) {
+                const int cc = i + ni * (j + nj * k);
+                hyper[cc] = i + j + k;
+                const int idx[3] = {i, j, k};
+                for (int d = 0; d < 3; ++d)
+                    for (int hs = 0; hs < 2; ++hs) {
+                        const int s = 2 * d + hs;
+                        const int m = idx[d];
+                        int fi = hs ? m + 1 : m;
+                        if (per[d] && fi == n3[d]) fi = 0;
+                        const size_t f = face_index(d, i, j, k, fi);
+                        const double sg = hs ? 1.0 : -1.0;
+                        for (int q = 0; q < 3; ++q) {
+                            Sout[((size_t)cc * 6 + s) * 3 + q] = sg * md->S[d][f * 3 + q];
+                            xf[((size_t)cc * 6 + s) * 3 + q] = md->xf[d][f * 3 + q];
+                        }
+                        int mm = m + (hs ? 1 : -1);
+                        int nb = -1;
+                        if (mm >= 0 && mm < n3[d]) nb = 0;
+                        else if (per[d]) { mm = (mm + n3[d]) % n3[d]; nb = 0; }
+                        if (nb == 0) {
+                            int id2[3] = {i, j, k};
+                            id2[d] = mm;
+                            nb = id2[0] + ni * (id2[1] + nj * id2[2]);
+                        }
+                        nbr[(size_t)cc * 6 + s] = nb;
+                        side_bc[(size_t)cc * 6 + s] = nb >= 0 ? -1 : md->bc_type[s];
+                    }
+            }
+    // least-squares weights over the first dim coordinates
+    const int dim = md->dim;
+    for (int cc = 0; cc < N; ++cc) {
+        double rows[6][3];
+        int used[6], nr = 0;
+        for (int s = 0; s < 6; ++s) {
+            const int nb = nbr[(size_t)cc * 6 + s];
+            const int bc = side_bc[(size_t)cc * 6 + s];
+            if (nb >= 0) {
+                for (int q = 0; q < 3; ++q) rows[nr][q] = md->centers[(size_t)nb * 3 + q] - md->centers[(size_t)cc * 3 + q];
+            } else if (bc == GSIS_BC_FARFIELD || bc == GSIS_BC_WALL) {
+                for (int q = 0; q < 3; ++q) rows[nr][q] = xf[((size_t)cc * 6 + s) * 3 + q] - md->centers[(size_t)cc * 3 + q];
+            } else {
+                continue;
+            }
+            used[nr++] = s;
+        }
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int r = 0; r < nr; ++r)
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) G[a][b] += rows[r][a] * rows[r][b];
+        for (int r = 0; r < nr; ++r) {
+            double rhs[3] = {0, 0, 0}, x[3] = {0, 0, 0};
+            for (int a = 0; a < dim; ++a) rhs[a] = rows[r][a];
+            double Gc[3][3];
+            std::memcpy(Gc, G, sizeof(G));
+            if (!solve_small(dim, Gc, rhs, x))
+                return set_err(c, GSIS_ERR_ARG, "degenerate least-squares stencil at cell " + std::to_string(cc));
+            for (int a = 0; a < dim; ++a) lsq[((size_t)cc * 6 + used[r]) * 3 + a] = x[a];
+        }
+    }
+
+    Mesh& m = c->m;
+    m.ni = ni; m.nj = nj; m.nk = nk; m.dim = dim; m.N = N; m.H = ni + nj + nk - 2;
+    std::memcpy(m.bc_type, md->bc_type, sizeof(m.bc_type));
+    std::memcpy(m.bc_state, md->bc_state, sizeof(m.bc_state));
+    std::vector<double> cen(md->centers, md->centers + (size_t)N * 3), vol(md->volumes, md->volumes + N);
+    m.cen = upload(c, cen);
+    m.vol = upload(c, vol);
+    m.Sout = upload(c, Sout);
+    m.xf = upload(c, xf);
+    m.lsq_w = upload(c, lsq);
+    m.nbr = upload(c, nbr);
+    m.side_bc = upload(c, side_bc);
+    m.hyper = upload(c, hyper);
+    std::vector<int> bct(md->bc_type, md->bc_type + 6);
+    std::vector<double> bcs(&md->bc_state[0][0], &md->bc_state[0][0] + 30);
+    c->d_bc_type = upload(c, bct);
+    c->d_bc_state = upload(c, bcs);
+    c->host_W0.assign(md->W0, md->W0 + (size_t)N * 5);
+    const size_t N5 = (size_t)N * 5 * sizeof(double);
+    c->W = (double*)dev_alloc(c, N5); c->Wh = (double*)dev_alloc(c, N5); c->Wp = (double*)dev_alloc(c, N5);
+    c->Wm = (double*)dev_alloc(c, N5); c->U = (double*)dev_alloc(c, N5); c->Un = (double*)dev_alloc(c, N5);
+    c->dU = (double*)dev_alloc(c, N5); c->dU2 = (double*)dev_alloc(c, N5); c->R = (double*)dev_alloc(c, N5);
+    c->D = (double*)dev_alloc(c, N * sizeof(double));
+    c->lamS = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
+    c->gu = (double*)dev_alloc(c, (size_t)N * 9 * sizeof(double));
+    c->gT = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
+    c->grho = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
+    c->gU = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
+    c->hot = (double*)dev_alloc(c, (size_t)N * HOTN * sizeof(double));
+    c->kin = (double*)dev_alloc(c, (size_t)N * HOTN * sizeof(double));
+    c->nsf = (double*)dev_alloc(c, (size_t)N * HOTN * sizeof(double));
+    c->kn_gll = (double*)dev_alloc(c, N * sizeof(double));
+    c->wall_den = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
+    c->eps_buf = (double*)dev_alloc(c, 4 * sizeof(double));
+    c->flag = (uint8_t*)dev_alloc(c, N);
+    c->cell2dvm = (int*)dev_alloc(c, N * sizeof(int));
+    c->old_cell2dvm = (int*)dev_alloc(c, N * sizeof(int));
+    c->ghost_id = (int*)dev_alloc(c, N * sizeof(int));
+    c->ghost_cell = (int*)dev_alloc(c, N * sizeof(int));
+    c->enter_list = (int*)dev_alloc(c, N * sizeof(int));
+    c->hp_off = (int*)dev_alloc(c, (m.H + 1) * sizeof(int));
+    c->hp_cnt = (int*)dev_alloc(c, (m.H + 1) * sizeof(int));
+    c->d_count = (int*)dev_alloc(c, 4 * sizeof(int));
+    c->specs = (RecSpec*)dev_alloc(c, (size_t)std::max(N, 6) * sizeof(RecSpec));
+    c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
+    c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
+    if (!m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wh ||
+        !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->gu || !c->gT ||
+        !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->eps_buf || !c->flag ||
+        !c->cell2dvm || !c->old_cell2dvm || !c->ghost_id || !c->ghost_cell || !c->enter_list || !c->hp_off ||
+        !c->hp_cnt || !c->d_count || !c->specs || !c->recGhost.scal || !c->recBC.scal || !c->d_bc_type ||
+        !c->d_bc_state)
+        return set_err(c, GSIS_ERR_OOM, "device allocation failed in gsis_set_mesh");
+    cudaMemsetAsync(c->wall_den, 0, (size_t)N * 6 * sizeof(double), c->stream);
+    cudaMemsetAsync(c->kn_gll, 0, (size_t)N * sizeof(double), c->stream);
+    c->mesh_set = true;
+    if (c->vgrid_set) {
+        c->recGhost.tab = (double*)dev_alloc(c, (size_t)N * NTAB * c->vg.NT * sizeof(double));
+        if (!c->recGhost.tab) return set_err(c, GSIS_ERR_OOM, "device allocation failed (ghost tables)");
+    }
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "gsis_set_mesh")) return GSIS_ERR_CUDA;
+    return GSIS_OK;
+}
+
+gsis_status gsis_set_velocity_grid(gsis_ctx* c, const gsis_vgrid_desc* vd) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!vd) return set_err(c, GSIS_ERR_ARG, "NULL velocity-grid descriptor");
+    if (c->started) return set_err(c, GSIS_ERR_STATE, "velocity grid cannot change after the first iterate");
+    for (int d = 0; d < 3; ++d)
+        if (vd->n[d] < 1 || !(vd->hi[d] > vd->lo[d]) || !std::isfinite(vd->lo[d]) || !std::isfinite(vd->hi[d]))
+            return set_err(c, GSIS_ERR_ARG, "velocity grid needs n >= 1 and hi > lo on every axis");
+    const long long Nv = (long long)vd->n[0] * vd->n[1] * vd->n[2];
+    if (Nv > (1ll << 31)) return set_err(c, GSIS_ERR_ARG, "too many velocities");
+    std::vector<double> xi;
+    double w = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        const double h = (vd->hi[d] - vd->lo[d]) / vd->n[d];
+        for (int q = 0; q < vd->n[d]; ++q) xi.push_back(vd->lo[d] + (q + 0.5) * h);
+        w *= h;
+        c->nv3[d] = vd->n[d];
+        c->vlo[d] = vd->lo[d];
+        c->vhi[d] = vd->hi[d];
+    }
+    if (c->d_xi) dev_free(c, c->d_xi);
+    if (c->recBC.tab) dev_free(c, c->recBC.tab);
+    if (c->recGhost.tab) dev_free(c, c->recGhost.tab);
+    c->recGhost.tab = nullptr;
+    c->d_xi = upload(c, xi);
+    c->vg.nx = vd->n[0]; c->vg.ny = vd->n[1]; c->vg.nz = vd->n[2];
+    c->vg.NT = vd->n[0] + vd->n[1] + vd->n[2];
+    c->vg.Nv = Nv;
+    c->vg.w = w;
+    c->vg.xi = c->d_xi;
+    c->recBC.tab = (double*)dev_alloc(c, 6 * NTAB * c->vg.NT * sizeof(double));
+    if (c->mesh_set) c->recGhost.tab = (double*)dev_alloc(c, (size_t)c->m.N * NTAB * c->vg.NT * sizeof(double));
+    if (!c->d_xi || !c->recBC.tab || (c->mesh_set && !c->recGhost.tab))
+        return set_err(c, GSIS_ERR_OOM, "device allocation failed in gsis_set_velocity_grid");
+    c->cap_Nd = 0;   // record tables depend on NT: reallocate the DVM arrays at the next region build
+    c->vgrid_set = true;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "gsis_set_velocity_grid")) return GSIS_ERR_CUDA;
+    return GSIS_OK;
+}
+
+gsis_status gsis_debug_set_region(gsis_ctx* c, const uint8_t* flags) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!c->mesh_set) return set_err(c, GSIS_ERR_STATE, "set the mesh before forcing a region");
+    if (c->started) return set_err(c, GSIS_ERR_STATE, "the region can only be forced before the first iterate");
+    if (!flags) return set_err(c, GSIS_ERR_ARG, "NULL flags");
+    c->forced_flags.assign(flags, flags + c->m.N);
+    for (auto& v : c->forced_flags) v = v ? 1 : 0;
+    c->have_forced = true;
+    return GSIS_OK;
+}
+
+gsis_status gsis_iterate(gsis_ctx* c, int max_iter, gsis_report* rep) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!c->mesh_set || !c->vgrid_set) return set_err(c, GSIS_ERR_STATE, "set the mesh and velocity grid first");
+    if (max_iter < 0) return set_err(c, GSIS_ERR_ARG, "max_iter must be >= 0");
+    for (int i = 0; i < GSIS_NPHASE; ++i) c->phase_ms[i] = 0.0;
+    const long long l0 = c->launches, s0 = c->sweep_launches;
+    bool used[GSIS_NPHASE] = {false};
+    if (!c->started) {
+        used[GSIS_PH_PRESOLVE] = true;
+        st = start(c);
+        if (st != GSIS_OK) return st;
+        phase_collect(c, used);
+        used[GSIS_PH_PRESOLVE] = false;
+    }
+    int done = 0;
+    double eps = rep ? rep->eps : 0.0;
+    bool converged = false;
+    for (int it = 0; it < max_iter; ++it) {
+        for (bool& u : used) u = false;
+        st = gsis_step(c, &eps, used);
+        if (st != GSIS_OK) return st;
+        phase_collect(c, used);
+        ++done;
+        if (eps < c->p.tol) { converged = true; break; }
+    }
+    if (rep) {
+        rep->iterations = done;
+        rep->total_iterations = c->iteration;
+        rep->eps = eps;
+        rep->converged = converged ? 1 : 0;
+        rep->n_dvm = c->Nd;
+        rep->n_v = c->vg.Nv;
+        rep->vdf_bytes = c->Nd * c->vg.Nv * (long long)vdf_elem_bytes(c->p.vdf_dtype);
+        rep->presolve_blocks = c->presolve_blocks;
+        for (int i = 0; i < GSIS_NPHASE; ++i) rep->phase_ms[i] = c->phase_ms[i];
+        rep->sweep_launches = c->sweep_launches - s0;
+        rep->kernel_launches = c->launches - l0;
+    }
+    return GSIS_OK;
+}
+
+gsis_status gsis_moments(gsis_ctx* c, unsigned mask, double* dst, int dst_is_device) {
+    if (!c) return GSIS_ERR_ARG;
+    if (!dst) return set_err(c, GSIS_ERR_ARG, "NULL destination");
+    if (!c->mesh_set) return set_err(c, GSIS_ERR_STATE, "no mesh");
+    if (mask == 0 || mask >= (1u << GSIS_NFIELDS)) return set_err(c, GSIS_ERR_ARG, "bad field mask");
+    const int N = c->m.N;
+    std::vector<double> W((size_t)N * 5), hot((size_t)N * HOTN), kn(N, 0.0);
+    std::vector<int> c2d(N, -1);
+    if (c->started) {
+        cudaMemcpyAsync(W.data(), c->W, W.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hot.data(), c->hot, hot.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(kn.data(), c->kn_gll, kn.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(c2d.data(), c->cell2dvm, c2d.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, GSIS_ERR_CUDA, "gsis_moments copy failed");
+        }
+    } else {
+        W = c->host_W0;
+        std::fill(hot.begin(), hot.end(), 0.0);
+    }
+    int nsel = 0;
+    for (int b = 0; b < GSIS_NFIELDS; ++b) nsel += (mask >> b) & 1;
+    std::vector<double> out((size_t)N * nsel);
+    for (int cc = 0; cc < N; ++cc) {
+        int o = 0;
+        for (int b = 0; b < GSIS_NFIELDS; ++b) {
+            if (!((mask >> b) & 1)) continue;
+            double v;
+            if (b < 5) v = W[(size_t)cc * 5 + b];
+            else if (b < 14) v = hot[(size_t)cc * HOTN + (b - 5)];
+            else if (b == 14) v = kn[cc];
+            else v = c2d[cc] >= 0 ? 1.0 : 0.0;
+            out[(size_t)cc * nsel + o++] = v;
+        }
+    }
+    if (dst_is_device) {
+        if (cudaMemcpy(dst, out.data(), out.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, GSIS_ERR_ARG, "destination is not device memory");
+        }
+    } else {
+        std::memcpy(dst, out.data(), out.size() * 8);
+    }
+    return GSIS_OK;
+}
+
+gsis_status gsis_get_vdf(gsis_ctx* c, double* dst, int* cells, long long capacity) {
+    if (!c) return GSIS_ERR_ARG;
+    if (!c->started) return set_err(c, GSIS_ERR_STATE, "no VDF before the first iterate");
+    const long long n = c->Nd * c->vg.Nv;
+    if (!dst || capacity < n) return set_err(c, GSIS_ERR_ARG, "destination too small");
+    const size_t eb = vdf_elem_bytes(c->p.vdf_dtype);
+    std::vector<unsigned char> raw((size_t)n * eb);
+    cudaMemcpyAsync(raw.data(), c->f, raw.size(), cudaMemcpyDeviceToHost, c->stream);
+    std::vector<int> dc(c->Nd);
+    if (c->Nd) cudaMemcpyAsync(dc.data(), c->dvm_cell, dc.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, GSIS_ERR_CUDA, "gsis_get_vdf copy failed");
+    }
+    for (long long i = 0; i < n; ++i) {
+        double v;
+        switch (c->p.vdf_dtype) {
+            case GSIS_F64: std::memcpy(&v, &raw[(size_t)i * 8], 8); break;
+            case GSIS_F32: { float x; std::memcpy(&x, &raw[(size_t)i * 4], 4); v = x; break; }
+            case GSIS_BF16: { uint16_t h; std::memcpy(&h, &raw[(size_t)i * 2], 2); uint32_t b = (uint32_t)h << 16;
+                              float x; std::memcpy(&x, &b, 4); v = x; break; }
+            default: { uint16_t h; std::memcpy(&h, &raw[(size_t)i * 2], 2);
+                       __half_raw hr; hr.x = h; v = (double)__half2float(__half(hr)); break; }
+        }
+        dst[i] = v;
+    }
+    if (cells) std::memcpy(cells, dc.data(), dc.size() * 4);
+    return GSIS_OK;
+}
+
+const char* gsis_last_error(const gsis_ctx* c) {
+    if (!c) return "NULL context";
+    return c->err.c_str();
+}
+
+void gsis_free(gsis_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    cudaGetLastError();
+    std::vector<void*> all = c->allocations;
+    for (void* p : all) dev_free(c, p);
+    if (c->events)
+        for (int i = 0; i < 2 * GSIS_NPHASE; ++i) cudaEventDestroy(c->ev[i]);
+    if (c->h_eps) cudaFreeHost(c->h_eps);
+    if (c->h_count) cudaFreeHost(c->h_count);
+    delete c;
+}
+
+}  // extern "C"

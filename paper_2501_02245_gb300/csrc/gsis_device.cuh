@@ -1,0 +1,102 @@
+// Device helpers shared by the GSIS kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include "gsis_internal.h"
+
+namespace gsis {
+
+constexpr double GAMMA = 5.0 / 3.0;
+constexpr double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- storage conversion
+template <typename S> struct Store;
+template <> struct Store<double> {
+    static __device__ __forceinline__ double ld(const double* p) { return *p; }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    static __device__ __forceinline__ double ld(const float* p) { return (double)*p; }
+    static __device__ __forceinline__ void st(float* p, double v) { *p = (float)v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ double ld(const __nv_bfloat16* p) { return (double)__bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ double ld(const __half* p) { return (double)__half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, double v) { *p = __float2half_rn((float)v); }
+};
+
+// ---------------------------------------------------------------- small math
+__device__ __forceinline__ double minmod(double a, double b) {
+    return (a > 0.0 && b > 0.0) ? fmin(a, b) : ((a < 0.0 && b < 0.0) ? fmax(a, b) : 0.0);
+}
+
+__device__ __forceinline__ double viscosity(double T, double mu0, double omega) {
+    return mu0 * pow(T, omega);
+}
+
+// ---------------------------------------------------------------- velocity index
+__device__ __forceinline__ void vsplit(long long v, int nx, int ny, int& ix, int& iy, int& iz) {
+    ix = (int)(v % nx);
+    long long t = v / nx;
+    iy = (int)(t % ny);
+    iz = (int)(t / ny);
+}
+
+// ---------------------------------------------------------------- distribution records
+// value at node (ix, iy, iz): E_x E_y E_z * (p0 + B_x+B_y+B_z + (R_x+R_y+R_z)(C2_x+C2_y+C2_z)
+//                                              + 2 (P2xy cx cy + P2xz cx cz + P2yz cy cz))
+__device__ __forceinline__ double eval_rec(const double* __restrict__ scal, const double* __restrict__ tab,
+                                           int NT, int nx, int ny, int ix, int iy, int iz) {
+    const int jy = nx + iy, jz = nx + ny + iz;
+    double e = tab[ix] * tab[jy] * tab[jz];
+    const double* B = tab + NT;
+    const double* C2 = tab + 3 * NT;
+    const double* Rr = tab + 4 * NT;
+    double poly = scal[RS_P0] + (B[ix] + B[jy] + B[jz]) + (Rr[ix] + Rr[jy] + Rr[jz]) * (C2[ix] + C2[jy] + C2[jz]);
+    if (scal[RS_OFFD] != 0.0) {
+        const double* C = tab + 2 * NT;
+        double cx = C[ix], cy = C[jy], cz = C[jz];
+        poly += 2.0 * (scal[RS_P2XY] * cx * cy + scal[RS_P2XZ] * cx * cz + scal[RS_P2YZ] * cy * cz);
+    }
+    return e * poly;
+}
+
+__device__ __forceinline__ const double* rec_scal(const Records& r, long long i) { return r.scal + i * RS; }
+__device__ __forceinline__ const double* rec_tab(const Records& r, long long i, int NT) {
+    return r.tab + i * (long long)(NTAB * NT);
+}
+
+// ---------------------------------------------------------------- deterministic reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of K values per thread (blockDim.x a multiple of 32, <= 1024).
+// Result valid in thread 0 (returned there; other threads get partial values).
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* [32*K] */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) smem[wid * K + k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += smem[w * K + k];
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace gsis

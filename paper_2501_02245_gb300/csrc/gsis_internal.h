@@ -1,0 +1,167 @@
+// Internal declarations of the GSIS library (not part of the public ABI).
+//
+// Device data layout (all FP64 unless stated):
+//   mesh, per cell c (ncell = N):   vol[N], cen[N][3], hyper[N] (i+j+k, int)
+//   mesh, per cell side s (0..5 = i-lo, i-hi, j-lo, j-hi, k-lo, k-hi):
+//     nbr[N][6] (int, neighbour cell or -1), side_bc[N][6] (int),
+//     Sout[N][6][3] (outward area vector), xf[N][6][3], lsq_w[N][6][3]
+//   velocity grid: xi[NT] = x-nodes | y-nodes | z-nodes (NT = nx+ny+nz)
+//   DVM list (compacted kinetic cells, sorted by hyperplane, then flat index):
+//     dvm_cell[Nd] (int), cell2dvm[N] (int, -1 for NS cells), hp_off[H+1]
+//     dside_kind[Nd][6], dside_ref[Nd][6], dside_nb2[Nd][6] (int)
+//     SoV[Nd][6][3] = Sout/V of the DVM cell
+//     f[Nd][Nv] in the storage type, velocity index innermost (x fastest)
+//   distribution records (EqRec): scalar block [RS] + five axis tables [5][NT]
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "../../include/gsis.h"
+
+namespace gsis {
+
+constexpr int RS = 16;          // scalars per distribution record
+constexpr int NTAB = 5;         // axis tables per record: E, B, C, C2, R
+constexpr int MOMN = 19;        // 13 velocity moments + 6 wall half-range fluxes
+constexpr int HOTN = 9;         // sigma xx,yy,zz,xy,xz,yz; q x,y,z
+
+// record scalar slots
+enum { RS_P0 = 0, RS_P2XY = 1, RS_P2XZ = 2, RS_P2YZ = 3, RS_OFFD = 4, RS_UX = 5, RS_UY = 6, RS_UZ = 7,
+       RS_ALPHA0 = 8 };
+
+// DVM side kinds
+enum { SK_NONE = 0, SK_DVM = 1, SK_GHOST = 2, SK_FAR = 3, SK_WALL = 4 };
+
+struct VGridDev {
+    int nx, ny, nz, NT;
+    long long Nv;
+    double w;
+    const double* xi;            // [NT]
+};
+
+struct Records {                 // R records
+    double* scal;                // [R][RS]
+    double* tab;                 // [R][NTAB][NT]
+};
+
+// Base polynomial of a record in c = xi - u:
+//   p0 + p.c + c.P2.c + (r.c) c^2, optionally conservation-corrected to U.
+struct RecSpec {
+    double rho, u[3], T;         // Maxwellian factor
+    double p0, p[3], P2[6], r[3];
+    double U[5];                 // target conserved moments (rho, rho u, rho E)
+    int correct;
+};
+
+struct Mesh {
+    int ni = 0, nj = 0, nk = 0, dim = 0, N = 0, H = 0;
+    int bc_type[6];
+    double bc_state[6][5];
+    double *vol = nullptr, *cen = nullptr, *Sout = nullptr, *xf = nullptr, *lsq_w = nullptr;
+    int *nbr = nullptr, *side_bc = nullptr, *hyper = nullptr;
+};
+
+struct Ctx;
+}  // namespace gsis
+
+struct gsis_ctx {
+    gsis_params p{};
+    gsis_allocator alloc{};
+    bool have_alloc = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    bool broken = false;
+    bool mesh_set = false, vgrid_set = false, started = false;
+    std::vector<void*> allocations;
+    double mu0 = 0.0;
+
+    gsis::Mesh m;
+    int* d_bc_type = nullptr;      // [6]
+    double* d_bc_state = nullptr;  // [6][5]
+    std::vector<double> host_W0;
+    std::vector<uint8_t> forced_flags;
+    bool have_forced = false;
+
+    // velocity grid
+    int nv3[3] = {0, 0, 0};
+    double vlo[3], vhi[3];
+    gsis::VGridDev vg{};
+    double* d_xi = nullptr;
+
+    // macro state
+    double *W = nullptr, *Wh = nullptr, *Wp = nullptr, *Wm = nullptr, *U = nullptr, *Un = nullptr;
+    double *dU = nullptr, *dU2 = nullptr, *R = nullptr, *D = nullptr, *lamS = nullptr;
+    double *gu = nullptr, *gT = nullptr, *grho = nullptr, *gU = nullptr;
+    double *hot = nullptr, *kin = nullptr, *nsf = nullptr, *kn_gll = nullptr;
+    double *eps_buf = nullptr, *h_eps = nullptr;
+    int *err_flag = nullptr, *h_err = nullptr;
+    uint8_t* flag = nullptr;
+
+    // DVM state
+    long long Nd = 0, cap_Nd = 0;
+    int *dvm_cell = nullptr, *cell2dvm = nullptr, *hp_off = nullptr, *hp_cnt = nullptr;
+    int *dside_kind = nullptr, *dside_ref = nullptr, *dside_nb2 = nullptr;
+    double* SoV = nullptr;
+    void* f = nullptr;
+    double *tau = nullptr, *mom = nullptr, *rho_w = nullptr, *wall_den = nullptr;
+    gsis::Records recG{}, recHalf{}, recNew{}, recGhost{}, recBC{};
+    int* ghost_id = nullptr;       // [N] ghost record index or -1
+    int* ghost_cell = nullptr;     // [N] cell of each ghost record
+    int n_ghost = 0;
+    gsis::RecSpec* specs = nullptr;  // scratch, capacity N records
+    double* momh = nullptr;        // [Nd][MOMN] moments of f^{n+1/2}
+    int* old_cell2dvm = nullptr;   // [N] scratch for re-compaction
+    int* enter_list = nullptr;     // [N] scratch: DVM indices entering the region
+    int* enter_of = nullptr;       // [Nd] entering slot of each DVM cell or -1
+    int* d_count = nullptr;        // scratch counters
+    int* h_count = nullptr;
+
+    // bookkeeping
+    int iteration = 0;
+    int presolve_blocks = 0;
+    long long launches = 0, sweep_launches = 0;
+    cudaEvent_t ev[2 * GSIS_NPHASE];
+    bool events = false;
+    double phase_ms[GSIS_NPHASE];
+};
+
+namespace gsis {
+
+// ---------------------------------------------------------------------------- kernels (launchers)
+// equilibrium.cu
+void launch_build_records(gsis_ctx* c, const Records& out, int nrec, const RecSpec* d_specs);
+void launch_cell_eq(gsis_ctx* c);
+void launch_bc_records(gsis_ctx* c);
+void launch_wall_den(gsis_ctx* c);
+void launch_ghost_records(gsis_ctx* c);
+void launch_correction_records(gsis_ctx* c);
+void launch_seed_records(gsis_ctx* c, int n_enter, int grad13);
+// sweep.cu
+void launch_sweep(gsis_ctx* c, int pass);
+// moments.cu
+void launch_moments(gsis_ctx* c, const double* Wref, int correct_pass, double* out);
+void launch_half_state(gsis_ctx* c);
+void launch_hot(gsis_ctx* c);
+// macro.cu
+void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U);
+void launch_nsf(gsis_ctx* c, const double* Wprim, double* out);
+void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons);
+void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim);
+void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term);
+void launch_eps(gsis_ctx* c, const double* Wn, const double* Wp);
+// adapt.cu
+void launch_kn_gll(gsis_ctx* c, const double* Wprim);
+int  build_region(gsis_ctx* c);   // returns new Nd; builds lists and remaps f
+
+// ---------------------------------------------------------------------------- host helpers
+gsis_status set_err(gsis_ctx* c, gsis_status s, const std::string& msg);
+void* dev_alloc(gsis_ctx* c, size_t bytes);
+void dev_free(gsis_ctx* c, void* p);
+size_t vdf_elem_bytes(int dtype);
+bool cuda_ok(gsis_ctx* c, cudaError_t e, const char* what);
+
+}  // namespace gsis
+
+#define GSIS_LAUNCH_CHECK(ctx) do { (ctx)->launches++; } while (0)

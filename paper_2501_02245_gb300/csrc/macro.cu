@@ -1,0 +1,499 @@
+// Macroscopic synthetic solve (Eq. macro with the constitutive relations of
+// Eq. full_constitutive and Eq. NSF_constitutive), monatomic gas, on ALL cells.
+//
+// Flux and relaxation choices (the paper defers them to another work; the
+// same choices are made in the CPU reference):
+//  * inviscid: HLLC with Davis wave speeds on index-space MUSCL-minmod states
+//    of (rho, u, p), first order next to boundaries;
+//  * viscous: NSF from the mean of the two cells' least-squares gradients
+//    corrected along the line of centres, at the mean cell u and T, plus the
+//    mean of the two cells' HoT;
+//  * far field: HLLC against the boundary state plus the cell's HoT;
+//    wall: cell pressure, no mass flux, NSF at u = 0 and T = T_w from a
+//    one-sided gradient, plus the cell's HoT;
+//  * DP-LUR pseudo-time relaxation (Wright, Candler & Bose 1998): scalar
+//    diagonal (1/CFL + 1/2) sum lambda |S| (+ V/dt with the time term of
+//    Eq. macro), k_sub Jacobi sweeps over Rusanov-split Euler flux changes.
+// Each interior face flux is evaluated by both of its cells with the same
+// canonical orientation (low-index cell = L), so the two evaluations are
+// bitwise equal and the scheme is exactly conservative.
+#include "gsis_device.cuh"
+
+namespace gsis {
+
+struct MacroArgs {
+    int N;
+    const int* nbr;
+    const int* side_bc;
+    const double* Sout;
+    const double* xf;
+    const double* cen;
+    const double* vol;
+    const double* lsq_w;
+    const double* bc_state;   // [6][5]
+    double mu0, omega;
+};
+
+static MacroArgs margs(gsis_ctx* c) {
+    MacroArgs a;
+    a.N = c->m.N;
+    a.nbr = c->m.nbr;
+    a.side_bc = c->m.side_bc;
+    a.Sout = c->m.Sout;
+    a.xf = c->m.xf;
+    a.cen = c->m.cen;
+    a.vol = c->m.vol;
+    a.lsq_w = c->m.lsq_w;
+    a.bc_state = c->d_bc_state;
+    a.mu0 = c->mu0;
+    a.omega = c->p.omega;
+    return a;
+}
+
+// ---------------------------------------------------------------------------- gradients
+// Least-squares gradient (face neighbours plus boundary face centres with the
+// boundary value: far field -> boundary state; wall -> u = 0, |u| = 0, T = T_w,
+// rho = cell value).  gu[c][j][i] = d u_j / d x_i.
+__global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with_rho_U, double* __restrict__ gu,
+                            double* __restrict__ gT, double* __restrict__ grho, double* __restrict__ gU) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    const double* wc = Wp + c * 5;
+    const double Uc = sqrt(wc[1] * wc[1] + wc[2] * wc[2] + wc[3] * wc[3]);
+    double g[6][3];
+    for (int q = 0; q < 6; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
+    for (int s = 0; s < 6; ++s) {
+        const int n = a.nbr[c * 6 + s];
+        const int bc = a.side_bc[c * 6 + s];
+        double val[6];   // ux, uy, uz, T, rho, U
+        if (n >= 0) {
+            const double* wn = Wp + n * 5;
+            val[0] = wn[1]; val[1] = wn[2]; val[2] = wn[3]; val[3] = wn[4]; val[4] = wn[0];
+            val[5] = sqrt(wn[1] * wn[1] + wn[2] * wn[2] + wn[3] * wn[3]);
+        } else if (bc == GSIS_BC_FARFIELD) {
+            const double* st = a.bc_state + s * 5;
+            val[0] = st[1]; val[1] = st[2]; val[2] = st[3]; val[3] = st[4]; val[4] = st[0];
+            val[5] = sqrt(st[1] * st[1] + st[2] * st[2] + st[3] * st[3]);
+        } else if (bc == GSIS_BC_WALL) {
+            const double* st = a.bc_state + s * 5;
+            val[0] = 0.0; val[1] = 0.0; val[2] = 0.0; val[3] = st[4]; val[4] = wc[0]; val[5] = 0.0;
+        } else {
+            continue;
+        }
+        const double phic[6] = {wc[1], wc[2], wc[3], wc[4], wc[0], Uc};
+        const double* w = a.lsq_w + ((long long)c * 6 + s) * 3;
+        for (int q = 0; q < 6; ++q) {
+            const double dphi = val[q] - phic[q];
+            g[q][0] += w[0] * dphi;
+            g[q][1] += w[1] * dphi;
+            g[q][2] += w[2] * dphi;
+        }
+    }
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) gu[(long long)c * 9 + j * 3 + i] = g[j][i];
+    for (int i = 0; i < 3; ++i) gT[(long long)c * 3 + i] = g[3][i];
+    if (with_rho_U) {
+        for (int i = 0; i < 3; ++i) {
+            grho[(long long)c * 3 + i] = g[4][i];
+            gU[(long long)c * 3 + i] = g[5][i];
+        }
+    }
+}
+
+void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U) {
+    const int N = c->m.N;
+    k_gradients<<<(N + 127) / 128, 128, 0, c->stream>>>(margs(c), Wprim, with_rho_U ? 1 : 0, c->gu, c->gT, c->grho,
+                                                        c->gU);
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------- NSF
+__device__ __forceinline__ void nsf_of(double mu, const double* gu /*[j][i]*/, const double* gT, double* sig,
+                                       double* q) {
+    // G[i][j] = d u_j / d x_i = gu[j*3 + i]
+    const double div = gu[0] + gu[4] + gu[8];
+    const double two3 = 2.0 / 3.0;
+    sig[0] = -mu * (2.0 * gu[0] - two3 * div);
+    sig[1] = -mu * (2.0 * gu[4] - two3 * div);
+    sig[2] = -mu * (2.0 * gu[8] - two3 * div);
+    sig[3] = -mu * (gu[0 * 3 + 1] + gu[1 * 3 + 0]);   // xy: du_x/dy + du_y/dx
+    sig[4] = -mu * (gu[0 * 3 + 2] + gu[2 * 3 + 0]);   // xz
+    sig[5] = -mu * (gu[1 * 3 + 2] + gu[2 * 3 + 1]);   // yz
+    const double kap = 3.75 * mu;
+    q[0] = -kap * gT[0];
+    q[1] = -kap * gT[1];
+    q[2] = -kap * gT[2];
+}
+
+__global__ void k_nsf(int N, const double* __restrict__ Wp, const double* __restrict__ gu,
+                      const double* __restrict__ gT, double mu0, double omega, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const double mu = viscosity(Wp[c * 5 + 4], mu0, omega);
+    nsf_of(mu, gu + (long long)c * 9, gT + (long long)c * 3, out + (long long)c * HOTN, out + (long long)c * HOTN + 6);
+}
+
+void launch_nsf(gsis_ctx* c, const double* Wprim, double* out) {
+    launch_gradients(c, Wprim, false);
+    const int N = c->m.N;
+    k_nsf<<<(N + 127) / 128, 128, 0, c->stream>>>(N, Wprim, c->gu, c->gT, c->mu0, c->p.omega, out);
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------- conversions
+__global__ void k_prim_to_cons(int N, const double* __restrict__ Wp, double* __restrict__ U) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const double r = Wp[c * 5], ux = Wp[c * 5 + 1], uy = Wp[c * 5 + 2], uz = Wp[c * 5 + 3], T = Wp[c * 5 + 4];
+    U[c * 5] = r;
+    U[c * 5 + 1] = r * ux;
+    U[c * 5 + 2] = r * uy;
+    U[c * 5 + 3] = r * uz;
+    U[c * 5 + 4] = r * (1.5 * T + 0.5 * (ux * ux + uy * uy + uz * uz));
+}
+
+__device__ __forceinline__ void cons_to_prim(const double* U, double* Wp) {
+    const double r = U[0];
+    const double ux = U[1] / r, uy = U[2] / r, uz = U[3] / r;
+    Wp[0] = r;
+    Wp[1] = ux;
+    Wp[2] = uy;
+    Wp[3] = uz;
+    Wp[4] = (2.0 * U[4] / r - (ux * ux + uy * uy + uz * uz)) / 3.0;
+}
+
+__global__ void k_cons_to_prim(int N, const double* __restrict__ U, double* __restrict__ Wp) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    cons_to_prim(U + c * 5, Wp + c * 5);
+}
+
+void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons) {
+    const int N = c->m.N;
+    k_prim_to_cons<<<(N + 127) / 128, 128, 0, c->stream>>>(N, Wprim, Ucons);
+    c->launches++;
+}
+
+void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim) {
+    const int N = c->m.N;
+    k_cons_to_prim<<<(N + 127) / 128, 128, 0, c->stream>>>(N, Ucons, Wprim);
+    c->launches++;
+}
+
+// ---------------------------------------------------------------------------- fluxes
+// HLLC flux per unit area through the unit normal n (Toro, ch. 10).
+__device__ void hllc(double rL, const double* uL, double pL, double rR, const double* uR, double pR,
+                     const double* n, double* F) {
+    const double g = GAMMA;
+    const double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+    const double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+    const double aL = sqrt(g * pL / rL), aR = sqrt(g * pR / rR);
+    const double EL = pL / (g - 1.0) + 0.5 * rL * (uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2]);
+    const double ER = pR / (g - 1.0) + 0.5 * rR * (uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2]);
+    const double SL = fmin(unL - aL, unR - aR);
+    const double SR = fmax(unL + aL, unR + aR);
+    const double Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR));
+    // F_L if S_L >= 0; else F*_L if S* >= 0; else F*_R if S_R >= 0; else F_R
+    const bool left = (SL >= 0.0) || (Ss >= 0.0);
+    const bool use_plain = (SL >= 0.0) || !(left || SR >= 0.0);
+    // the side whose flux (or star flux) is needed
+    const double r = left ? rL : rR;
+    const double* u = left ? uL : uR;
+    const double p = left ? pL : pR;
+    const double E = left ? EL : ER;
+    const double un = left ? unL : unR;
+    const double S = left ? SL : SR;
+    double Fk[5];
+    Fk[0] = r * un;
+    for (int d = 0; d < 3; ++d) Fk[1 + d] = r * u[d] * un + p * n[d];
+    Fk[4] = (E + p) * un;
+    if (use_plain) {
+        for (int q = 0; q < 5; ++q) F[q] = Fk[q];
+        return;
+    }
+    const double coef = r * (S - un) / (S - Ss);
+    const double e = E / r + (Ss - un) * (Ss + p / (r * (S - un)));
+    F[0] = Fk[0] + S * (coef - r);
+    for (int d = 0; d < 3; ++d) F[1 + d] = Fk[1 + d] + S * (coef * (u[d] + (Ss - un) * n[d]) - r * u[d]);
+    F[4] = Fk[4] + S * (coef * e - E);
+}
+
+__device__ __forceinline__ void euler_flux_dot(const double* U, const double* S, double* F) {
+    const double r = U[0];
+    const double ux = U[1] / r, uy = U[2] / r, uz = U[3] / r;
+    const double p = (GAMMA - 1.0) * (U[4] - 0.5 * r * (ux * ux + uy * uy + uz * uz));
+    const double uS = ux * S[0] + uy * S[1] + uz * S[2];
+    F[0] = r * uS;
+    F[1] = U[1] * uS + p * S[0];
+    F[2] = U[2] * uS + p * S[1];
+    F[3] = U[3] * uS + p * S[2];
+    F[4] = (U[4] + p) * uS;
+}
+
+__device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u, p)
+    q[0] = w[0]; q[1] = w[1]; q[2] = w[2]; q[3] = w[3]; q[4] = w[0] * w[4];
+}
+
+// Residual R_c = -sum_F F.S_out, spectral radii, diagonal D and dU0 = R/D.
+__global__ void k_residual(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ U,
+                           const double* __restrict__ Un, const double* __restrict__ gu,
+                           const double* __restrict__ gT, const double* __restrict__ hot, double cfl, double dt,
+                           double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
+                           double* __restrict__ dU) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    const double* wc = Wm + c * 5;
+    const double rho_c = wc[0], T_c = wc[4], p_c = rho_c * T_c;
+    const double u_c[3] = {wc[1], wc[2], wc[3]};
+    const double a_c = sqrt(GAMMA * p_c / rho_c);
+    const double mu_c = viscosity(T_c, a.mu0, a.omega);
+    double Rc[5] = {0, 0, 0, 0, 0};
+    double lam_sum = 0.0;
+    for (int s = 0; s < 6; ++s) {
+        const int n = a.nbr[c * 6 + s];
+        const int bc = a.side_bc[c * 6 + s];
+        const double* So = a.Sout + ((long long)c * 6 + s) * 3;
+        if (n >= 0) {
+            const bool isL = (s & 1) != 0;
+            const int L = isL ? c : n, Rr = isL ? n : c;
+            const double S[3] = {isL ? So[0] : -So[0], isL ? So[1] : -So[1], isL ? So[2] : -So[2]};
+            const int d = s >> 1;
+            const double Sabs = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+            const double nn[3] = {S[0] / Sabs, S[1] / Sabs, S[2] / Sabs};
+            double qL[5], qR[5], qq[5], slL[5] = {0, 0, 0, 0, 0}, slR[5] = {0, 0, 0, 0, 0};
+            prim5(Wm + L * 5, qL);
+            prim5(Wm + Rr * 5, qR);
+            {
+                const int lo = a.nbr[L * 6 + 2 * d], hi = a.nbr[L * 6 + 2 * d + 1];
+                if (lo >= 0 && hi >= 0) {
+                    double ql[5], qh[5];
+                    prim5(Wm + lo * 5, ql);
+                    prim5(Wm + hi * 5, qh);
+                    for (int q = 0; q < 5; ++q) slL[q] = minmod(qL[q] - ql[q], qh[q] - qL[q]);
+                }
+            }
+            {
+                const int lo = a.nbr[Rr * 6 + 2 * d], hi = a.nbr[Rr * 6 + 2 * d + 1];
+                if (lo >= 0 && hi >= 0) {
+                    double ql[5], qh[5];
+                    prim5(Wm + lo * 5, ql);
+                    prim5(Wm + hi * 5, qh);
+                    for (int q = 0; q < 5; ++q) slR[q] = minmod(qR[q] - ql[q], qh[q] - qR[q]);
+                }
+            }
+            double fl[5], fr[5];
+            for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + 0.5 * slL[q]; fr[q] = qR[q] - 0.5 * slR[q]; }
+            double F[5];
+            hllc(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, F);
+            for (int q = 0; q < 5; ++q) F[q] *= Sabs;
+            // viscous + HoT
+            const double* wL = Wm + L * 5;
+            const double* wR = Wm + Rr * 5;
+            const double uf[3] = {0.5 * (wL[1] + wR[1]), 0.5 * (wL[2] + wR[2]), 0.5 * (wL[3] + wR[3])};
+            const double Tf = 0.5 * (wL[4] + wR[4]);
+            const double muf = viscosity(Tf, a.mu0, a.omega);
+            double e[3];
+            for (int i = 0; i < 3; ++i) e[i] = a.cen[Rr * 3 + i] - a.cen[L * 3 + i];
+            const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            for (int i = 0; i < 3; ++i) e[i] /= dist;
+            double guf[9], gTf[3];
+            for (int j = 0; j < 3; ++j) {
+                double gav[3];
+                for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gu[(long long)L * 9 + j * 3 + i] + gu[(long long)Rr * 9 + j * 3 + i]);
+                const double corr = (wR[1 + j] - wL[1 + j]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
+                for (int i = 0; i < 3; ++i) guf[j * 3 + i] = gav[i] + corr * e[i];
+            }
+            {
+                double gav[3];
+                for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gT[(long long)L * 3 + i] + gT[(long long)Rr * 3 + i]);
+                const double corr = (wR[4] - wL[4]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
+                for (int i = 0; i < 3; ++i) gTf[i] = gav[i] + corr * e[i];
+            }
+            double sig[6], qf[3];
+            nsf_of(muf, guf, gTf, sig, qf);
+            const double* hL = hot + (long long)L * HOTN;
+            const double* hR = hot + (long long)Rr * HOTN;
+            double Sg[6], Q[3];
+            for (int q = 0; q < 6; ++q) Sg[q] = sig[q] + 0.5 * (hL[q] + hR[q]);
+            for (int q = 0; q < 3; ++q) Q[q] = qf[q] + 0.5 * (hL[6 + q] + hR[6 + q]);
+            const double SigS[3] = {Sg[0] * S[0] + Sg[3] * S[1] + Sg[4] * S[2],
+                                    Sg[3] * S[0] + Sg[1] * S[1] + Sg[5] * S[2],
+                                    Sg[4] * S[0] + Sg[5] * S[1] + Sg[2] * S[2]};
+            F[1] += SigS[0];
+            F[2] += SigS[1];
+            F[3] += SigS[2];
+            F[4] += (SigS[0] * uf[0] + SigS[1] * uf[1] + SigS[2] * uf[2]) + (Q[0] * S[0] + Q[1] * S[1] + Q[2] * S[2]);
+            const double sgn = isL ? -1.0 : 1.0;
+            for (int q = 0; q < 5; ++q) Rc[q] += sgn * F[q];
+            const double aL = sqrt(GAMMA * wL[4]), aR = sqrt(GAMMA * wR[4]);
+            const double lam = fabs(uf[0] * nn[0] + uf[1] * nn[1] + uf[2] * nn[2]) + 0.5 * (aL + aR) +
+                               5.0 * muf / (0.5 * (wL[0] + wR[0]) * dist);
+            lamS[(long long)c * 6 + s] = lam * Sabs;
+            lam_sum += lam * Sabs;
+        } else if (bc == GSIS_BC_FARFIELD || bc == GSIS_BC_WALL) {
+            const double* st = a.bc_state + s * 5;
+            const double Sabs = sqrt(So[0] * So[0] + So[1] * So[1] + So[2] * So[2]);
+            const double nn[3] = {So[0] / Sabs, So[1] / Sabs, So[2] / Sabs};
+            const double* h = hot + (long long)c * HOTN;
+            double Fb[5];
+            double eb[3];
+            for (int i = 0; i < 3; ++i) eb[i] = a.xf[((long long)c * 6 + s) * 3 + i] - a.cen[c * 3 + i];
+            const double bdist = sqrt(eb[0] * eb[0] + eb[1] * eb[1] + eb[2] * eb[2]);
+            if (bc == GSIS_BC_FARFIELD) {
+                hllc(rho_c, u_c, p_c, st[0], st + 1, st[0] * st[4], nn, Fb);
+                for (int q = 0; q < 5; ++q) Fb[q] *= Sabs;
+                const double SigS[3] = {h[0] * So[0] + h[3] * So[1] + h[4] * So[2],
+                                        h[3] * So[0] + h[1] * So[1] + h[5] * So[2],
+                                        h[4] * So[0] + h[5] * So[1] + h[2] * So[2]};
+                const double ufb[3] = {0.5 * (u_c[0] + st[1]), 0.5 * (u_c[1] + st[2]), 0.5 * (u_c[2] + st[3])};
+                Fb[1] += SigS[0];
+                Fb[2] += SigS[1];
+                Fb[3] += SigS[2];
+                Fb[4] += (SigS[0] * ufb[0] + SigS[1] * ufb[1] + SigS[2] * ufb[2]) +
+                         (h[6] * So[0] + h[7] * So[1] + h[8] * So[2]);
+            } else {
+                const double Tw = st[4];
+                for (int i = 0; i < 3; ++i) eb[i] /= bdist;
+                double guw[9], gTw[3];
+                for (int j = 0; j < 3; ++j) {
+                    const double* gc = gu + (long long)c * 9 + j * 3;
+                    const double corr = (0.0 - u_c[j]) / bdist - (gc[0] * eb[0] + gc[1] * eb[1] + gc[2] * eb[2]);
+                    for (int i = 0; i < 3; ++i) guw[j * 3 + i] = gc[i] + corr * eb[i];
+                }
+                {
+                    const double* gc = gT + (long long)c * 3;
+                    const double corr = (Tw - T_c) / bdist - (gc[0] * eb[0] + gc[1] * eb[1] + gc[2] * eb[2]);
+                    for (int i = 0; i < 3; ++i) gTw[i] = gc[i] + corr * eb[i];
+                }
+                double sig[6], qw[3];
+                nsf_of(viscosity(Tw, a.mu0, a.omega), guw, gTw, sig, qw);
+                double Sg[6], Q[3];
+                for (int q = 0; q < 6; ++q) Sg[q] = sig[q] + h[q];
+                for (int q = 0; q < 3; ++q) Q[q] = qw[q] + h[6 + q];
+                const double SigS[3] = {Sg[0] * So[0] + Sg[3] * So[1] + Sg[4] * So[2],
+                                        Sg[3] * So[0] + Sg[1] * So[1] + Sg[5] * So[2],
+                                        Sg[4] * So[0] + Sg[5] * So[1] + Sg[2] * So[2]};
+                Fb[0] = 0.0;
+                Fb[1] = p_c * So[0] + SigS[0];
+                Fb[2] = p_c * So[1] + SigS[1];
+                Fb[3] = p_c * So[2] + SigS[2];
+                Fb[4] = Q[0] * So[0] + Q[1] * So[1] + Q[2] * So[2];
+            }
+            for (int q = 0; q < 5; ++q) Rc[q] -= Fb[q];
+            const double lam = fabs(u_c[0] * nn[0] + u_c[1] * nn[1] + u_c[2] * nn[2]) + a_c +
+                               5.0 * mu_c / (rho_c * 2.0 * bdist);
+            lamS[(long long)c * 6 + s] = lam * Sabs;
+            lam_sum += lam * Sabs;
+        } else {
+            lamS[(long long)c * 6 + s] = 0.0;
+        }
+    }
+    double Dc = (1.0 / cfl + 0.5) * lam_sum;
+    if (dt > 0.0) {
+        const double Vdt = a.vol[c] / dt;
+        for (int q = 0; q < 5; ++q) Rc[q] -= Vdt * (U[c * 5 + q] - Un[c * 5 + q]);
+        Dc += Vdt;
+    }
+    D[c] = Dc;
+    for (int q = 0; q < 5; ++q) {
+        R[c * 5 + q] = Rc[q];
+        dU[c * 5 + q] = Rc[q] / Dc;
+    }
+}
+
+// One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D.
+__global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double* __restrict__ R,
+                        const double* __restrict__ D, const double* __restrict__ lamS, const double* __restrict__ dUin,
+                        double* __restrict__ dUout) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    double off[5] = {0, 0, 0, 0, 0};
+    for (int s = 0; s < 6; ++s) {
+        const int n = a.nbr[c * 6 + s];
+        if (n < 0) continue;
+        const double* So = a.Sout + ((long long)c * 6 + s) * 3;
+        double Uj[5], Uj2[5], F1[5], F0[5];
+        for (int q = 0; q < 5; ++q) { Uj[q] = U[n * 5 + q]; Uj2[q] = Uj[q] + dUin[n * 5 + q]; }
+        euler_flux_dot(Uj2, So, F1);
+        euler_flux_dot(Uj, So, F0);
+        const double ls = lamS[(long long)c * 6 + s];
+        for (int q = 0; q < 5; ++q) off[q] += 0.5 * ((F1[q] - F0[q]) - ls * dUin[n * 5 + q]);
+    }
+    for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) / D[c];
+}
+
+__global__ void k_update(int N, double* __restrict__ U, const double* __restrict__ dU, double* __restrict__ Wm) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    for (int q = 0; q < 5; ++q) U[c * 5 + q] += dU[c * 5 + q];
+    cons_to_prim(U + c * 5, Wm + c * 5);
+}
+
+// `steps` DP-LUR pseudo-steps on c->U / c->Wm (prim kept in step), HoT from c->hot,
+// time term against c->Un when time_term.
+void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term) {
+    (void)with_hot;
+    const int N = c->m.N;
+    const int nb = (N + 127) / 128;
+    MacroArgs a = margs(c);
+    const double dt = time_term ? c->p.dt : 0.0;
+    for (int it = 0; it < steps; ++it) {
+        launch_gradients(c, c->Wm, false);
+        k_residual<<<nb, 128, 0, c->stream>>>(a, c->Wm, c->U, c->Un, c->gu, c->gT, c->hot, c->p.cfl, dt, c->R, c->D,
+                                             c->lamS, c->dU);
+        c->launches++;
+        double* din = c->dU;
+        double* dout = c->dU2;
+        for (int s = 0; s < c->p.k_sub; ++s) {
+            k_relax<<<nb, 128, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout);
+            c->launches++;
+            double* t = din; din = dout; dout = t;
+        }
+        k_update<<<nb, 128, 0, c->stream>>>(N, c->U, din, c->Wm);
+        c->launches++;
+    }
+}
+
+// ---------------------------------------------------------------------------- residual epsilon
+// Convergence criterion of Sec. 4: max over {rho, u (as a vector), T} of
+// sqrt(sum (Wn - Wp)^2 vol / sum Wp^2 vol), quantities with a zero denominator
+// left out.  out[0] = epsilon, out[1] = number of cells with non-finite or
+// non-positive rho / T in Wn.
+__global__ void k_eps(int N, const double* __restrict__ Wn, const double* __restrict__ Wp,
+                      const double* __restrict__ vol, double* __restrict__ out) {
+    __shared__ double sm[32 * 7];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const double V = vol[c];
+        const double* a = Wn + c * 5;
+        const double* b = Wp + c * 5;
+        const double dr = a[0] - b[0];
+        acc[0] += dr * dr * V;
+        acc[1] += b[0] * b[0] * V;
+        double du = 0.0, uu = 0.0;
+        for (int i = 1; i < 4; ++i) { du += (a[i] - b[i]) * (a[i] - b[i]); uu += b[i] * b[i]; }
+        acc[2] += du * V;
+        acc[3] += uu * V;
+        const double dT = a[4] - b[4];
+        acc[4] += dT * dT * V;
+        acc[5] += b[4] * b[4] * V;
+        bool bad = !(a[0] > 0.0) || !(a[4] > 0.0) || !isfinite(a[0]) || !isfinite(a[4]);
+        for (int i = 1; i < 4; ++i) bad = bad || !isfinite(a[i]);
+        acc[6] += bad ? 1.0 : 0.0;
+    }
+    block_sum<7>(acc, sm);
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int q = 0; q < 3; ++q)
+            if (acc[2 * q + 1] > 0.0) e = fmax(e, sqrt(acc[2 * q] / acc[2 * q + 1]));
+        out[0] = e;
+        out[1] = acc[6];
+    }
+}
+
+void launch_eps(gsis_ctx* c, const double* Wn, const double* Wp) {
+    k_eps<<<1, 1024, 0, c->stream>>>(c->m.N, Wn, Wp, c->m.vol, c->eps_buf);
+    c->launches++;
+}
+
+}  // namespace gsis

@@ -1,0 +1,49 @@
+"""Shared helpers for the GPU parity tests: run the CUDA path (through the C
+ABI) and the oracle on the same seeded case and collect comparable states."""
+import numpy as np
+
+from oracle.gsis import OracleSolver
+
+# FP64 tolerance on macroscopic fields (relative), the stated target of the path.
+RTOL_W = 1e-10
+
+
+def rel_err(a, b, scale=None):
+    a = np.asarray(a); b = np.asarray(b)
+    s = np.max(np.abs(b)) if scale is None else scale
+    return float(np.max(np.abs(a - b)) / max(s, 1e-300))
+
+
+def w_rel_err(Wg, Wo):
+    """Max over the five primitive fields of max|dW| / max|W| (velocity as one field)."""
+    errs = [rel_err(Wg[:, 0], Wo[:, 0]), rel_err(Wg[:, 1:4], Wo[:, 1:4]), rel_err(Wg[:, 4], Wo[:, 4])]
+    return max(errs)
+
+
+def run_oracle(case, n_iter, flags=None):
+    o = OracleSolver(case, flags_override=flags)
+    o.initialise()
+    hist = [o.W.copy()]
+    for _ in range(n_iter):
+        o.step()
+        hist.append(o.W.copy())
+    return o, hist
+
+
+def run_gpu(case, n_iter, vdf_dtype="f64", flags=None):
+    from paper_2501_02245_gb300 import Solver
+    s = Solver.from_case(case, vdf_dtype=vdf_dtype, forced_flags=flags)
+    s.iterate(0)
+    hist = [s.W()]
+    reps = []
+    for _ in range(n_iter):
+        reps.append(s.iterate(1))
+        hist.append(s.W())
+    return s, hist, reps
+
+
+def vdf_by_cell(solver, n_dvm, ncell, nv):
+    cells, f = solver.vdf(n_dvm)
+    full = np.zeros((ncell, nv))
+    full[cells] = f
+    return full
