@@ -1,0 +1,315 @@
+"""Benchmark of the adaptive GSIS hot path on one GB300 (or N independent replicas).
+
+Default workload: hypersonic cylinder, Ma = 5, Kn = 0.01, wall at 2 T_inf,
+128 x 128 O-grid, 48x48x24 velocity grid, FP64, adaptive with Kn_ref = 0.01.
+A step is one GSIS iteration (cell equilibrium, kinetic sweep, moments and
+HoT, synthetic solve, VDF correction, residual) over the resident state.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsis|reference]
+                    [--config cylinder|shock|cylinder_full|sphere] [--dtype f64|f32|bf16|f16]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload (a 12 x 12 O-grid with the same velocity
+grid), in the same metric.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell×velocity updates/s and time-to-converged state vs plain FP64 GPU"
+UNIT = "cell*velocity updates/s"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk (4 flop) x 2.07 GHz
+# algorithmic FP64 flops of one point update of the kinetic sweep on a 2D
+# structured mesh (4 active faces, FMA = 2), counted from the scheme: reference
+# distribution and 1/tau 14, face normal speeds 4 x 5, two outgoing faces 2 x 4,
+# two own limited slopes 2 x 4, two incoming MUSCL face values 2 x 8, division 1.
+SWEEP_FLOPS_PER_POINT_2D = 67
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsis", choices=["gsis", "reference"])
+    ap.add_argument("--config", default="cylinder", choices=["cylinder", "shock", "cylinder_full", "sphere"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "f16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_case(config, small=False):
+    from workloads import shock_1d_case, cylinder_case, sphere_case
+    if config == "shock":
+        return shock_1d_case(n_cells=200 if not small else 40)
+    if config in ("cylinder", "cylinder_full"):
+        adaptive = config == "cylinder"
+        if small:
+            return cylinder_case(n_r=12, n_theta=12, presolve_max_blocks=1, macro_steps=20, adaptive=adaptive)
+        return cylinder_case(adaptive=adaptive)
+    if small:
+        return sphere_case(n_r=6, n_pol=4, n_az=4, presolve_max_blocks=1, macro_steps=10)
+    return sphere_case()
+
+
+def workload_name(config, dtype):
+    return {
+        "cylinder": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, velocity grid 48x48x24, adaptive Kn_ref=0.01",
+        "cylinder_full": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, velocity grid 48x48x24, full kinetic",
+        "shock": "1D normal shock Ma=2, 200 cells on [-25,25] mfp, velocity grid 48x24x24, all kinetic",
+        "sphere": "3D sphere Ma=5 Kn=0.005 Tw=2, O-grid 96x64x64, velocity grid 48^3, adaptive Kn_ref=0.01",
+    }[config] + ", VDF " + dtype
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks / throttle reasons every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(config, dtype):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current sweep source (else null)."""
+    p = os.path.join(ROOT, "profiles", "sweep_%s_%s.json" % (config, dtype))
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    sha = source_sha(["paper_2501_02245_gb300/csrc/sweep.cu", "paper_2501_02245_gb300/csrc/gsis_device.cuh"])
+    if d.get("sweep_src_sha") != sha:
+        return None
+    return d.get("dram_bytes_per_launch_full")
+
+
+def cpu_baseline(config, steps=1):
+    """The oracle as it stands, timed on a bounded sample of the workload:
+    one GSIS iteration on a 12x12 O-grid (same velocity grid, same physics)."""
+    from oracle.gsis import OracleSolver
+    case = make_case(config, small=True)
+    o = OracleSolver(case)
+    o.initialise()
+    t = time.perf_counter()
+    pts = 0
+    for _ in range(steps):
+        o.step()
+        pts += int(o.dvm.sum()) * o.vg.nv
+    dt = time.perf_counter() - t
+    return pts / dt, dt, int(o.dvm.sum()), o.vg.nv, case.mesh.ncell
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle.gsis import OracleSolver
+    case = make_case(args.config, small=True)
+    o = OracleSolver(case)
+    o.initialise()
+    for _ in range(args.warmup):
+        o.step()
+    t = time.perf_counter()
+    pts = 0
+    for _ in range(args.steps):
+        o.step()
+        pts += int(o.dvm.sum()) * o.vg.nv
+    dt = time.perf_counter() - t
+    value = pts / dt
+    sample = ("one GSIS iteration per step of the FP64 oracle on a %d-cell %s sample (%d DVM cells) with the "
+              "workload's velocity grid (%d velocities)" % (case.mesh.ncell, args.config, int(o.dvm.sum()), o.vg.nv))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.config, args.dtype), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def mesh_bytes(case):
+    m = case.mesh
+    b = m.centers.nbytes + m.volumes.nbytes + sum(a.nbytes for a in m.S) + sum(a.nbytes for a in m.xf)
+    return b + case.W0.nbytes
+
+
+def run_gsis(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2501_02245_gb300 import Solver
+    case = make_case(args.config)
+    case.tol = 0.0   # time exactly the requested number of iterations
+    stream = torch.cuda.current_stream()
+    s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
+    rep0 = s.iterate(0)
+    for _ in range(args.warmup):
+        s.iterate(1)
+    clocks = Clocks(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    rep = s.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    pts = rep["n_dvm"] * rep["n_v"] * args.steps
+    t_max = ms
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = pts * ws / (t_max * 1e-3)
+    # dominant kernel: the sweep; its launches are bracketed by CUDA events on the context stream
+    sweep_ms_per_launch = rep["phase_ms"]["sweep"] / max(rep["sweep_launches"], 1)
+    pts_per_launch = rep["n_dvm"] * rep["n_v"]
+    eb = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[args.dtype]
+    traffic = traffic_from_profile(args.config, args.dtype)
+    if args.dtype == "f64":
+        flops = SWEEP_FLOPS_PER_POINT_2D * pts_per_launch
+        achieved = flops / (sweep_ms_per_launch * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "k_sweep<double> (one Gauss-Seidel pass)",
+                "peak_source": "FP64 unit counts x clock: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
+                "algorithmic": "%d FP64 flop per (cell, velocity) per pass" % SWEEP_FLOPS_PER_POINT_2D}
+    else:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+        bytes_alg = 2 * eb * pts_per_launch   # read f once + write f once per pass
+        achieved = bytes_alg / (sweep_ms_per_launch * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_sweep (one Gauss-Seidel pass)", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "algorithmic": "2 x %d bytes per (cell, velocity) per pass" % eb}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": workload_name(args.config, args.dtype), "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "n_dvm": rep["n_dvm"], "n_cells": case.mesh.ncell, "n_v": rep["n_v"],
+                       "vdf_bytes": rep["vdf_bytes"], "l2": "VDF (%.1f GB) larger than L2" % (rep["vdf_bytes"] / 1e9),
+                       "presolve_blocks": rep0["presolve_blocks"], "eps_last": rep["eps"],
+                       "phase_ms_per_step": {k: v / args.steps for k, v in rep["phase_ms"].items() if v > 0}},
+            "roofline": roof, "clocks": ck, "gpu_launches": rep["kernel_launches"]}
+    s.close()
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, case, stream)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, nd, nv, nc = cpu_baseline(args.config)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one GSIS iteration of the FP64 oracle on a %d-cell sample of the workload "
+                                          "(%d DVM cells, %d velocities), %.1f s" % (nc, nd, nv, dt)}
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e(args, case, stream):
+    """The same metric through the public API from host data: context creation,
+    mesh and velocity-grid upload (host -> device), the adaptive start, the
+    timed iterations, and the macroscopic result read back to the host."""
+    import torch
+    from paper_2501_02245_gb300 import Solver
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
+    s.iterate(0)
+    rep = s.iterate(args.steps)
+    W = s.W()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    s.close()
+    pts = rep["n_dvm"] * rep["n_v"] * args.steps
+    return {"value": pts / dt, "unit": UNIT, "h2d_bytes_per_step": mesh_bytes(case) // args.steps,
+            "d2h_bytes_per_step": (W.nbytes + 16 * args.steps) // args.steps,
+            "includes": "set-up upload, NS presolve and region, %d iterations, result read-back" % args.steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gsis(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
