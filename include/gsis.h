@@ -197,6 +197,36 @@ void gsis_free(gsis_ctx* ctx);
 /* Library version string. */
 const char* gsis_version(void);
 
+/* Allocation-free evaluation of conservation-corrected discrete Maxwellians
+ * (the paper has no counterpart; this is a library service).
+ *
+ * For callers that must not allocate device memory: applications whose device
+ * memory is owned entirely by their own arena or pool and that forbid any
+ * other allocation, and latency-critical loops where a cudaMalloc (which may
+ * synchronise the device and take an unbounded time) is not allowed.  The
+ * function allocates nothing: its intermediate data live in one fixed-size
+ * array of device memory (about 3.9 MB) that every GPU loading the library
+ * holds until the process exits.
+ *
+ * W:      device pointer, [n][5] states (rho, ux, uy, uz, T), rho > 0, T > 0.
+ * vgrid:  host pointer, the velocity grid (as for gsis_set_velocity_grid).
+ * f_out:  device pointer, [n][nx*ny*nz] doubles (x fastest): row k receives
+ *         the Maxwellian of W[k] corrected so that its discrete mass,
+ *         momentum and energy equal those of W[k] exactly (the same rows the
+ *         all-kinetic start of gsis_iterate stores as the initial VDF).
+ * cuda_stream: cudaStream_t on which the work is queued (NULL = default).
+ * Limits: n <= 256 and nx + ny + nz <= 384 per call, else GSIS_ERR_ARG;
+ * process more states in several calls.  Other errors: GSIS_ERR_ARG for NULL
+ * pointers or an invalid grid, GSIS_ERR_CUDA when a CUDA call fails.
+ * The first call on a device looks up the address of the device array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls whose device work overlaps (other streams, other
+ * host threads) race on it: order them on one stream.  Asynchronous: returns
+ * after queueing the work. */
+gsis_status gsis_corrected_maxwellian_noalloc(const double* W, int n, const gsis_vgrid_desc* vgrid,
+                                              double* f_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

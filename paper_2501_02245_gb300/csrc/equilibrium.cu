@@ -165,6 +165,14 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
     }
 }
 
+// Context-free launcher of the record builder (caller supplies every buffer).
+void build_records_raw(const RecSpec* d_specs, int nrec, const Records& out, const VGridDev& vg, cudaStream_t st) {
+    if (nrec <= 0) return;
+    const int threads = 128;
+    const int blocks = (nrec * 32 + threads - 1) / threads;
+    k_build_records<<<blocks, threads, 0, st>>>(d_specs, nrec, out, vg);
+}
+
 void launch_build_records(gsis_ctx* c, const Records& out, int nrec, const RecSpec* d_specs) {
     if (nrec <= 0) return;
     const int threads = 128;

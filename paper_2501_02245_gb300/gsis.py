@@ -23,7 +23,8 @@ FIELDS = ["rho", "ux", "uy", "uz", "T", "hot_sxx", "hot_syy", "hot_szz", "hot_sx
 PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual", "presolve"]
 
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
-            "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version"]
+            "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
+            "gsis_corrected_maxwellian_noalloc"]
 
 
 class GsisError(RuntimeError):
@@ -91,6 +92,8 @@ def load():
     lib.gsis_free.argtypes = [vp]
     lib.gsis_free.restype = None
     lib.gsis_version.restype = ctypes.c_char_p
+    lib.gsis_corrected_maxwellian_noalloc.argtypes = [vp, c_int, ctypes.POINTER(VGridDesc), vp, vp]
+    lib.gsis_corrected_maxwellian_noalloc.restype = c_int
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
                  "gsis_get_vdf", "gsis_debug_set_region"):
         getattr(lib, name).restype = c_int

@@ -1,0 +1,81 @@
+"""The allocation-free entry point gsis_corrected_maxwellian_noalloc.
+
+It serves callers that must not allocate device memory (an application that
+owns all device memory through its own pool, or a latency-critical loop where
+cudaMalloc may stall).  Its rows must equal the conservation-corrected
+Maxwellians that the existing path stores as the initial VDF of an
+all-kinetic run (gsis_iterate start, read back with gsis_get_vdf), within the
+FP64 tolerance of the other parity tests, on two calls in a row (different
+inputs, so nothing left in the shared device array from the first call can
+leak into the second).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads import shock_1d_case
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10   # relative to the largest value, as in the VDF parity checks
+
+
+def _existing_rows(case):
+    from paper_2501_02245_gb300 import Solver
+    s = Solver.from_case(case)
+    s.iterate(0)
+    cells, f = s.vdf(case.mesh.ncell)
+    s.close()
+    out = np.zeros_like(f)
+    out[cells] = f
+    return out
+
+
+def _noalloc_rows(case, stream):
+    import torch
+    from paper_2501_02245_gb300 import gsis
+    lib = gsis.load()
+    n = case.mesh.ncell
+    nv = case.vgrid.nv
+    W = torch.tensor(case.W0, dtype=torch.float64, device="cuda")
+    out = torch.full((n, nv), float("nan"), dtype=torch.float64, device="cuda")
+    vg = gsis.VGridDesc()
+    for d in range(3):
+        vg.n[d], vg.lo[d], vg.hi[d] = case.vgrid.n[d], case.vgrid.lo[d], case.vgrid.hi[d]
+    st = lib.gsis_corrected_maxwellian_noalloc(ctypes.c_void_p(W.data_ptr()), n, ctypes.byref(vg),
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    assert st == gsis.GSIS_OK
+    stream.synchronize()
+    return out.cpu().numpy()
+
+
+def test_noalloc_matches_existing_entry_point_two_calls():
+    import torch
+    stream = torch.cuda.current_stream()
+    first = shock_1d_case(Ma=2.0, n_cells=40, half_width=10.0, nv=(20, 10, 9), vmax=8.0)
+    second = shock_1d_case(Ma=3.0, n_cells=32, half_width=8.0, nv=(24, 12, 10), vmax=10.0)
+    for case in (first, second):
+        ref = _existing_rows(case)
+        got = _noalloc_rows(case, stream)
+        assert np.all(np.isfinite(got))
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < TOL, err
+
+
+def test_noalloc_rejects_sizes_beyond_limits():
+    import torch
+    from paper_2501_02245_gb300 import gsis
+    lib = gsis.load()
+    vg = gsis.VGridDesc()
+    for d in range(3):
+        vg.n[d], vg.lo[d], vg.hi[d] = 8, -5.0, 5.0
+    W = torch.ones((300, 5), dtype=torch.float64, device="cuda")
+    out = torch.empty((300, 512), dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p
+    assert lib.gsis_corrected_maxwellian_noalloc(p(W.data_ptr()), 257, ctypes.byref(vg), p(out.data_ptr()),
+                                                 None) == gsis.GSIS_ERR_ARG
+    vg.n[0] = 300   # nx + ny + nz = 316 is fine, 400 is not
+    vg.n[1] = 92
+    assert lib.gsis_corrected_maxwellian_noalloc(p(W.data_ptr()), 1, ctypes.byref(vg), p(out.data_ptr()),
+                                                 None) == gsis.GSIS_ERR_ARG
