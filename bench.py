@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsis", choices=["gsis", "reference"])
-    ap.add_argument("--config", default="cylinder", choices=["cylinder", "shock", "cylinder_full", "sphere"])
+    ap.add_argument("--config", default="cylinder",
+                    choices=["cylinder", "shock", "cylinder_full", "sphere", "cylinder32"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "f16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -53,6 +54,8 @@ def make_case(config, small=False):
     from workloads import shock_1d_case, cylinder_case, sphere_case
     if config == "shock":
         return shock_1d_case(n_cells=200 if not small else 40)
+    if config == "cylinder32":   # reduced mesh, same velocity grid (for profiler captures)
+        return cylinder_case(n_r=32, n_theta=32, presolve_max_blocks=5)
     if config in ("cylinder", "cylinder_full"):
         adaptive = config == "cylinder"
         if small:
@@ -67,6 +70,7 @@ def workload_name(config, dtype):
     return {
         "cylinder": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, velocity grid 48x48x24, adaptive Kn_ref=0.01",
         "cylinder_full": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, velocity grid 48x48x24, full kinetic",
+        "cylinder32": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 32x32, velocity grid 48x48x24, adaptive Kn_ref=0.01",
         "shock": "1D normal shock Ma=2, 200 cells on [-25,25] mfp, velocity grid 48x24x24, all kinetic",
         "sphere": "3D sphere Ma=5 Kn=0.005 Tw=2, O-grid 96x64x64, velocity grid 48^3, adaptive Kn_ref=0.01",
     }[config] + ", VDF " + dtype
