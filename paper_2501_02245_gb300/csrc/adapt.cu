@@ -141,7 +141,7 @@ __global__ void k_dvm_sides(int Nd, const int* __restrict__ dvm_cell, const int*
                             const int* __restrict__ nbr, const int* __restrict__ side_bc,
                             const double* __restrict__ Sout, const double* __restrict__ vol,
                             const int* __restrict__ ghost_id, int* __restrict__ kind, int* __restrict__ ref,
-                            int* __restrict__ nb2, double* __restrict__ SoV) {
+                            int* __restrict__ nb2, double* __restrict__ SoV, float* __restrict__ SoVf) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nd) return;
     const int c = dvm_cell[k];
@@ -168,7 +168,11 @@ __global__ void k_dvm_sides(int Nd, const int* __restrict__ dvm_cell, const int*
         kind[(long long)k * 6 + s] = kd;
         ref[(long long)k * 6 + s] = r;
         nb2[(long long)k * 6 + s] = r2;
-        for (int i = 0; i < 3; ++i) SoV[((long long)k * 6 + s) * 3 + i] = Sout[((long long)c * 6 + s) * 3 + i] / V;
+        for (int i = 0; i < 3; ++i) {
+            const double v = Sout[((long long)c * 6 + s) * 3 + i] / V;
+            SoV[((long long)k * 6 + s) * 3 + i] = v;
+            if (SoVf) SoVf[((long long)k * 6 + s) * 3 + i] = (float)v;
+        }
     }
 }
 
@@ -212,15 +216,21 @@ static bool ensure_dvm_capacity(gsis_ctx* c, long long Nd) {
     long long cap = Nd > 0 ? Nd : 1;
     const int NT = c->vg.NT;
     dev_free(c, c->dvm_cell); dev_free(c, c->dside_kind); dev_free(c, c->dside_ref); dev_free(c, c->dside_nb2);
-    dev_free(c, c->SoV); dev_free(c, c->tau); dev_free(c, c->mom); dev_free(c, c->momh); dev_free(c, c->rho_w);
+    dev_free(c, c->SoV); dev_free(c, c->itau); dev_free(c, c->mom); dev_free(c, c->momh); dev_free(c, c->rho_w);
     dev_free(c, c->recG.scal); dev_free(c, c->recG.tab); dev_free(c, c->recHalf.scal); dev_free(c, c->recHalf.tab);
     dev_free(c, c->recNew.scal); dev_free(c, c->recNew.tab); dev_free(c, c->enter_of);
+    dev_free(c, c->SoVf); dev_free(c, c->itauf); dev_free(c, c->rho_wf);
+    dev_free(c, c->recG.tabf); dev_free(c, c->recG.scalf); dev_free(c, c->recHalf.tabf);
+    dev_free(c, c->recHalf.scalf); dev_free(c, c->recNew.tabf); dev_free(c, c->recNew.scalf);
+    c->SoVf = nullptr; c->itauf = nullptr; c->rho_wf = nullptr;
+    c->recG.tabf = c->recHalf.tabf = c->recNew.tabf = nullptr;
+    c->recG.scalf = c->recHalf.scalf = c->recNew.scalf = nullptr;
     c->dvm_cell = (int*)dev_alloc(c, cap * sizeof(int));
     c->dside_kind = (int*)dev_alloc(c, cap * 6 * sizeof(int));
     c->dside_ref = (int*)dev_alloc(c, cap * 6 * sizeof(int));
     c->dside_nb2 = (int*)dev_alloc(c, cap * 6 * sizeof(int));
     c->SoV = (double*)dev_alloc(c, cap * 18 * sizeof(double));
-    c->tau = (double*)dev_alloc(c, cap * sizeof(double));
+    c->itau = (double*)dev_alloc(c, cap * sizeof(double));
     c->mom = (double*)dev_alloc(c, cap * MOMN * sizeof(double));
     c->momh = (double*)dev_alloc(c, cap * MOMN * sizeof(double));
     c->rho_w = (double*)dev_alloc(c, cap * 6 * sizeof(double));
@@ -231,7 +241,21 @@ static bool ensure_dvm_capacity(gsis_ctx* c, long long Nd) {
     c->recNew.scal = (double*)dev_alloc(c, cap * RS * sizeof(double));
     c->recNew.tab = (double*)dev_alloc(c, cap * NTAB * NT * sizeof(double));
     c->enter_of = (int*)dev_alloc(c, cap * sizeof(int));
-    if (!c->dvm_cell || !c->dside_kind || !c->dside_ref || !c->dside_nb2 || !c->SoV || !c->tau || !c->mom ||
+    if (c->p.vdf_dtype != GSIS_F64) {
+        c->SoVf = (float*)dev_alloc(c, cap * 18 * sizeof(float));
+        c->itauf = (float*)dev_alloc(c, cap * sizeof(float));
+        c->rho_wf = (float*)dev_alloc(c, cap * 6 * sizeof(float));
+        c->recG.tabf = (float*)dev_alloc(c, cap * NTAB * NT * sizeof(float));
+        c->recG.scalf = (float*)dev_alloc(c, cap * RS * sizeof(float));
+        c->recHalf.tabf = (float*)dev_alloc(c, cap * NTAB * NT * sizeof(float));
+        c->recHalf.scalf = (float*)dev_alloc(c, cap * RS * sizeof(float));
+        c->recNew.tabf = (float*)dev_alloc(c, cap * NTAB * NT * sizeof(float));
+        c->recNew.scalf = (float*)dev_alloc(c, cap * RS * sizeof(float));
+        if (!c->SoVf || !c->itauf || !c->rho_wf || !c->recG.tabf || !c->recG.scalf || !c->recHalf.tabf ||
+            !c->recHalf.scalf || !c->recNew.tabf || !c->recNew.scalf)
+            return false;
+    }
+    if (!c->dvm_cell || !c->dside_kind || !c->dside_ref || !c->dside_nb2 || !c->SoV || !c->itau || !c->mom ||
         !c->momh || !c->rho_w || !c->recG.scal || !c->recG.tab || !c->recHalf.scal || !c->recHalf.tab ||
         !c->recNew.scal || !c->recNew.tab || !c->enter_of)
         return false;
@@ -279,7 +303,7 @@ int build_region(gsis_ctx* c) {
         const int kb = (int)((Nd_new + 127) / 128);
         k_dvm_sides<<<kb, 128, 0, c->stream>>>((int)Nd_new, c->dvm_cell, c->cell2dvm, c->m.nbr, c->m.side_bc,
                                                c->m.Sout, c->m.vol, c->ghost_id, c->dside_kind, c->dside_ref,
-                                               c->dside_nb2, c->SoV);
+                                               c->dside_nb2, c->SoV, c->SoVf);
         k_enter_mark<<<kb, 128, 0, c->stream>>>((int)Nd_new, c->dvm_cell, c->old_cell2dvm, c->enter_list,
                                                 c->enter_of, c->d_count + 1);
         c->launches += 2;

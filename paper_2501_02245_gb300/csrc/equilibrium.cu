@@ -154,6 +154,7 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
         scal[RS_UY] = s.u[1];
         scal[RS_UZ] = s.u[2];
         for (int k = 0; k < 5; ++k) scal[RS_ALPHA0 + k] = alpha[k];
+        for (int q = RS_ALPHA0 + 5; q < RS; ++q) scal[q] = 0.0;
     }
     for (int k = 0; k < 7; ++k) coef[k] = __shfl_sync(0xffffffffu, coef[k], 0);
     for (int idx = lane; idx < NT; idx += 32) {
@@ -162,6 +163,14 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
         tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * (c * c);
         tab[4 * NT + idx] = s.r[d] * c;
         if (d == 0) tab[idx] *= A;
+        if (out.tabf) {
+            float* tf = out.tabf + (long long)r * NTAB * NT;
+            for (int t = 0; t < NTAB; ++t) tf[t * NT + idx] = (float)tab[t * NT + idx];
+        }
+    }
+    if (out.scalf) {
+        __syncwarp();
+        if (lane < RS) out.scalf[(long long)r * RS + lane] = (float)scal[lane];
     }
 }
 
@@ -203,7 +212,7 @@ __device__ static void spec_maxwellian(RecSpec& s, double rho, const double* u, 
 __global__ void k_cell_eq(int Nd, const int* __restrict__ dvm_cell, const double* __restrict__ W,
                           const double* __restrict__ mom, const int* __restrict__ side_bc,
                           const double* __restrict__ wall_den, double mu0, double omega,
-                          RecSpec* specs, double* tau, double* rho_w) {
+                          RecSpec* specs, double* itau, double* rho_w, float* itauf, float* rho_wf) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nd) return;
     const int c = dvm_cell[k];
@@ -217,11 +226,13 @@ __global__ void k_cell_eq(int Nd, const int* __restrict__ dvm_cell, const double
     spec_maxwellian(s, rho, u, T, 1);
     for (int d = 0; d < 3; ++d) { s.p[d] = -5.0 * T * sc * q[d]; s.r[d] = sc * q[d]; }
     specs[k] = s;
-    tau[k] = viscosity(T, mu0, omega) / p;
+    itau[k] = p / viscosity(T, mu0, omega);   // 1/tau, tau = mu(T)/p
+    if (itauf) itauf[k] = (float)itau[k];
     for (int sd = 0; sd < 6; ++sd) {
         double v = 0.0;
         if (side_bc[c * 6 + sd] == GSIS_BC_WALL) v = m[13 + sd] / wall_den[c * 6 + sd];
         rho_w[(long long)k * 6 + sd] = v;
+        if (rho_wf) rho_wf[(long long)k * 6 + sd] = (float)v;
     }
 }
 
@@ -229,7 +240,8 @@ void launch_cell_eq(gsis_ctx* c) {
     const int Nd = (int)c->Nd;
     if (Nd == 0) return;
     k_cell_eq<<<(Nd + 127) / 128, 128, 0, c->stream>>>(Nd, c->dvm_cell, c->W, c->mom, c->m.side_bc, c->wall_den,
-                                                        c->mu0, c->p.omega, c->specs, c->tau, c->rho_w);
+                                                        c->mu0, c->p.omega, c->specs, c->itau, c->rho_w, c->itauf,
+                                                        c->rho_wf);
     c->launches++;
     launch_build_records(c, c->recG, Nd, c->specs);
 }

@@ -152,6 +152,15 @@ gsis_status start(gsis_ctx* c) {
                                     cudaMemcpyHostToDevice, c->stream), "upload W0"))
         return GSIS_ERR_CUDA;
     cudaMemsetAsync(c->hot, 0, (size_t)N * HOTN * sizeof(double), c->stream);
+    if (c->p.vdf_dtype != GSIS_F64) {   // FP32 copies of the boundary and ghost records for the FP32 sweep
+        const size_t NT = c->vg.NT;
+        c->recBC.tabf = (float*)dev_alloc(c, 6 * NTAB * NT * sizeof(float));
+        c->recBC.scalf = (float*)dev_alloc(c, 6 * RS * sizeof(float));
+        c->recGhost.tabf = (float*)dev_alloc(c, (size_t)N * NTAB * NT * sizeof(float));
+        c->recGhost.scalf = (float*)dev_alloc(c, (size_t)N * RS * sizeof(float));
+        if (!c->recBC.tabf || !c->recBC.scalf || !c->recGhost.tabf || !c->recGhost.scalf)
+            return set_err(c, GSIS_ERR_OOM, "device allocation failed (FP32 record copies)");
+    }
     launch_bc_records(c);
     launch_wall_den(c);
     phase_begin(c, GSIS_PH_PRESOLVE);
@@ -369,6 +378,19 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
                         side_bc[(size_t)cc * 6 + s] = nb >= 0 ? -1 : md->bc_type[s];
                     }
             }
+    // face-normal components that are nonzero on some flux-carrying face
+    {
+        bool any_y = false, any_z = false;
+        for (int cc = 0; cc < N; ++cc)
+            for (int s = 0; s < 6; ++s) {
+                const bool active = nbr[(size_t)cc * 6 + s] >= 0 || side_bc[(size_t)cc * 6 + s] == GSIS_BC_FARFIELD ||
+                                    side_bc[(size_t)cc * 6 + s] == GSIS_BC_WALL;
+                if (!active) continue;
+                any_y = any_y || Sout[((size_t)cc * 6 + s) * 3 + 1] != 0.0;
+                any_z = any_z || Sout[((size_t)cc * 6 + s) * 3 + 2] != 0.0;
+            }
+        c->normal_components = any_z ? 3 : (any_y ? 2 : 1);
+    }
     // least-squares weights over the first dim coordinates
     const int dim = md->dim;
     for (int cc = 0; cc < N; ++cc) {

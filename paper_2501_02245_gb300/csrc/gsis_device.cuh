@@ -15,19 +15,39 @@ template <typename S> struct Store;
 template <> struct Store<double> {
     static __device__ __forceinline__ double ld(const double* p) { return *p; }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+    static __device__ __forceinline__ float ldf(const double* p) { return (float)*p; }
+    static __device__ __forceinline__ void stf(double* p, float v) { *p = (double)v; }
 };
 template <> struct Store<float> {
     static __device__ __forceinline__ double ld(const float* p) { return (double)*p; }
     static __device__ __forceinline__ void st(float* p, double v) { *p = (float)v; }
+    static __device__ __forceinline__ float ldf(const float* p) { return *p; }
+    static __device__ __forceinline__ void stf(float* p, float v) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ double ld(const __nv_bfloat16* p) { return (double)__bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+    static __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 template <> struct Store<__half> {
     static __device__ __forceinline__ double ld(const __half* p) { return (double)__half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, double v) { *p = __float2half_rn((float)v); }
+    static __device__ __forceinline__ float ldf(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void stf(__half* p, float v) { *p = __float2half_rn(v); }
 };
+
+// load / store in the arithmetic type T (double or float)
+template <typename T, typename S> __device__ __forceinline__ T ldT(const S* p);
+template <> __device__ __forceinline__ double ldT<double, double>(const double* p) { return *p; }
+template <typename T, typename S> __device__ __forceinline__ void stT(S* p, T v);
+template <> __device__ __forceinline__ void stT<double, double>(double* p, double v) { *p = v; }
+template <> __device__ __forceinline__ float ldT<float, float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ldT<float, __nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float ldT<float, __half>(const __half* p) { return __half2float(*p); }
+template <> __device__ __forceinline__ void stT<float, float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stT<float, __nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ void stT<float, __half>(__half* p, float v) { *p = __float2half_rn(v); }
 
 // ---------------------------------------------------------------- small math
 __device__ __forceinline__ double minmod(double a, double b) {
@@ -70,6 +90,38 @@ __device__ __forceinline__ const double* rec_tab(const Records& r, long long i, 
     return r.tab + i * (long long)(NTAB * NT);
 }
 
+// Record access in the arithmetic type T (the FP32 copies for T = float).
+template <typename T> struct RecT;
+template <> struct RecT<double> {
+    static __device__ __forceinline__ const double* scal(const Records& r, long long i) { return r.scal + i * RS; }
+    static __device__ __forceinline__ const double* tab(const Records& r, long long i, int NT) {
+        return r.tab + i * (long long)(NTAB * NT);
+    }
+};
+template <> struct RecT<float> {
+    static __device__ __forceinline__ const float* scal(const Records& r, long long i) { return r.scalf + i * RS; }
+    static __device__ __forceinline__ const float* tab(const Records& r, long long i, int NT) {
+        return r.tabf + i * (long long)(NTAB * NT);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T eval_recT(const T* __restrict__ scal, const T* __restrict__ tab, int NT, int nx, int ny,
+                                       int ix, int iy, int iz) {
+    const int jy = nx + iy, jz = nx + ny + iz;
+    T e = tab[ix] * tab[jy] * tab[jz];
+    const T* B = tab + NT;
+    const T* C2 = tab + 3 * NT;
+    const T* Rr = tab + 4 * NT;
+    T poly = scal[RS_P0] + (B[ix] + B[jy] + B[jz]) + (Rr[ix] + Rr[jy] + Rr[jz]) * (C2[ix] + C2[jy] + C2[jz]);
+    if (scal[RS_OFFD] != T(0)) {
+        const T* C = tab + 2 * NT;
+        T cx = C[ix], cy = C[jy], cz = C[jz];
+        poly += T(2) * (scal[RS_P2XY] * cx * cy + scal[RS_P2XZ] * cx * cz + scal[RS_P2YZ] * cy * cz);
+    }
+    return e * poly;
+}
+
 // ---------------------------------------------------------------- deterministic reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -90,6 +142,7 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* smem /* [32*K]
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             double s = 0.0;
             for (int w = 0; w < nw; ++w) s += smem[w * K + k];

@@ -43,6 +43,8 @@ struct VGridDev {
 struct Records {                 // R records
     double* scal;                // [R][RS]
     double* tab;                 // [R][NTAB][NT]
+    float* tabf = nullptr;       // FP32 copy of tab (reduced-precision VDF storage only)
+    float* scalf = nullptr;      // FP32 copy of scal
 };
 
 // Base polynomial of a record in c = xi - u:
@@ -78,6 +80,7 @@ struct gsis_ctx {
     double mu0 = 0.0;
 
     gsis::Mesh m;
+    int normal_components = 3;     // 1: only x, 2: x and y, 3: x, y, z components of face normals are nonzero
     int* d_bc_type = nullptr;      // [6]
     double* d_bc_state = nullptr;  // [6][5]
     std::vector<double> host_W0;
@@ -104,8 +107,9 @@ struct gsis_ctx {
     int *dvm_cell = nullptr, *cell2dvm = nullptr, *hp_off = nullptr, *hp_cnt = nullptr;
     int *dside_kind = nullptr, *dside_ref = nullptr, *dside_nb2 = nullptr;
     double* SoV = nullptr;
+    float *SoVf = nullptr, *itauf = nullptr, *rho_wf = nullptr;   // FP32 mirrors for the FP32 sweep
     void* f = nullptr;
-    double *tau = nullptr, *mom = nullptr, *rho_w = nullptr, *wall_den = nullptr;
+    double *itau = nullptr, *mom = nullptr, *rho_w = nullptr, *wall_den = nullptr;
     gsis::Records recG{}, recHalf{}, recNew{}, recGhost{}, recBC{};
     int* ghost_id = nullptr;       // [N] ghost record index or -1
     int* ghost_cell = nullptr;     // [N] cell of each ghost record

@@ -2,90 +2,144 @@
 // (Eq. full_constitutive) and the VDF correction of Eq. updatef.
 //
 // One block per DVM cell reduces over all discrete velocities in a fixed
-// order (per-thread strided partial sums, then a warp-shuffle tree and a
-// block tree), so results are bitwise reproducible.  Moments are taken about
-// a reference velocity u_ref (the cell's current macroscopic velocity) to
+// order, so results are bitwise reproducible.  Moments are taken about a
+// reference velocity u_ref (the cell's current macroscopic velocity) to
 // avoid cancellation:
 //   m[0] = sum w f, m[1..3] = sum w c f, m[4..9] = sum w c_i c_j f
 //   (xx, yy, zz, xy, xz, yz), m[10..12] = sum w c^2 c f,  c = xi - u_ref,
 //   m[13+s] = sum_{xi.S_s > 0} w (xi.S_s) f for wall sides s (outgoing mass
 //   flux through the wall face, for the diffuse-wall density).
+//
+// Row factoring: a thread owns whole x-rows (fixed iy, iz) of the cell's VDF.
+// Per point it accumulates only sum f c_x^k, k = 0..3 (c_x^k from shared
+// memory), and folds the row sums into the 13 moments with the row constants
+// c_y, c_z once per row.  In the correction pass the two corrected
+// Maxwellians are evaluated with their y/z factors hoisted out of the row.
+//
+// Arithmetic type T: FP64 for an FP64 VDF; for FP32/BF16/FP16 storage the
+// per-row work (row sums over at most nx <= 64 nodes, the correction) is
+// FP32 and every sum across rows and cells is FP64.  The FP32 row sum of
+// n terms carries a relative rounding error below n * 2^-24 (< 4e-6 for
+// n = 64) of the sum of |terms|, far under the storage rounding of BF16/FP16
+// (2^-9 / 2^-12 per value) and comparable to FP32 storage rounding.
 #include "gsis_device.cuh"
 
 namespace gsis {
 
-template <typename S, bool CORRECT>
+template <typename S, typename T, bool CORRECT>
 __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__ dvm_cell,
                                                  const double* __restrict__ Wref, const int* __restrict__ side_bc,
                                                  const double* __restrict__ Sout, S* __restrict__ f, Records recNew,
                                                  Records recHalf, VGridDev vg, double* __restrict__ mom) {
     const int k = blockIdx.x;
     if (k >= Nd) return;
-    __shared__ double sm[32 * MOMN];
+    extern __shared__ double sh_raw[];
+    T* sh = reinterpret_cast<T*>(sh_raw);
+    __shared__ double red[32 * MOMN];
+    const int nx = vg.nx, ny = vg.ny, nz = vg.nz, NT = vg.NT;
     const int c = dvm_cell[k];
     const double ux = Wref[c * 5 + 1], uy = Wref[c * 5 + 2], uz = Wref[c * 5 + 3];
-    const int NT = vg.NT, nx = vg.nx, ny = vg.ny;
-    int wall_s[6];
-    int nwall = 0;
+    T* scx = sh;                 // c_x, c_x^2, c_x^3
+    T* scx2 = sh + nx;
+    T* scx3 = sh + 2 * nx;
+    T* tN = sh + 3 * nx;         // x-tables E, B, C2, R of M~(W^{n+1})
+    T* tH = sh + 7 * nx;         // x-tables of M~(W^{n+1/2})
+    const T* TN = CORRECT ? RecT<T>::tab(recNew, k, NT) : nullptr;
+    const T* TH = CORRECT ? RecT<T>::tab(recHalf, k, NT) : nullptr;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double cx = vg.xi[i] - ux;
+        scx[i] = (T)cx;
+        scx2[i] = (T)(cx * cx);
+        scx3[i] = (T)(cx * cx * cx);
+        if (CORRECT) {
+            tN[i] = TN[i]; tN[nx + i] = TN[NT + i]; tN[2 * nx + i] = TN[3 * NT + i]; tN[3 * nx + i] = TN[4 * NT + i];
+            tH[i] = TH[i]; tH[nx + i] = TH[NT + i]; tH[2 * nx + i] = TH[3 * NT + i]; tH[3 * nx + i] = TH[4 * NT + i];
+        }
+    }
+    __syncthreads();
+    T p0N = T(0), p0H = T(0);
+    if (CORRECT) {
+        p0N = RecT<T>::scal(recNew, k)[RS_P0];
+        p0H = RecT<T>::scal(recHalf, k)[RS_P0];
+    }
+    int wall_mask = 0;
     for (int s = 0; s < 6; ++s)
-        if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_s[nwall++] = s;
+        if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
     double acc[MOMN];
 #pragma unroll
     for (int q = 0; q < MOMN; ++q) acc[q] = 0.0;
     S* fk = f + (long long)k * vg.Nv;
-    const double* sN = CORRECT ? rec_scal(recNew, k) : nullptr;
-    const double* tN = CORRECT ? rec_tab(recNew, k, NT) : nullptr;
-    const double* sH = CORRECT ? rec_scal(recHalf, k) : nullptr;
-    const double* tH = CORRECT ? rec_tab(recHalf, k, NT) : nullptr;
-    for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
-        int ix, iy, iz;
-        vsplit(v, nx, ny, ix, iy, iz);
-        double fv = Store<S>::ld(fk + v);
+    const int rows = ny * nz;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int iy = r % ny, iz = r / ny;
+        const int jy = nx + iy, jz = nx + ny + iz;
+        const double xy = vg.xi[jy], xz = vg.xi[jz];
+        const double cy = xy - uy, cz = xz - uz;
+        T eN = T(0), bN = T(0), c2N = T(0), rN = T(0), eH = T(0), bH = T(0), c2H = T(0), rH = T(0);
         if (CORRECT) {
-            fv = fv + (eval_rec(sN, tN, NT, nx, ny, ix, iy, iz) - eval_rec(sH, tH, NT, nx, ny, ix, iy, iz));
-            Store<S>::st(fk + v, fv);
-            fv = Store<S>::ld(fk + v);   // moments of the stored value
+            eN = TN[jy] * TN[jz]; bN = TN[NT + jy] + TN[NT + jz];
+            c2N = TN[3 * NT + jy] + TN[3 * NT + jz]; rN = TN[4 * NT + jy] + TN[4 * NT + jz];
+            eH = TH[jy] * TH[jz]; bH = TH[NT + jy] + TH[NT + jz];
+            c2H = TH[3 * NT + jy] + TH[3 * NT + jz]; rH = TH[4 * NT + jy] + TH[4 * NT + jz];
         }
-        const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
-        const double cx = x0 - ux, cy = x1 - uy, cz = x2 - uz;
-        const double c2 = cx * cx + cy * cy + cz * cz;
-        acc[0] += fv;
-        acc[1] += fv * cx;
-        acc[2] += fv * cy;
-        acc[3] += fv * cz;
-        acc[4] += fv * cx * cx;
-        acc[5] += fv * cy * cy;
-        acc[6] += fv * cz * cz;
-        acc[7] += fv * cx * cy;
-        acc[8] += fv * cx * cz;
-        acc[9] += fv * cy * cz;
-        acc[10] += fv * c2 * cx;
-        acc[11] += fv * c2 * cy;
-        acc[12] += fv * c2 * cz;
-        for (int q = 0; q < nwall; ++q) {
-            const double* Sw = Sout + ((long long)c * 6 + wall_s[q]) * 3;
-            const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
-            if (xn > 0.0) acc[13 + q] += xn * fv;
+        S* row = fk + (long long)r * nx;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        for (int ix = 0; ix < nx; ++ix) {
+            T fv = ldT<T, S>(row + ix);
+            if (CORRECT) {
+                const T vN = (tN[ix] * eN) * (p0N + (tN[nx + ix] + bN) + (tN[3 * nx + ix] + rN) * (tN[2 * nx + ix] + c2N));
+                const T vH = (tH[ix] * eH) * (p0H + (tH[nx + ix] + bH) + (tH[3 * nx + ix] + rH) * (tH[2 * nx + ix] + c2H));
+                stT<T, S>(row + ix, fv + (vN - vH));
+                fv = ldT<T, S>(row + ix);   // moments of the stored value
+            }
+            s0 += fv;
+            s1 += fv * scx[ix];
+            s2 += fv * scx2[ix];
+            s3 += fv * scx3[ix];
+            if (wall_mask) {
+#pragma unroll
+                for (int s = 0; s < 6; ++s) {
+                    if ((wall_mask >> s) & 1) {
+                        const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+                        const double xn = vg.xi[ix] * Sw[0] + xy * Sw[1] + xz * Sw[2];
+                        if (xn > 0.0) acc[13 + s] += xn * (double)fv;
+                    }
+                }
+            }
         }
+        const double d0 = s0, d1 = s1, d2 = s2, d3 = s3;
+        const double t = cy * cy + cz * cz;
+        acc[0] += d0;
+        acc[1] += d1;
+        acc[2] += d0 * cy;
+        acc[3] += d0 * cz;
+        acc[4] += d2;
+        acc[5] += d0 * (cy * cy);
+        acc[6] += d0 * (cz * cz);
+        acc[7] += d1 * cy;
+        acc[8] += d1 * cz;
+        acc[9] += d0 * (cy * cz);
+        acc[10] += d3 + d1 * t;
+        acc[11] += cy * (d2 + d0 * t);
+        acc[12] += cz * (d2 + d0 * t);
     }
-    block_sum<MOMN>(acc, sm);
+    block_sum<MOMN>(acc, red);
     if (threadIdx.x == 0) {
         double* m = mom + (long long)k * MOMN;
-        for (int q = 0; q < 13; ++q) m[q] = acc[q] * vg.w;
-        for (int s = 0; s < 6; ++s) m[13 + s] = 0.0;
-        for (int q = 0; q < nwall; ++q) m[13 + wall_s[q]] = acc[13 + q] * vg.w;
+        for (int q = 0; q < MOMN; ++q) m[q] = acc[q] * vg.w;
     }
 }
 
-template <typename S>
+template <typename S, typename T>
 static void moments_t(gsis_ctx* c, const double* Wref, bool correct, double* out) {
     const int Nd = (int)c->Nd;
+    const size_t smem = (size_t)(correct ? 11 : 3) * c->vg.nx * sizeof(T);
     if (correct)
-        k_moments<S, true><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (S*)c->f,
-                                                       c->recNew, c->recHalf, c->vg, out);
+        k_moments<S, T, true><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout,
+                                                             (S*)c->f, c->recNew, c->recHalf, c->vg, out);
     else
-        k_moments<S, false><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (S*)c->f,
-                                                        c->recNew, c->recHalf, c->vg, out);
+        k_moments<S, T, false><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout,
+                                                              (S*)c->f, c->recNew, c->recHalf, c->vg, out);
     c->launches++;
 }
 
@@ -95,10 +149,10 @@ static void moments_t(gsis_ctx* c, const double* Wref, bool correct, double* out
 void launch_moments(gsis_ctx* c, const double* Wref, int correct_pass, double* out) {
     if (c->Nd == 0) return;
     switch (c->p.vdf_dtype) {
-        case GSIS_F64: moments_t<double>(c, Wref, correct_pass != 0, out); break;
-        case GSIS_F32: moments_t<float>(c, Wref, correct_pass != 0, out); break;
-        case GSIS_BF16: moments_t<__nv_bfloat16>(c, Wref, correct_pass != 0, out); break;
-        default: moments_t<__half>(c, Wref, correct_pass != 0, out); break;
+        case GSIS_F64: moments_t<double, double>(c, Wref, correct_pass != 0, out); break;
+        case GSIS_F32: moments_t<float, float>(c, Wref, correct_pass != 0, out); break;
+        case GSIS_BF16: moments_t<__nv_bfloat16, float>(c, Wref, correct_pass != 0, out); break;
+        default: moments_t<__half, float>(c, Wref, correct_pass != 0, out); break;
     }
 }
 
