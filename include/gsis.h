@@ -83,7 +83,7 @@ typedef struct {
 typedef struct {
     double Kn;            /* free-stream Knudsen number; mu(T0) from the Kn definition of Sec. 2 */
     double omega;         /* viscosity index: mu = mu(T0) (T/T0)^omega (Sec. 2)                  */
-    int    adaptive;      /* 1: Sec. 3.4 Steps 1-3 (NS presolve, Kn_Gll region); 0: all cells DVM */
+    int    adaptive;      /* 1: Sec. 3.4 Steps 2-3 (Kn_Gll region, re-identification); 0: all cells DVM */
     double Kn_ref;        /* reference Knudsen number of the DVM-region rule (Sec. 3.2)           */
     int    adapt_every;   /* the region is re-identified once, after this many GSIS iterations    */
     int    wall_layers;   /* cell layers next to a wall that are always DVM                        */
@@ -93,7 +93,9 @@ typedef struct {
     int    k_sub;         /* Jacobi sweeps of the data-parallel relaxation per pseudo-step         */
     double dt;            /* time step of Eq. macro; 0 = steady form (dt -> infinity)              */
     double tol;           /* convergence tolerance on epsilon (Sec. 4), also for the NS presolve   */
-    int    presolve_max_blocks; /* NS presolve: at most this many blocks of macro_steps steps      */
+    int    presolve_max_blocks; /* Sec. 3.4 Step 1 NS presolve (HoT = 0): at most this many blocks of
+                                   macro_steps steps, stopping when epsilon between blocks < tol;
+                                   0 = start from W0 directly                                     */
     unsigned long long spin_limit; /* iteration limit of any bounded device wait (0 = default)    */
 } gsis_params;
 

@@ -18,8 +18,9 @@ import numpy as np
 
 from . import model as M
 from .mesh import Topology, BC_NONE, BC_FARFIELD, BC_WALL
-from .kinetic import KineticInputs, sweep, wall_density
-from .macro import (MacroGeometry, primitives, cell_gradients, nsf, macro_solve, boundary_values, lsq_grad)
+from .kinetic import KineticInputs, sweep, wall_density, wall_kinetic_flux
+from .macro import (MacroGeometry, primitives, cell_gradients, nsf, macro_solve, boundary_values, lsq_grad,
+                    wall_nsf_flux)
 
 
 def residual_eps(Wn, Wp, vol):
@@ -153,9 +154,11 @@ class OracleSolver:
         self.W = U_to_prim(U)
 
     def initialise(self):
+        # Sec. 3.4 Step 1: the initial field from the macroscopic equations (also
+        # used to start an all-kinetic run when presolve blocks are requested)
+        if self.case.presolve_max_blocks > 0:
+            self.presolve()
         if self.case.adaptive:
-            if self.case.presolve_max_blocks > 0:
-                self.presolve()
             self.set_region(self.region(self.W), self.W)
         else:
             self.dvm[:] = True
@@ -201,6 +204,26 @@ class OracleSolver:
                     rho_w[(c, sd.bc_side)] = wall_density(self.f[c], sd.S_out, mw[sd.bc_side], vg)
         return KineticInputs(gt, tau, ghost, ff, mw, rho_w)
 
+    def wall_correction(self, W_half, mw):
+        """Per wall face (order of the wall faces of the macro geometry): for a
+        DVM cell, the kinetic wall flux of f^{n+1/2} minus the NSF wall flux at
+        W^{n+1/2}; zero for NS cells.  Added to the NSF wall flux inside the
+        synthetic solve."""
+        geo = self.geo
+        idx = np.nonzero(geo.bT == BC_WALL)[0]
+        corr = np.zeros((len(idx), 5))
+        if len(idx) == 0:
+            return corr
+        gu, gT = self.gradients(W_half)
+        F_nsf = wall_nsf_flux(geo, self.bc_state, W_half[:, 0], W_half[:, 1:4], W_half[:, 4], gu, gT,
+                              self.mu0, self.omega)
+        for r, f_i in enumerate(idx):
+            c = geo.bC[f_i]
+            if self.dvm[c]:
+                F_kin = wall_kinetic_flux(self.f[c], geo.bS[f_i], mw[geo.bSide[f_i]], self.vg)
+                corr[r] = F_kin - F_nsf[r]
+        return corr
+
     def step(self):
         """One GSIS iteration; returns epsilon."""
         case = self.case
@@ -221,9 +244,11 @@ class OracleSolver:
         self.hot_sigma = np.where(self.dvm[:, None, None], sig_k - sig_n, 0.0)
         self.hot_q = np.where(self.dvm[:, None], q_k - q_n, 0.0)
         self.W_half = W_half
+        bcorr = np.zeros((len(self.geo.bC), 5))
+        bcorr[self.geo.bT == BC_WALL] = self.wall_correction(W_half, inp.mw)
         U = macro_solve(self.geo, self.bc_state, prim_to_U(W_half), self.hot_sigma, self.hot_q,
                         self.mu0, self.omega, case.cfl, case.k_sub, case.macro_steps,
-                        case.dt, prim_to_U(self.W))
+                        case.dt, prim_to_U(self.W), bcorr)
         W_new = U_to_prim(U)
         for c in range(self.N):
             if self.dvm[c]:

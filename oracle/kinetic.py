@@ -55,6 +55,20 @@ def wall_density(f_cell, S_out, Mw, vg):
     return num / den
 
 
+def wall_kinetic_flux(f_cell, S_out, Mw, vg):
+    """Flux of (mass, momentum, energy) through a diffuse-wall face carried by
+    the face distribution: the cell's f for outgoing velocities (xi . S > 0)
+    and rho_w M_w, with rho_w from zero net mass flux of that same f, for the
+    incoming ones: sum_v w (xi . S) (1, xi, |xi|^2/2) f_face."""
+    xi = vg.xi
+    xn = xi @ S_out
+    rho_w = wall_density(f_cell, S_out, Mw, vg)
+    face = np.where(xn > 0, f_cell, rho_w * Mw)
+    g = vg.w * xn * face
+    return np.array([np.sum(g), g @ xi[:, 0], g @ xi[:, 1], g @ xi[:, 2],
+                     np.sum(g * 0.5 * np.sum(xi * xi, axis=1))])
+
+
 def slope(topo, f, dvm, c, d):
     cm = topo.step(c, d, -1)
     cp = topo.step(c, d, +1)
@@ -103,3 +117,4 @@ def sweep(topo, vg, f, dvm, inp):
     for c in reversed(cells):
         update_cell(topo, vg, f, dvm, inp, c)
     return f
+

@@ -15,8 +15,11 @@ another paper.  The reading taken, for the monatomic gas (no source):
   of the two cells' high-order terms (HoT, zero in NS cells);
 * boundaries: far field = HLLC against the boundary state plus the cell's
   HoT (no NSF part: the far field is taken as gradient-free);
-  wall = cell pressure, no mass flux, NSF at u = 0, T = T_w from a one-sided
-  gradient, plus the cell's HoT;
+  wall of an NS cell (and in the NS presolve) = cell pressure, no mass flux,
+  NSF at u = 0, T = T_w from a one-sided gradient; wall of a DVM cell = the
+  kinetic wall flux of f^{n+1/2} plus the change of that NSF wall flux since
+  W^{n+1/2}, so that at convergence the synthetic equations see exactly the
+  wall flux of the kinetic solution (slip and temperature jump included);
 * pseudo-time relaxation: data-parallel line-free relaxation (DP-LUR of
   Wright, Candler & Bose, AIAA J. 36 (1998)) with a scalar diagonal
   (1/CFL + 1/2) sum_F lambda_F |S_F|, lambda_F = |u.n| + a + 5 mu/(rho d),
@@ -187,9 +190,37 @@ def euler_flux_dot(U, S):
                            ((U[:, 4] + p) * uS)[:, None]], axis=1)
 
 
-def residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega):
+def wall_nsf_flux(geo, bc_state, rho, u, T, gu, gT, mu0, omega):
+    """NSF flux through every wall face (in the order of the wall faces in
+    geo): no mass flux, cell pressure, NSF stress and heat flux at u = 0,
+    T = T_w from the cell gradient corrected along the cell-to-face line."""
+    wl = geo.bT == BC_WALL
+    idx = np.nonzero(wl)[0]
+    c = geo.bC[idx]
+    Sb = geo.bS[idx]
+    Tw = bc_state[geo.bSide[idx], 4]
+    e_b = geo.be[idx]
+    db = geo.bdist[idx]
+
+    def wall_grad(gc, phic, phiw):
+        corr = (phiw - phic) / db - np.sum(gc * e_b, axis=1)
+        return gc + corr[:, None] * e_b
+
+    guw = np.stack([wall_grad(gu[c, :, j], u[c, j], 0.0) for j in range(3)], axis=2)
+    gTw = wall_grad(gT[c], T[c], Tw)
+    sig_w, q_w = nsf(viscosity(Tw, mu0, omega), guw, gTw)
+    SigS = np.einsum("fij,fj->fi", sig_w, Sb)
+    F = np.zeros((len(idx), 5))
+    F[:, 1:4] = (rho[c] * T[c])[:, None] * Sb + SigS
+    F[:, 4] = np.sum(q_w * Sb, axis=1)
+    return F
+
+
+def residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, bface_corr=None):
     """R_c = -sum over faces of the outward flux (Eq. macro, steady part);
-    returns R[N, 5] and the face spectral radii needed by the relaxation."""
+    returns R[N, 5] and the face spectral radii needed by the relaxation.
+    bface_corr [boundary faces, 5] is a frozen correction added to the
+    boundary face fluxes (used at the walls of DVM cells)."""
     N = geo.N
     rho, u, T = primitives(U)
     p = rho * T
@@ -263,24 +294,9 @@ def residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega):
         Fb[idx, 4] += np.sum(SigS * ufb, axis=1) + np.sum(hot_q[c] * Sb, axis=1)
     if np.any(wl):
         idx = np.nonzero(wl)[0]
-        c = C[idx]
-        Sb = geo.bS[idx]
-        Tw = st[idx, 4]
-        e_b = geo.be[idx]
-        db = geo.bdist[idx]
-
-        def wall_grad(gc, phic, phiw):
-            corr = (phiw - phic) / db - np.sum(gc * e_b, axis=1)
-            return gc + corr[:, None] * e_b
-
-        guw = np.stack([wall_grad(gu[c, :, j], u[c, j], 0.0) for j in range(3)], axis=2)
-        gTw = wall_grad(gT[c], T[c], Tw)
-        sig_w, q_w = nsf(viscosity(Tw, mu0, omega), guw, gTw)
-        Sig = sig_w + hot_sigma[c]
-        Q = q_w + hot_q[c]
-        SigS = np.einsum("fij,fj->fi", Sig, Sb)
-        Fb[idx, 1:4] = p[c][:, None] * Sb + SigS
-        Fb[idx, 4] = np.sum(Q * Sb, axis=1)
+        Fb[idx] = wall_nsf_flux(geo, bc_state, rho, u, T, gu, gT, mu0, omega)
+    if bface_corr is not None:
+        Fb = Fb + bface_corr
     np.add.at(R, C, -Fb)
     use = ff | wl
     lam_b = (np.abs(np.sum(u[C] * geo.bn, axis=1)) + a[C] + 5.0 * mu_c[C] / (rho[C] * 2.0 * geo.bdist))
@@ -288,11 +304,11 @@ def residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega):
     return R, lamS, lam_sum
 
 
-def relax_step(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, cfl, k_sub, dt=0.0, Un=None):
+def relax_step(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, cfl, k_sub, dt=0.0, Un=None, bface_corr=None):
     """One DP-LUR pseudo-time step; returns the new U.  With dt > 0 the
     residual carries the physical-time term of Eq. macro, -V (U - U^n)/dt,
     and the diagonal gains V/dt (dual time stepping)."""
-    R, lamS, lam_sum = residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega)
+    R, lamS, lam_sum = residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, bface_corr)
     D = (1.0 / cfl + 0.5) * lam_sum
     if dt > 0.0:
         vol = geo.topo.vol
@@ -311,11 +327,15 @@ def relax_step(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, cfl, k_sub, dt=0.
     return U + dU
 
 
-def macro_solve(geo, bc_state, U0, hot_sigma, hot_q, mu0, omega, cfl, k_sub, steps, dt=0.0, Un=None):
+def macro_solve(geo, bc_state, U0, hot_sigma, hot_q, mu0, omega, cfl, k_sub, steps, dt=0.0, Un=None,
+                bface_corr=None):
     """steps DP-LUR pseudo-time steps of the synthetic equations (Eq. macro)
     from U0.  dt = 0 is the steady form (dt -> infinity); dt > 0 keeps the
-    time term (U - Un)/dt of Eq. macro with Un the previous GSIS state."""
+    time term (U - Un)/dt of Eq. macro with Un the previous GSIS state.
+    bface_corr [boundary faces, 5] is a frozen correction of the boundary
+    face fluxes: at the wall of a DVM cell, the kinetic wall flux of f^{n+1/2}
+    minus the NSF wall flux at W^{n+1/2}; zero elsewhere."""
     U = U0.copy()
     for _ in range(steps):
-        U = relax_step(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, cfl, k_sub, dt, Un)
+        U = relax_step(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, cfl, k_sub, dt, Un, bface_corr)
     return U

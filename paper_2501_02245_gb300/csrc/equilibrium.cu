@@ -274,29 +274,46 @@ void launch_bc_records(gsis_ctx* c) {
 
 // Denominator of the diffuse-wall density: sum over incoming velocities
 // (xi . S_out <= 0) of w |xi . S_out| M_w, one block per (cell, wall side).
+// Also the incoming half-range moments of the wall Maxwellian,
+// wall_in[c][s] = sum_{xi.S <= 0} w (xi.S) (1, xi, |xi|^2/2) M_w, so that the
+// kinetic wall flux of a face is (outgoing moments) + rho_w * wall_in.
 __global__ void k_wall_den(int N, const int* __restrict__ side_bc, const double* __restrict__ Sout,
-                           Records bc, VGridDev vg, double* wall_den) {
+                           Records bc, VGridDev vg, double* wall_den, double* wall_in) {
     const int c = blockIdx.x;
-    __shared__ double sm[32];
+    __shared__ double sm[32 * 6];
     for (int s = 0; s < 6; ++s) {
         if (side_bc[c * 6 + s] != GSIS_BC_WALL) continue;
         const double* S = Sout + ((long long)c * 6 + s) * 3;
         const double* sc = rec_scal(bc, s);
         const double* tb = rec_tab(bc, s, vg.NT);
-        double acc[1] = {0.0};
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
             int ix, iy, iz;
             vsplit(v, vg.nx, vg.ny, ix, iy, iz);
-            const double xn = vg.xi[ix] * S[0] + vg.xi[vg.nx + iy] * S[1] + vg.xi[vg.nx + vg.ny + iz] * S[2];
-            if (!(xn > 0.0)) acc[0] += -xn * eval_rec(sc, tb, vg.NT, vg.nx, vg.ny, ix, iy, iz);
+            const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
+            const double xn = x0 * S[0] + x1 * S[1] + x2 * S[2];
+            if (!(xn > 0.0)) {
+                const double m = eval_rec(sc, tb, vg.NT, vg.nx, vg.ny, ix, iy, iz);
+                const double g = xn * m;
+                acc[0] += -g;
+                acc[1] += g;
+                acc[2] += g * x0;
+                acc[3] += g * x1;
+                acc[4] += g * x2;
+                acc[5] += g * 0.5 * (x0 * x0 + x1 * x1 + x2 * x2);
+            }
         }
-        block_sum<1>(acc, sm);
-        if (threadIdx.x == 0) wall_den[c * 6 + s] = acc[0] * vg.w;
+        block_sum<6>(acc, sm);
+        if (threadIdx.x == 0) {
+            wall_den[c * 6 + s] = acc[0] * vg.w;
+            for (int q = 0; q < 5; ++q) wall_in[((long long)c * 6 + s) * 5 + q] = acc[1 + q] * vg.w;
+        }
     }
 }
 
 void launch_wall_den(gsis_ctx* c) {
-    k_wall_den<<<c->m.N, 256, 0, c->stream>>>(c->m.N, c->m.side_bc, c->m.Sout, c->recBC, c->vg, c->wall_den);
+    k_wall_den<<<c->m.N, 256, 0, c->stream>>>(c->m.N, c->m.side_bc, c->m.Sout, c->recBC, c->vg, c->wall_den,
+                                              c->wall_in);
     c->launches++;
 }
 

@@ -129,6 +129,7 @@ gsis_status check_ctx(gsis_ctx* c) {
 gsis_status presolve(gsis_ctx* c) {
     const int N = c->m.N;
     cudaMemsetAsync(c->hot, 0, (size_t)N * HOTN * sizeof(double), c->stream);
+    cudaMemsetAsync(c->wall_corr, 0, (size_t)N * 30 * sizeof(double), c->stream);   // plain NSF walls
     launch_prim_to_cons(c, c->W, c->U);
     cudaMemcpyAsync(c->Wm, c->W, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     c->presolve_blocks = 0;
@@ -164,7 +165,7 @@ gsis_status start(gsis_ctx* c) {
     launch_bc_records(c);
     launch_wall_den(c);
     phase_begin(c, GSIS_PH_PRESOLVE);
-    if (c->p.adaptive && c->p.presolve_max_blocks > 0) {
+    if (c->p.presolve_max_blocks > 0) {   // Sec. 3.4 Step 1 (also starts an all-kinetic run)
         gsis_status s = presolve(c);
         if (s != GSIS_OK) return s;
     }
@@ -218,9 +219,11 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     used[GSIS_PH_MOMENTS] = true;
     phase_begin(c, GSIS_PH_MOMENTS);
     launch_moments(c, c->W, 0, c->momh);
+    launch_wall_flux(c);
     launch_half_state(c);
-    launch_nsf(c, c->Wh, c->nsf);
+    launch_nsf(c, c->Wh, c->nsf);   // leaves the gradients of W^{n+1/2} in gu, gT
     launch_hot(c);
+    if (c->has_wall) launch_wall_corr(c);
     phase_end(c, GSIS_PH_MOMENTS);
     // 4. synthetic solve over all cells from W^{n+1/2}
     used[GSIS_PH_MACRO] = true;
@@ -381,15 +384,18 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     // face-normal components that are nonzero on some flux-carrying face
     {
         bool any_y = false, any_z = false;
+        int max_dir = 0;
         for (int cc = 0; cc < N; ++cc)
             for (int s = 0; s < 6; ++s) {
                 const bool active = nbr[(size_t)cc * 6 + s] >= 0 || side_bc[(size_t)cc * 6 + s] == GSIS_BC_FARFIELD ||
                                     side_bc[(size_t)cc * 6 + s] == GSIS_BC_WALL;
                 if (!active) continue;
+                max_dir = std::max(max_dir, s / 2 + 1);
                 any_y = any_y || Sout[((size_t)cc * 6 + s) * 3 + 1] != 0.0;
                 any_z = any_z || Sout[((size_t)cc * 6 + s) * 3 + 2] != 0.0;
             }
-        c->normal_components = any_z ? 3 : (any_y ? 2 : 1);
+        // directions 0..D-1 carry flux and normal components 0..D-1 can be nonzero
+        c->normal_components = std::max(max_dir, any_z ? 3 : (any_y ? 2 : 1));
     }
     // least-squares weights over the first dim coordinates
     const int dim = md->dim;
@@ -447,6 +453,8 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->dU = (double*)dev_alloc(c, N5); c->dU2 = (double*)dev_alloc(c, N5); c->R = (double*)dev_alloc(c, N5);
     c->D = (double*)dev_alloc(c, N * sizeof(double));
     c->lamS = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
+    c->Ff = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
+    c->lamf = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
     c->gu = (double*)dev_alloc(c, (size_t)N * 9 * sizeof(double));
     c->gT = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
     c->grho = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
@@ -456,6 +464,11 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->nsf = (double*)dev_alloc(c, (size_t)N * HOTN * sizeof(double));
     c->kn_gll = (double*)dev_alloc(c, N * sizeof(double));
     c->wall_den = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
+    c->wall_in = (double*)dev_alloc(c, (size_t)N * 30 * sizeof(double));
+    c->wall_kin = (double*)dev_alloc(c, (size_t)N * 30 * sizeof(double));
+    c->wall_corr = (double*)dev_alloc(c, (size_t)N * 30 * sizeof(double));
+    c->has_wall = false;
+    for (int s = 0; s < 6; ++s) c->has_wall = c->has_wall || md->bc_type[s] == GSIS_BC_WALL;
     c->eps_buf = (double*)dev_alloc(c, 4 * sizeof(double));
     c->flag = (uint8_t*)dev_alloc(c, N);
     c->cell2dvm = (int*)dev_alloc(c, N * sizeof(int));
@@ -470,13 +483,18 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
     if (!m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wh ||
-        !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->gu || !c->gT ||
-        !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->eps_buf || !c->flag ||
+        !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
+        !c->lamf || !c->gu || !c->gT ||
+        !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->wall_in ||
+        !c->wall_kin || !c->wall_corr || !c->eps_buf || !c->flag ||
         !c->cell2dvm || !c->old_cell2dvm || !c->ghost_id || !c->ghost_cell || !c->enter_list || !c->hp_off ||
         !c->hp_cnt || !c->d_count || !c->specs || !c->recGhost.scal || !c->recBC.scal || !c->d_bc_type ||
         !c->d_bc_state)
         return set_err(c, GSIS_ERR_OOM, "device allocation failed in gsis_set_mesh");
     cudaMemsetAsync(c->wall_den, 0, (size_t)N * 6 * sizeof(double), c->stream);
+    cudaMemsetAsync(c->wall_in, 0, (size_t)N * 30 * sizeof(double), c->stream);
+    cudaMemsetAsync(c->wall_kin, 0, (size_t)N * 30 * sizeof(double), c->stream);
+    cudaMemsetAsync(c->wall_corr, 0, (size_t)N * 30 * sizeof(double), c->stream);
     cudaMemsetAsync(c->kn_gll, 0, (size_t)N * sizeof(double), c->stream);
     c->mesh_set = true;
     if (c->vgrid_set) {

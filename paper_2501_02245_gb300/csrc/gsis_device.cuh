@@ -105,19 +105,24 @@ template <> struct RecT<float> {
     }
 };
 
+// Record tables are read-only while the kernels that evaluate them run, so
+// they are read through the non-coherent path (__ldg): this also tells the
+// compiler they cannot alias the VDF being updated.
 template <typename T>
 __device__ __forceinline__ T eval_recT(const T* __restrict__ scal, const T* __restrict__ tab, int NT, int nx, int ny,
                                        int ix, int iy, int iz) {
     const int jy = nx + iy, jz = nx + ny + iz;
-    T e = tab[ix] * tab[jy] * tab[jz];
+    T e = __ldg(tab + ix) * __ldg(tab + jy) * __ldg(tab + jz);
     const T* B = tab + NT;
     const T* C2 = tab + 3 * NT;
     const T* Rr = tab + 4 * NT;
-    T poly = scal[RS_P0] + (B[ix] + B[jy] + B[jz]) + (Rr[ix] + Rr[jy] + Rr[jz]) * (C2[ix] + C2[jy] + C2[jz]);
-    if (scal[RS_OFFD] != T(0)) {
+    T poly = __ldg(scal + RS_P0) + (__ldg(B + ix) + __ldg(B + jy) + __ldg(B + jz)) +
+             (__ldg(Rr + ix) + __ldg(Rr + jy) + __ldg(Rr + jz)) * (__ldg(C2 + ix) + __ldg(C2 + jy) + __ldg(C2 + jz));
+    if (__ldg(scal + RS_OFFD) != T(0)) {
         const T* C = tab + 2 * NT;
-        T cx = C[ix], cy = C[jy], cz = C[jz];
-        poly += T(2) * (scal[RS_P2XY] * cx * cy + scal[RS_P2XZ] * cx * cz + scal[RS_P2YZ] * cy * cz);
+        T cx = __ldg(C + ix), cy = __ldg(C + jy), cz = __ldg(C + jz);
+        poly += T(2) * (__ldg(scal + RS_P2XY) * cx * cy + __ldg(scal + RS_P2XZ) * cx * cz +
+                        __ldg(scal + RS_P2YZ) * cy * cz);
     }
     return e * poly;
 }

@@ -81,6 +81,7 @@ struct gsis_ctx {
 
     gsis::Mesh m;
     int normal_components = 3;     // 1: only x, 2: x and y, 3: x, y, z components of face normals are nonzero
+    bool has_wall = false;         // some boundary side is a diffuse wall
     int* d_bc_type = nullptr;      // [6]
     double* d_bc_state = nullptr;  // [6][5]
     std::vector<double> host_W0;
@@ -96,6 +97,7 @@ struct gsis_ctx {
     // macro state
     double *W = nullptr, *Wh = nullptr, *Wp = nullptr, *Wm = nullptr, *U = nullptr, *Un = nullptr;
     double *dU = nullptr, *dU2 = nullptr, *R = nullptr, *D = nullptr, *lamS = nullptr;
+    double *Ff = nullptr, *lamf = nullptr;   // interior face fluxes [N][3][5] and lambda|S| [N][3] (high faces)
     double *gu = nullptr, *gT = nullptr, *grho = nullptr, *gU = nullptr;
     double *hot = nullptr, *kin = nullptr, *nsf = nullptr, *kn_gll = nullptr;
     double *eps_buf = nullptr, *h_eps = nullptr;
@@ -110,6 +112,9 @@ struct gsis_ctx {
     float *SoVf = nullptr, *itauf = nullptr, *rho_wf = nullptr;   // FP32 mirrors for the FP32 sweep
     void* f = nullptr;
     double *itau = nullptr, *mom = nullptr, *rho_w = nullptr, *wall_den = nullptr;
+    double *wall_in = nullptr;     // [N][6][5] incoming half-range moments of the wall Maxwellian
+    double *wall_kin = nullptr;    // [N][6][5] kinetic wall flux of f^{n+1/2}
+    double *wall_corr = nullptr;   // [N][6][5] kinetic minus NSF wall flux at W^{n+1/2} (0 for NS cells)
     gsis::Records recG{}, recHalf{}, recNew{}, recGhost{}, recBC{};
     int* ghost_id = nullptr;       // [N] ghost record index or -1
     int* ghost_cell = nullptr;     // [N] cell of each ghost record
@@ -148,6 +153,8 @@ void launch_sweep(gsis_ctx* c, int pass);
 void launch_moments(gsis_ctx* c, const double* Wref, int correct_pass, double* out);
 void launch_half_state(gsis_ctx* c);
 void launch_hot(gsis_ctx* c);
+void launch_wall_flux(gsis_ctx* c);
+void launch_wall_corr(gsis_ctx* c);
 // macro.cu
 void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U);
 void launch_nsf(gsis_ctx* c, const double* Wprim, double* out);

@@ -14,9 +14,9 @@
 //  * DP-LUR pseudo-time relaxation (Wright, Candler & Bose 1998): scalar
 //    diagonal (1/CFL + 1/2) sum lambda |S| (+ V/dt with the time term of
 //    Eq. macro), k_sub Jacobi sweeps over Rusanov-split Euler flux changes.
-// Each interior face flux is evaluated by both of its cells with the same
-// canonical orientation (low-index cell = L), so the two evaluations are
-// bitwise equal and the scheme is exactly conservative.
+// Every interior face flux is evaluated once, by one thread (face kernel),
+// and gathered by both cells in a fixed order (cell kernel), so the scheme is
+// exactly conservative and deterministic.
 #include "gsis_device.cuh"
 
 namespace gsis {
@@ -69,11 +69,11 @@ __global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with
         if (n >= 0) {
             const double* wn = Wp + n * 5;
             val[0] = wn[1]; val[1] = wn[2]; val[2] = wn[3]; val[3] = wn[4]; val[4] = wn[0];
-            val[5] = sqrt(wn[1] * wn[1] + wn[2] * wn[2] + wn[3] * wn[3]);
+            val[5] = with_rho_U ? sqrt(wn[1] * wn[1] + wn[2] * wn[2] + wn[3] * wn[3]) : 0.0;
         } else if (bc == GSIS_BC_FARFIELD) {
             const double* st = a.bc_state + s * 5;
             val[0] = st[1]; val[1] = st[2]; val[2] = st[3]; val[3] = st[4]; val[4] = st[0];
-            val[5] = sqrt(st[1] * st[1] + st[2] * st[2] + st[3] * st[3]);
+            val[5] = with_rho_U ? sqrt(st[1] * st[1] + st[2] * st[2] + st[3] * st[3]) : 0.0;
         } else if (bc == GSIS_BC_WALL) {
             const double* st = a.bc_state + s * 5;
             val[0] = 0.0; val[1] = 0.0; val[2] = 0.0; val[3] = st[4]; val[4] = wc[0]; val[5] = 0.0;
@@ -82,7 +82,8 @@ __global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with
         }
         const double phic[6] = {wc[1], wc[2], wc[3], wc[4], wc[0], Uc};
         const double* w = a.lsq_w + ((long long)c * 6 + s) * 3;
-        for (int q = 0; q < 6; ++q) {
+        const int nq = with_rho_U ? 6 : 4;
+        for (int q = 0; q < nq; ++q) {
             const double dphi = val[q] - phic[q];
             g[q][0] += w[0] * dphi;
             g[q][1] += w[1] * dphi;
@@ -102,8 +103,8 @@ __global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with
 
 void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U) {
     const int N = c->m.N;
-    k_gradients<<<(N + 127) / 128, 128, 0, c->stream>>>(margs(c), Wprim, with_rho_U ? 1 : 0, c->gu, c->gT, c->grho,
-                                                        c->gU);
+    k_gradients<<<(N + 63) / 64, 64, 0, c->stream>>>(margs(c), Wprim, with_rho_U ? 1 : 0, c->gu, c->gT, c->grho,
+                                                     c->gU);
     c->launches++;
 }
 
@@ -196,7 +197,6 @@ __device__ void hllc(double rL, const double* uL, double pL, double rR, const do
     // F_L if S_L >= 0; else F*_L if S* >= 0; else F*_R if S_R >= 0; else F_R
     const bool left = (SL >= 0.0) || (Ss >= 0.0);
     const bool use_plain = (SL >= 0.0) || !(left || SR >= 0.0);
-    // the side whose flux (or star flux) is needed
     const double r = left ? rL : rR;
     const double* u = left ? uL : uR;
     const double p = left ? pL : pR;
@@ -234,102 +234,186 @@ __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u
     q[0] = w[0]; q[1] = w[1]; q[2] = w[2]; q[3] = w[3]; q[4] = w[0] * w[4];
 }
 
-// Residual R_c = -sum_F F.S_out, spectral radii, diagonal D and dU0 = R/D.
-__global__ void k_residual(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ U,
-                           const double* __restrict__ Un, const double* __restrict__ gu,
-                           const double* __restrict__ gT, const double* __restrict__ hot, double cfl, double dt,
-                           double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
-                           double* __restrict__ dU) {
+// Interior face between L = cell c and R = its neighbour across side 2d+1
+// (area vector S pointing L -> R).  Writes the total face flux (inviscid +
+// viscous + HoT) F.S to Ff[c][d][5] and lambda |S| to lamf[c][d]; faces that
+// do not exist (boundary) get lamf = -1.
+__global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ gu,
+                            const double* __restrict__ gT, const double* __restrict__ hot, int ndir,
+                            double* __restrict__ Ff, double* __restrict__ lamf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.N * ndir) return;
+    const int L = t / ndir, d = t % ndir;
+    const int Rr = a.nbr[L * 6 + 2 * d + 1];
+    double* F = Ff + ((long long)L * 3 + d) * 5;
+    if (Rr < 0) {
+        lamf[(long long)L * 3 + d] = -1.0;
+        return;
+    }
+    const double* S = a.Sout + ((long long)L * 6 + 2 * d + 1) * 3;
+    const double Sabs = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    const double nn[3] = {S[0] / Sabs, S[1] / Sabs, S[2] / Sabs};
+    double qL[5], qR[5], slL[5] = {0, 0, 0, 0, 0}, slR[5] = {0, 0, 0, 0, 0};
+    prim5(Wm + L * 5, qL);
+    prim5(Wm + Rr * 5, qR);
+    {
+        const int lo = a.nbr[L * 6 + 2 * d], hi = Rr;
+        if (lo >= 0) {
+            double ql[5];
+            prim5(Wm + lo * 5, ql);
+            for (int q = 0; q < 5; ++q) slL[q] = minmod(qL[q] - ql[q], qR[q] - qL[q]);
+            (void)hi;
+        }
+    }
+    {
+        const int hi = a.nbr[Rr * 6 + 2 * d + 1];
+        if (hi >= 0) {
+            double qh[5];
+            prim5(Wm + hi * 5, qh);
+            for (int q = 0; q < 5; ++q) slR[q] = minmod(qR[q] - qL[q], qh[q] - qR[q]);
+        }
+    }
+    double fl[5], fr[5];
+    for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + 0.5 * slL[q]; fr[q] = qR[q] - 0.5 * slR[q]; }
+    double Fv[5];
+    hllc(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, Fv);
+    for (int q = 0; q < 5; ++q) Fv[q] *= Sabs;
+    // viscous + HoT
+    const double* wL = Wm + L * 5;
+    const double* wR = Wm + Rr * 5;
+    const double uf[3] = {0.5 * (wL[1] + wR[1]), 0.5 * (wL[2] + wR[2]), 0.5 * (wL[3] + wR[3])};
+    const double Tf = 0.5 * (wL[4] + wR[4]);
+    const double muf = viscosity(Tf, a.mu0, a.omega);
+    double e[3];
+    for (int i = 0; i < 3; ++i) e[i] = a.cen[Rr * 3 + i] - a.cen[L * 3 + i];
+    const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    for (int i = 0; i < 3; ++i) e[i] /= dist;
+    double guf[9], gTf[3];
+    for (int j = 0; j < 3; ++j) {
+        double gav[3];
+        for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gu[(long long)L * 9 + j * 3 + i] + gu[(long long)Rr * 9 + j * 3 + i]);
+        const double corr = (wR[1 + j] - wL[1 + j]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
+        for (int i = 0; i < 3; ++i) guf[j * 3 + i] = gav[i] + corr * e[i];
+    }
+    {
+        double gav[3];
+        for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gT[(long long)L * 3 + i] + gT[(long long)Rr * 3 + i]);
+        const double corr = (wR[4] - wL[4]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
+        for (int i = 0; i < 3; ++i) gTf[i] = gav[i] + corr * e[i];
+    }
+    double sig[6], qf[3];
+    nsf_of(muf, guf, gTf, sig, qf);
+    const double* hL = hot + (long long)L * HOTN;
+    const double* hR = hot + (long long)Rr * HOTN;
+    double Sg[6], Q[3];
+    for (int q = 0; q < 6; ++q) Sg[q] = sig[q] + 0.5 * (hL[q] + hR[q]);
+    for (int q = 0; q < 3; ++q) Q[q] = qf[q] + 0.5 * (hL[6 + q] + hR[6 + q]);
+    const double SigS[3] = {Sg[0] * S[0] + Sg[3] * S[1] + Sg[4] * S[2], Sg[3] * S[0] + Sg[1] * S[1] + Sg[5] * S[2],
+                            Sg[4] * S[0] + Sg[5] * S[1] + Sg[2] * S[2]};
+    F[0] = Fv[0];
+    F[1] = Fv[1] + SigS[0];
+    F[2] = Fv[2] + SigS[1];
+    F[3] = Fv[3] + SigS[2];
+    F[4] = Fv[4] + ((SigS[0] * uf[0] + SigS[1] * uf[1] + SigS[2] * uf[2]) + (Q[0] * S[0] + Q[1] * S[1] + Q[2] * S[2]));
+    const double aL = sqrt(GAMMA * wL[4]), aR = sqrt(GAMMA * wR[4]);
+    const double lam = fabs(uf[0] * nn[0] + uf[1] * nn[1] + uf[2] * nn[2]) + 0.5 * (aL + aR) +
+                       5.0 * muf / (0.5 * (wL[0] + wR[0]) * dist);
+    lamf[(long long)L * 3 + d] = lam * Sabs;
+}
+
+// NSF flux through wall side s of cell c at state w (prim) with cell gradients
+// gu, gT: no mass flux, cell pressure, NSF stress and heat flux at u = 0,
+// T = T_w from the cell gradient corrected along the cell-to-face line.
+__device__ void wall_nsf_flux(const MacroArgs& a, const double* w, const double* gu, const double* gT, int c, int s,
+                              double* Fb) {
+    const double* So = a.Sout + ((long long)c * 6 + s) * 3;
+    const double Tw = a.bc_state[s * 5 + 4];
+    double eb[3];
+    for (int i = 0; i < 3; ++i) eb[i] = a.xf[((long long)c * 6 + s) * 3 + i] - a.cen[c * 3 + i];
+    const double bdist = sqrt(eb[0] * eb[0] + eb[1] * eb[1] + eb[2] * eb[2]);
+    for (int i = 0; i < 3; ++i) eb[i] /= bdist;
+    double guw[9], gTw[3];
+    for (int j = 0; j < 3; ++j) {
+        const double* gc = gu + j * 3;
+        const double corr = (0.0 - w[1 + j]) / bdist - (gc[0] * eb[0] + gc[1] * eb[1] + gc[2] * eb[2]);
+        for (int i = 0; i < 3; ++i) guw[j * 3 + i] = gc[i] + corr * eb[i];
+    }
+    {
+        const double corr = (Tw - w[4]) / bdist - (gT[0] * eb[0] + gT[1] * eb[1] + gT[2] * eb[2]);
+        for (int i = 0; i < 3; ++i) gTw[i] = gT[i] + corr * eb[i];
+    }
+    double sig[6], qw[3];
+    nsf_of(viscosity(Tw, a.mu0, a.omega), guw, gTw, sig, qw);
+    const double p = w[0] * w[4];
+    const double SigS[3] = {sig[0] * So[0] + sig[3] * So[1] + sig[4] * So[2],
+                            sig[3] * So[0] + sig[1] * So[1] + sig[5] * So[2],
+                            sig[4] * So[0] + sig[5] * So[1] + sig[2] * So[2]};
+    Fb[0] = 0.0;
+    Fb[1] = p * So[0] + SigS[0];
+    Fb[2] = p * So[1] + SigS[1];
+    Fb[3] = p * So[2] + SigS[2];
+    Fb[4] = qw[0] * So[0] + qw[1] * So[1] + qw[2] * So[2];
+}
+
+// Wall correction of the synthetic solve: for each wall side of a DVM cell,
+// the kinetic wall flux of f^{n+1/2} minus the NSF wall flux at W^{n+1/2}
+// (gradients of W^{n+1/2} in gu, gT); zero elsewhere.
+__global__ void k_wall_corr(MacroArgs a, const int* __restrict__ cell2dvm, const double* __restrict__ Wh,
+                            const double* __restrict__ gu, const double* __restrict__ gT,
+                            const double* __restrict__ wall_kin, double* __restrict__ wall_corr) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    for (int s = 0; s < 6; ++s) {
+        double* o = wall_corr + ((long long)c * 6 + s) * 5;
+        if (a.nbr[c * 6 + s] < 0 && a.side_bc[c * 6 + s] == GSIS_BC_WALL && cell2dvm[c] >= 0) {
+            double F[5];
+            wall_nsf_flux(a, Wh + c * 5, gu + (long long)c * 9, gT + (long long)c * 3, c, s, F);
+            const double* kin = wall_kin + ((long long)c * 6 + s) * 5;
+            for (int q = 0; q < 5; ++q) o[q] = kin[q] - F[q];
+        } else {
+            for (int q = 0; q < 5; ++q) o[q] = 0.0;
+        }
+    }
+}
+
+void launch_wall_corr(gsis_ctx* c) {
+    const int N = c->m.N;
+    k_wall_corr<<<(N + 63) / 64, 64, 0, c->stream>>>(margs(c), c->cell2dvm, c->Wh, c->gu, c->gT, c->wall_kin,
+                                                     c->wall_corr);
+    c->launches++;
+}
+
+// Cell residual R_c = -sum_F F.S_out (gathering the interior face fluxes in
+// side order, boundary faces evaluated here), lambda|S| per side, the
+// diagonal D and dU0 = R/D.
+__global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ U,
+                                const double* __restrict__ Un, const double* __restrict__ gu,
+                                const double* __restrict__ gT, const double* __restrict__ hot,
+                                const double* __restrict__ Ff, const double* __restrict__ lamf,
+                                const double* __restrict__ wall_corr, double cfl, double dt,
+                                double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
+                                double* __restrict__ dU) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.N) return;
     const double* wc = Wm + c * 5;
     const double rho_c = wc[0], T_c = wc[4], p_c = rho_c * T_c;
     const double u_c[3] = {wc[1], wc[2], wc[3]};
-    const double a_c = sqrt(GAMMA * p_c / rho_c);
-    const double mu_c = viscosity(T_c, a.mu0, a.omega);
     double Rc[5] = {0, 0, 0, 0, 0};
     double lam_sum = 0.0;
     for (int s = 0; s < 6; ++s) {
         const int n = a.nbr[c * 6 + s];
         const int bc = a.side_bc[c * 6 + s];
         const double* So = a.Sout + ((long long)c * 6 + s) * 3;
+        const int d = s >> 1;
         if (n >= 0) {
             const bool isL = (s & 1) != 0;
-            const int L = isL ? c : n, Rr = isL ? n : c;
-            const double S[3] = {isL ? So[0] : -So[0], isL ? So[1] : -So[1], isL ? So[2] : -So[2]};
-            const int d = s >> 1;
-            const double Sabs = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-            const double nn[3] = {S[0] / Sabs, S[1] / Sabs, S[2] / Sabs};
-            double qL[5], qR[5], qq[5], slL[5] = {0, 0, 0, 0, 0}, slR[5] = {0, 0, 0, 0, 0};
-            prim5(Wm + L * 5, qL);
-            prim5(Wm + Rr * 5, qR);
-            {
-                const int lo = a.nbr[L * 6 + 2 * d], hi = a.nbr[L * 6 + 2 * d + 1];
-                if (lo >= 0 && hi >= 0) {
-                    double ql[5], qh[5];
-                    prim5(Wm + lo * 5, ql);
-                    prim5(Wm + hi * 5, qh);
-                    for (int q = 0; q < 5; ++q) slL[q] = minmod(qL[q] - ql[q], qh[q] - qL[q]);
-                }
-            }
-            {
-                const int lo = a.nbr[Rr * 6 + 2 * d], hi = a.nbr[Rr * 6 + 2 * d + 1];
-                if (lo >= 0 && hi >= 0) {
-                    double ql[5], qh[5];
-                    prim5(Wm + lo * 5, ql);
-                    prim5(Wm + hi * 5, qh);
-                    for (int q = 0; q < 5; ++q) slR[q] = minmod(qR[q] - ql[q], qh[q] - qR[q]);
-                }
-            }
-            double fl[5], fr[5];
-            for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + 0.5 * slL[q]; fr[q] = qR[q] - 0.5 * slR[q]; }
-            double F[5];
-            hllc(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, F);
-            for (int q = 0; q < 5; ++q) F[q] *= Sabs;
-            // viscous + HoT
-            const double* wL = Wm + L * 5;
-            const double* wR = Wm + Rr * 5;
-            const double uf[3] = {0.5 * (wL[1] + wR[1]), 0.5 * (wL[2] + wR[2]), 0.5 * (wL[3] + wR[3])};
-            const double Tf = 0.5 * (wL[4] + wR[4]);
-            const double muf = viscosity(Tf, a.mu0, a.omega);
-            double e[3];
-            for (int i = 0; i < 3; ++i) e[i] = a.cen[Rr * 3 + i] - a.cen[L * 3 + i];
-            const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-            for (int i = 0; i < 3; ++i) e[i] /= dist;
-            double guf[9], gTf[3];
-            for (int j = 0; j < 3; ++j) {
-                double gav[3];
-                for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gu[(long long)L * 9 + j * 3 + i] + gu[(long long)Rr * 9 + j * 3 + i]);
-                const double corr = (wR[1 + j] - wL[1 + j]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
-                for (int i = 0; i < 3; ++i) guf[j * 3 + i] = gav[i] + corr * e[i];
-            }
-            {
-                double gav[3];
-                for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gT[(long long)L * 3 + i] + gT[(long long)Rr * 3 + i]);
-                const double corr = (wR[4] - wL[4]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
-                for (int i = 0; i < 3; ++i) gTf[i] = gav[i] + corr * e[i];
-            }
-            double sig[6], qf[3];
-            nsf_of(muf, guf, gTf, sig, qf);
-            const double* hL = hot + (long long)L * HOTN;
-            const double* hR = hot + (long long)Rr * HOTN;
-            double Sg[6], Q[3];
-            for (int q = 0; q < 6; ++q) Sg[q] = sig[q] + 0.5 * (hL[q] + hR[q]);
-            for (int q = 0; q < 3; ++q) Q[q] = qf[q] + 0.5 * (hL[6 + q] + hR[6 + q]);
-            const double SigS[3] = {Sg[0] * S[0] + Sg[3] * S[1] + Sg[4] * S[2],
-                                    Sg[3] * S[0] + Sg[1] * S[1] + Sg[5] * S[2],
-                                    Sg[4] * S[0] + Sg[5] * S[1] + Sg[2] * S[2]};
-            F[1] += SigS[0];
-            F[2] += SigS[1];
-            F[3] += SigS[2];
-            F[4] += (SigS[0] * uf[0] + SigS[1] * uf[1] + SigS[2] * uf[2]) + (Q[0] * S[0] + Q[1] * S[1] + Q[2] * S[2]);
+            const int L = isL ? c : n;
+            const double* F = Ff + ((long long)L * 3 + d) * 5;
             const double sgn = isL ? -1.0 : 1.0;
             for (int q = 0; q < 5; ++q) Rc[q] += sgn * F[q];
-            const double aL = sqrt(GAMMA * wL[4]), aR = sqrt(GAMMA * wR[4]);
-            const double lam = fabs(uf[0] * nn[0] + uf[1] * nn[1] + uf[2] * nn[2]) + 0.5 * (aL + aR) +
-                               5.0 * muf / (0.5 * (wL[0] + wR[0]) * dist);
-            lamS[(long long)c * 6 + s] = lam * Sabs;
-            lam_sum += lam * Sabs;
+            const double ls = lamf[(long long)L * 3 + d];
+            lamS[(long long)c * 6 + s] = ls;
+            lam_sum += ls;
         } else if (bc == GSIS_BC_FARFIELD || bc == GSIS_BC_WALL) {
             const double* st = a.bc_state + s * 5;
             const double Sabs = sqrt(So[0] * So[0] + So[1] * So[1] + So[2] * So[2]);
@@ -352,34 +436,13 @@ __global__ void k_residual(MacroArgs a, const double* __restrict__ Wm, const dou
                 Fb[4] += (SigS[0] * ufb[0] + SigS[1] * ufb[1] + SigS[2] * ufb[2]) +
                          (h[6] * So[0] + h[7] * So[1] + h[8] * So[2]);
             } else {
-                const double Tw = st[4];
-                for (int i = 0; i < 3; ++i) eb[i] /= bdist;
-                double guw[9], gTw[3];
-                for (int j = 0; j < 3; ++j) {
-                    const double* gc = gu + (long long)c * 9 + j * 3;
-                    const double corr = (0.0 - u_c[j]) / bdist - (gc[0] * eb[0] + gc[1] * eb[1] + gc[2] * eb[2]);
-                    for (int i = 0; i < 3; ++i) guw[j * 3 + i] = gc[i] + corr * eb[i];
-                }
-                {
-                    const double* gc = gT + (long long)c * 3;
-                    const double corr = (Tw - T_c) / bdist - (gc[0] * eb[0] + gc[1] * eb[1] + gc[2] * eb[2]);
-                    for (int i = 0; i < 3; ++i) gTw[i] = gc[i] + corr * eb[i];
-                }
-                double sig[6], qw[3];
-                nsf_of(viscosity(Tw, a.mu0, a.omega), guw, gTw, sig, qw);
-                double Sg[6], Q[3];
-                for (int q = 0; q < 6; ++q) Sg[q] = sig[q] + h[q];
-                for (int q = 0; q < 3; ++q) Q[q] = qw[q] + h[6 + q];
-                const double SigS[3] = {Sg[0] * So[0] + Sg[3] * So[1] + Sg[4] * So[2],
-                                        Sg[3] * So[0] + Sg[1] * So[1] + Sg[5] * So[2],
-                                        Sg[4] * So[0] + Sg[5] * So[1] + Sg[2] * So[2]};
-                Fb[0] = 0.0;
-                Fb[1] = p_c * So[0] + SigS[0];
-                Fb[2] = p_c * So[1] + SigS[1];
-                Fb[3] = p_c * So[2] + SigS[2];
-                Fb[4] = Q[0] * So[0] + Q[1] * So[1] + Q[2] * So[2];
+                wall_nsf_flux(a, wc, gu + (long long)c * 9, gT + (long long)c * 3, c, s, Fb);
+                const double* wcr = wall_corr + ((long long)c * 6 + s) * 5;
+                for (int q = 0; q < 5; ++q) Fb[q] += wcr[q];
             }
             for (int q = 0; q < 5; ++q) Rc[q] -= Fb[q];
+            const double a_c = sqrt(GAMMA * p_c / rho_c);
+            const double mu_c = viscosity(T_c, a.mu0, a.omega);
             const double lam = fabs(u_c[0] * nn[0] + u_c[1] * nn[1] + u_c[2] * nn[2]) + a_c +
                                5.0 * mu_c / (rho_c * 2.0 * bdist);
             lamS[(long long)c * 6 + s] = lam * Sabs;
@@ -434,22 +497,26 @@ __global__ void k_update(int N, double* __restrict__ U, const double* __restrict
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term) {
     (void)with_hot;
     const int N = c->m.N;
-    const int nb = (N + 127) / 128;
+    const int TB = 64;
+    const int nb = (N + TB - 1) / TB;
+    const int ndir = c->normal_components;   // index directions that carry flux
+    const int nf = (N * ndir + TB - 1) / TB;
     MacroArgs a = margs(c);
     const double dt = time_term ? c->p.dt : 0.0;
     for (int it = 0; it < steps; ++it) {
         launch_gradients(c, c->Wm, false);
-        k_residual<<<nb, 128, 0, c->stream>>>(a, c->Wm, c->U, c->Un, c->gu, c->gT, c->hot, c->p.cfl, dt, c->R, c->D,
-                                             c->lamS, c->dU);
-        c->launches++;
+        k_face_flux<<<nf, TB, 0, c->stream>>>(a, c->Wm, c->gu, c->gT, c->hot, ndir, c->Ff, c->lamf);
+        k_cell_residual<<<nb, TB, 0, c->stream>>>(a, c->Wm, c->U, c->Un, c->gu, c->gT, c->hot, c->Ff, c->lamf,
+                                                  c->wall_corr, c->p.cfl, dt, c->R, c->D, c->lamS, c->dU);
+        c->launches += 2;
         double* din = c->dU;
         double* dout = c->dU2;
         for (int s = 0; s < c->p.k_sub; ++s) {
-            k_relax<<<nb, 128, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout);
+            k_relax<<<nb, TB, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout);
             c->launches++;
             double* t = din; din = dout; dout = t;
         }
-        k_update<<<nb, 128, 0, c->stream>>>(N, c->U, din, c->Wm);
+        k_update<<<nb, TB, 0, c->stream>>>(N, c->U, din, c->Wm);
         c->launches++;
     }
 }

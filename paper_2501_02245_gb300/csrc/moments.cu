@@ -207,6 +207,76 @@ void launch_half_state(gsis_ctx* c) {
     c->launches++;
 }
 
+// Kinetic flux of (mass, momentum, energy) through each diffuse-wall face of a
+// DVM cell, carried by the face distribution of f^{n+1/2}: the cell's values
+// for outgoing velocities and rho_w M_w (rho_w from zero net mass flux) for
+// incoming ones: F = sum_{xi.S>0} w (xi.S) psi f + rho_w wall_in.
+template <typename S>
+__global__ void __launch_bounds__(256) k_wall_flux(int Nd, const int* __restrict__ dvm_cell,
+                                                   const int* __restrict__ side_bc, const double* __restrict__ Sout,
+                                                   const S* __restrict__ f, VGridDev vg,
+                                                   const double* __restrict__ wall_den,
+                                                   const double* __restrict__ wall_in, double* __restrict__ wall_kin) {
+    const int k = blockIdx.x;
+    if (k >= Nd) return;
+    const int c = dvm_cell[k];
+    __shared__ double sm[32 * 5];
+    for (int s = 0; s < 6; ++s) {
+        if (side_bc[c * 6 + s] != GSIS_BC_WALL) continue;
+        const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+        const S* fk = f + (long long)k * vg.Nv;
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
+            int ix, iy, iz;
+            vsplit(v, vg.nx, vg.ny, ix, iy, iz);
+            const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
+            const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
+            if (xn > 0.0) {
+                const double g = xn * Store<S>::ld(fk + v);
+                acc[0] += g;
+                acc[1] += g * x0;
+                acc[2] += g * x1;
+                acc[3] += g * x2;
+                acc[4] += g * 0.5 * (x0 * x0 + x1 * x1 + x2 * x2);
+            }
+        }
+        block_sum<5>(acc, sm);
+        if (threadIdx.x == 0) {
+            const long long o = ((long long)c * 6 + s) * 5;
+            const double rw = acc[0] * vg.w / wall_den[c * 6 + s];
+            for (int q = 0; q < 5; ++q) wall_kin[o + q] = acc[q] * vg.w + rw * wall_in[o + q];
+        }
+    }
+}
+
+void launch_wall_flux(gsis_ctx* c) {
+    const int Nd = (int)c->Nd;
+    if (Nd == 0 || !c->has_wall) return;
+    switch (c->p.vdf_dtype) {
+        case GSIS_F64:
+            k_wall_flux<double><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                            (const double*)c->f, c->vg, c->wall_den, c->wall_in,
+                                                            c->wall_kin);
+            break;
+        case GSIS_F32:
+            k_wall_flux<float><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                           (const float*)c->f, c->vg, c->wall_den, c->wall_in,
+                                                           c->wall_kin);
+            break;
+        case GSIS_BF16:
+            k_wall_flux<__nv_bfloat16><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                                   (const __nv_bfloat16*)c->f, c->vg, c->wall_den,
+                                                                   c->wall_in, c->wall_kin);
+            break;
+        default:
+            k_wall_flux<__half><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                            (const __half*)c->f, c->vg, c->wall_den, c->wall_in,
+                                                            c->wall_kin);
+            break;
+    }
+    c->launches++;
+}
+
 // HoT = kinetic - NSF(W^{n+1/2}) in DVM cells, zero in NS cells (Eq. full_constitutive).
 __global__ void k_hot(int N, const int* __restrict__ cell2dvm, const double* __restrict__ kin,
                       const double* __restrict__ nsf, double* __restrict__ hot) {

@@ -13,28 +13,24 @@
 //
 // Parallel structure.  Every dependency of the update at (c, xi) is on the
 // same velocity xi, and cells of one hyperplane never depend on each other.
-// A block owns 32 consecutive velocities (one per lane, so a warp reads 32
-// consecutive values of a cell row: coalesced, velocity innermost) and G
-// warps; warp w updates the cells k = w, w+G, ... of each hyperplane, and the
-// block synchronises once per hyperplane.  Each update first gathers all the
-// values of its stencil (own value, both neighbours and both second
-// neighbours along each direction) and then computes without branches on the
-// sign of xi.n, so the loads of consecutive cells overlap.
+// A block owns 32*VPT consecutive velocities: lane l of every warp handles
+// the VPT velocities l, l+32, ..., so each warp-wide load reads 32
+// consecutive values of a cell row (coalesced, velocity innermost).  The G
+// warps of the block split the cells of each hyperplane and the block
+// synchronises once per hyperplane.  A warp updates CB cells of a hyperplane
+// at a time: the cells' metadata (read through the non-coherent path, so the
+// compiler may load it ahead of the VDF stores), then the stencils of all
+// CB x VPT points (own value, both neighbours and both second neighbours per
+// direction), then the branch-free updates, then the stores -- so the memory
+// latency of CB x VPT independent updates overlaps.
 //
 // Arithmetic type T: FP64 for an FP64 VDF (ALU-bound on GB300: 2 DFMA/clk/SM),
-// FP32 for FP32 / BF16 / FP16 storage (HBM-bound).  Face-normal components
-// that are zero on every face of the mesh are skipped (NC).
+// FP32 for FP32 / BF16 / FP16 storage.  NC = number of index directions that
+// carry flux and of face-normal components that can be nonzero (1, 2 or 3 for
+// 1D, 2D and 3D meshes); the rest is skipped.
 #include "gsis_device.cuh"
 
 namespace gsis {
-
-template <typename T> struct Meta;
-template <> struct Meta<double> {
-    static __device__ __forceinline__ const double* sov(const double* d, const float*) { return d; }
-};
-template <> struct Meta<float> {
-    static __device__ __forceinline__ const float* sov(const double*, const float* f) { return f; }
-};
 
 struct SweepArgs {
     int H;
@@ -59,118 +55,189 @@ __device__ __forceinline__ T minmod_t(T a, T b) {
     return a * b > T(0) ? m : T(0);
 }
 
-template <int NC, typename T>
-__device__ __forceinline__ T normal_speed(T x0, T x1, T x2, const T* S) {
-    if (NC == 1) return x0 * S[0];
-    if (NC == 2) return x0 * S[0] + x1 * S[1];
-    return x0 * S[0] + x1 * S[1] + x2 * S[2];
-}
-
 template <typename T>
 __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
-// Values of the stencil of one (cell, velocity) point along direction d.
-template <typename T>
-struct Stencil {
-    T lo, hi, lo2, hi2;
+// per-thread velocity data
+template <typename T, int VPT>
+struct Vel {
+    long long v[VPT];
+    int ix[VPT], iy[VPT], iz[VPT];
+    T x0[VPT], x1[VPT], x2[VPT];
+    bool on[VPT];
 };
 
-template <typename S, typename T, int NC>
-__device__ __forceinline__ void update_point(const SweepArgs& a, S* __restrict__ f, int k, long long v, int ix, int iy,
-                                             int iz, T x0, T x1, T x2) {
-    const long long Nv = a.vg.Nv;
-    const int NT = a.vg.NT, nx = a.vg.nx, ny = a.vg.ny;
-    const int* kind = a.kind + (long long)k * 6;
-    const int* ref = a.ref + (long long)k * 6;
-    const int* nb2 = a.nb2 + (long long)k * 6;
-    constexpr int ND = 3;    // index directions (a direction whose sides are NONE costs only integer tests)
-    // ---- gather
-    S* fk = f + (long long)k * Nv + v;
-    const T fc = ldT<T, S>(fk);
-    Stencil<T> st[3];
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        const bool dl = kind[2 * d] == SK_DVM, dh = kind[2 * d + 1] == SK_DVM;
-        st[d].lo = dl ? ldT<T, S>(f + (long long)ref[2 * d] * Nv + v) : fc;
-        st[d].hi = dh ? ldT<T, S>(f + (long long)ref[2 * d + 1] * Nv + v) : fc;
-        st[d].lo2 = (dl && nb2[2 * d] >= 0) ? ldT<T, S>(f + (long long)nb2[2 * d] * Nv + v) : st[d].lo;
-        st[d].hi2 = (dh && nb2[2 * d + 1] >= 0) ? ldT<T, S>(f + (long long)nb2[2 * d + 1] * Nv + v) : st[d].hi;
-    }
-    // ---- compute
-    const T it = pick<T>(a.itau, a.itauf)[k];
-    T den = it;
-    T num = eval_recT<T>(RecT<T>::scal(a.recG, k), RecT<T>::tab(a.recG, k, NT), NT, nx, ny, ix, iy, iz) * it;
+// metadata of one DVM cell
+template <typename T, int NC>
+struct CellMeta {
+    int kd[2 * NC], rf[2 * NC], n2[2 * NC];
+    T it;
+    T S[2 * NC][NC];
+    T wall[2 * NC];
+};
+
+template <typename T, int NC>
+__device__ __forceinline__ void load_meta(const SweepArgs& a, int k, CellMeta<T, NC>& m) {
     const T* So = pick<T>(a.SoV, a.SoVf) + (long long)k * 18;
+    const T* rw = pick<T>(a.rho_w, a.rho_wf) + (long long)k * 6;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        const int kl = kind[2 * d], kh = kind[2 * d + 1];
-        // own limited slope (both neighbours DVM), else 0; unused neighbour values equal fc
-        const T own = (kl == SK_DVM && kh == SK_DVM) ? minmod_t<T>(fc - st[d].lo, st[d].hi - fc) : T(0);
+    for (int s = 0; s < 2 * NC; ++s) {
+        m.kd[s] = __ldg(a.kind + (long long)k * 6 + s);
+        m.rf[s] = __ldg(a.ref + (long long)k * 6 + s);
+        m.n2[s] = __ldg(a.nb2 + (long long)k * 6 + s);
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int s = 2 * d + side;
-            const int kd = side ? kh : kl;
-            if (kd == SK_NONE) continue;
-            const T xn = normal_speed<NC, T>(x0, x1, x2, So + 3 * s);
-            const T hs = side ? T(0.5) : T(-0.5);
-            T fin;
-            if (kd == SK_DVM) {
-                const T fn = side ? st[d].hi : st[d].lo;
-                const bool has2 = nb2[s] >= 0;
-                const T sn = has2 ? (side ? minmod_t<T>(fn - fc, st[d].hi2 - fn) : minmod_t<T>(fn - st[d].lo2, fc - fn))
-                                  : T(0);
-                fin = fn - hs * sn;
-            } else if (kd == SK_GHOST) {
-                fin = eval_recT<T>(RecT<T>::scal(a.recGhost, ref[s]), RecT<T>::tab(a.recGhost, ref[s], NT), NT, nx, ny,
-                                   ix, iy, iz);
-            } else if (kd == SK_FAR) {
-                fin = eval_recT<T>(RecT<T>::scal(a.recBC, ref[s]), RecT<T>::tab(a.recBC, ref[s], NT), NT, nx, ny, ix,
-                                   iy, iz);
-            } else {
-                fin = pick<T>(a.rho_w, a.rho_wf)[(long long)k * 6 + s] *
-                      eval_recT<T>(RecT<T>::scal(a.recBC, ref[s]), RecT<T>::tab(a.recBC, ref[s], NT), NT, nx, ny, ix,
-                                   iy, iz);
-            }
-            const bool out = xn > T(0);
-            den += out ? xn : T(0);
-            num -= out ? xn * hs * own : xn * fin;
-        }
+        for (int q = 0; q < NC; ++q) m.S[s][q] = __ldg(So + 3 * s + q);
+        m.wall[s] = __ldg(rw + s);
     }
-    stT<T, S>(fk, num / den);
+    m.it = __ldg(pick<T>(a.itau, a.itauf) + k);
 }
 
-template <typename S, typename T, int NC, int G>
+template <typename S, typename T, int NC, int VPT, int CB>
+__device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
+                                             const Vel<T, VPT>& V) {
+    const long long Nv = a.vg.Nv;
+    const int NT = a.vg.NT, nx = a.vg.nx, ny = a.vg.ny;
+    CellMeta<T, NC> m[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+        if (kon[b]) load_meta<T, NC>(a, kk[b], m[b]);
+    // ---- gather
+    T fc[CB][VPT];
+    T lo[CB][NC][VPT], hi[CB][NC][VPT], lo2[CB][NC][VPT], hi2[CB][NC][VPT];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+        if (!kon[b]) continue;
+        const S* fk = f + (long long)kk[b] * Nv;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) fc[b][u] = V.on[u] ? ldT<T, S>(fk + V.v[u]) : T(0);
+#pragma unroll
+        for (int d = 0; d < NC; ++d) {
+            const bool dl = m[b].kd[2 * d] == SK_DVM, dh = m[b].kd[2 * d + 1] == SK_DVM;
+            const bool dl2 = dl && m[b].n2[2 * d] >= 0, dh2 = dh && m[b].n2[2 * d + 1] >= 0;
+            const S* pl = f + (long long)m[b].rf[2 * d] * Nv;
+            const S* ph = f + (long long)m[b].rf[2 * d + 1] * Nv;
+            const S* pl2 = f + (long long)m[b].n2[2 * d] * Nv;
+            const S* ph2 = f + (long long)m[b].n2[2 * d + 1] * Nv;
+#pragma unroll
+            for (int u = 0; u < VPT; ++u) {
+                const bool on = V.on[u];
+                lo[b][d][u] = (dl && on) ? ldT<T, S>(pl + V.v[u]) : fc[b][u];
+                hi[b][d][u] = (dh && on) ? ldT<T, S>(ph + V.v[u]) : fc[b][u];
+                lo2[b][d][u] = (dl2 && on) ? ldT<T, S>(pl2 + V.v[u]) : lo[b][d][u];
+                hi2[b][d][u] = (dh2 && on) ? ldT<T, S>(ph2 + V.v[u]) : hi[b][d][u];
+            }
+        }
+    }
+    // ---- compute and store
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+        if (!kon[b]) continue;
+        const int k = kk[b];
+        const T* gs = RecT<T>::scal(a.recG, k);
+        const T* gt = RecT<T>::tab(a.recG, k, NT);
+        T den[VPT], num[VPT];
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            den[u] = m[b].it;
+            num[u] = eval_recT<T>(gs, gt, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]) * m[b].it;
+        }
+#pragma unroll
+        for (int d = 0; d < NC; ++d) {
+            const int kl = m[b].kd[2 * d], kh = m[b].kd[2 * d + 1];
+            if (kl == SK_NONE && kh == SK_NONE) continue;
+            const bool both = kl == SK_DVM && kh == SK_DVM;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int s = 2 * d + side;
+                const int kq = side ? kh : kl;
+                if (kq == SK_NONE) continue;
+                const T hs = side ? T(0.5) : T(-0.5);
+                const bool has2 = m[b].n2[s] >= 0;
+                const T* bs = nullptr;
+                const T* bt = nullptr;
+                T scale = T(1);
+                if (kq == SK_GHOST) {
+                    bs = RecT<T>::scal(a.recGhost, m[b].rf[s]);
+                    bt = RecT<T>::tab(a.recGhost, m[b].rf[s], NT);
+                } else if (kq == SK_FAR || kq == SK_WALL) {
+                    bs = RecT<T>::scal(a.recBC, m[b].rf[s]);
+                    bt = RecT<T>::tab(a.recBC, m[b].rf[s], NT);
+                    if (kq == SK_WALL) scale = m[b].wall[s];
+                }
+#pragma unroll
+                for (int u = 0; u < VPT; ++u) {
+                    T xn = V.x0[u] * m[b].S[s][0];
+                    if (NC >= 2) xn += V.x1[u] * m[b].S[s][NC >= 2 ? 1 : 0];
+                    if (NC >= 3) xn += V.x2[u] * m[b].S[s][NC >= 3 ? 2 : 0];
+                    const T own = both ? minmod_t<T>(fc[b][u] - lo[b][d][u], hi[b][d][u] - fc[b][u]) : T(0);
+                    T fin;
+                    if (kq == SK_DVM) {
+                        const T fn = side ? hi[b][d][u] : lo[b][d][u];
+                        const T sn = has2 ? (side ? minmod_t<T>(fn - fc[b][u], hi2[b][d][u] - fn)
+                                                  : minmod_t<T>(fn - lo2[b][d][u], fc[b][u] - fn))
+                                          : T(0);
+                        fin = fn - hs * sn;
+                    } else {
+                        fin = scale * eval_recT<T>(bs, bt, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
+                    }
+                    const bool out = xn > T(0);
+                    den[u] += out ? xn : T(0);
+                    num[u] -= out ? xn * hs * own : xn * fin;
+                }
+            }
+        }
+        S* fk = f + (long long)k * Nv;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u)
+            if (V.on[u]) stT<T, S>(fk + V.v[u], num[u] / den[u]);
+    }
+}
+
+template <typename S, typename T, int NC, int G, int VPT, int CB>
 __global__ void __launch_bounds__(32 * G) k_sweep(SweepArgs a, S* __restrict__ f, int pass) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long v = (long long)blockIdx.x * 32 + lane;
-    const bool active = v < a.vg.Nv;
-    int ix = 0, iy = 0, iz = 0;
-    if (active) vsplit(v, a.vg.nx, a.vg.ny, ix, iy, iz);
-    const T x0 = (T)a.vg.xi[ix], x1 = (T)a.vg.xi[a.vg.nx + iy], x2 = (T)a.vg.xi[a.vg.nx + a.vg.ny + iz];
+    Vel<T, VPT> V;
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        V.v[u] = (long long)blockIdx.x * (32 * VPT) + 32 * u + lane;
+        V.on[u] = V.v[u] < a.vg.Nv;
+        int ix = 0, iy = 0, iz = 0;
+        if (V.on[u]) vsplit(V.v[u], a.vg.nx, a.vg.ny, ix, iy, iz);
+        V.ix[u] = ix; V.iy[u] = iy; V.iz[u] = iz;
+        V.x0[u] = (T)a.vg.xi[ix];
+        V.x1[u] = (T)a.vg.xi[a.vg.nx + iy];
+        V.x2[u] = (T)a.vg.xi[a.vg.nx + a.vg.ny + iz];
+    }
     for (int hh = 0; hh < a.H; ++hh) {
         const int h = pass ? (a.H - 1 - hh) : hh;
-        const int kb = a.hp_off[h], ke = a.hp_off[h + 1];
-        if (active) {
-            if (pass == 0) {
-                for (int k = kb + w; k < ke; k += G) update_point<S, T, NC>(a, f, k, v, ix, iy, iz, x0, x1, x2);
-            } else {
-                for (int k = ke - 1 - w; k >= kb; k -= G) update_point<S, T, NC>(a, f, k, v, ix, iy, iz, x0, x1, x2);
+        const int kb = __ldg(a.hp_off + h), ke = __ldg(a.hp_off + h + 1);
+        const int n = ke - kb;
+        // warp w takes the cells w, w+G, w+2G, ... (in reverse order for the backward pass)
+        for (int i0 = w; i0 < n; i0 += G * CB) {
+            int kk[CB];
+            bool kon[CB];
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int i = i0 + b * G;
+                kon[b] = i < n;
+                kk[b] = pass ? (ke - 1 - i) : (kb + i);
             }
+            update_cells<S, T, NC, VPT, CB>(a, f, kk, kon, V);
         }
         if (G > 1) __syncthreads();
     }
 }
 
-template <typename S, typename T, int G>
+template <typename S, typename T, int G, int VPT, int CB>
 static void sweep_t(gsis_ctx* c, const SweepArgs& a, int pass) {
-    const unsigned blocks = (unsigned)((c->vg.Nv + 31) / 32);
+    const unsigned blocks = (unsigned)((c->vg.Nv + 32 * VPT - 1) / (32 * VPT));
     S* f = (S*)c->f;
     switch (c->normal_components) {
-        case 1: k_sweep<S, T, 1, G><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass); break;
-        case 2: k_sweep<S, T, 2, G><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass); break;
-        default: k_sweep<S, T, 3, G><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass); break;
+        case 1: k_sweep<S, T, 1, G, VPT, CB><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass); break;
+        case 2: k_sweep<S, T, 2, G, VPT, CB><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass); break;
+        default: k_sweep<S, T, 3, G, VPT, CB><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass); break;
     }
 }
 
@@ -193,10 +260,10 @@ void launch_sweep(gsis_ctx* c, int pass) {
     a.recBC = c->recBC;
     a.vg = c->vg;
     switch (c->p.vdf_dtype) {
-        case GSIS_F64: sweep_t<double, double, 2>(c, a, pass); break;
-        case GSIS_F32: sweep_t<float, float, 4>(c, a, pass); break;
-        case GSIS_BF16: sweep_t<__nv_bfloat16, float, 4>(c, a, pass); break;
-        default: sweep_t<__half, float, 4>(c, a, pass); break;
+        case GSIS_F64: sweep_t<double, double, 2, 1, 2>(c, a, pass); break;
+        case GSIS_F32: sweep_t<float, float, 4, 2, 2>(c, a, pass); break;
+        case GSIS_BF16: sweep_t<__nv_bfloat16, float, 4, 2, 2>(c, a, pass); break;
+        default: sweep_t<__half, float, 4, 2, 2>(c, a, pass); break;
     }
     c->launches++;
     c->sweep_launches++;

@@ -246,3 +246,18 @@ def test_no_dvm_cells_is_pure_navier_stokes():
         U = macro_solve(s2.geo, s2.bc_state, U, z, zq, s2.mu0, s2.omega, case.cfl, case.k_sub, case.macro_steps,
                         case.dt, U.copy())
     assert np.max(np.abs(U_to_prim(U) - s.W)) < 1e-14
+
+
+def test_wall_kinetic_flux_of_gas_at_rest():
+    """A Maxwellian at rest at the wall temperature meets a diffuse wall: the
+    re-emitted half-range equals the incoming one, so the face distribution is
+    that Maxwellian; the wall flux is the pressure rho T_w S, no mass, no energy."""
+    vg = M.VelocityGrid((32, 32, 32), (-8, -8, -8), (8, 8, 8))
+    rho, Tw = 1.7, 1.3
+    f = M.maxwellian(rho, [0.0, 0.0, 0.0], Tw, vg.xi)
+    Mw = M.maxwellian(1.0, [0.0, 0.0, 0.0], Tw, vg.xi)
+    S = np.array([-0.6, -0.8, 0.0]) * 0.05
+    F = K.wall_kinetic_flux(f, S, Mw, vg)
+    assert abs(F[0]) < 1e-14
+    assert np.allclose(F[1:4], rho * Tw * S, rtol=1e-10, atol=1e-14)
+    assert abs(F[4]) < 1e-13
