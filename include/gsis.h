@@ -97,6 +97,8 @@ typedef struct {
                                    macro_steps steps, stopping when epsilon between blocks < tol;
                                    0 = start from W0 directly                                     */
     unsigned long long spin_limit; /* iteration limit of any bounded device wait (0 = default)    */
+    double relax;         /* weight of the synthetic correction: W^{n+1} = W^{n+1/2} + relax *
+                             (W_synthetic - W^{n+1/2}); 1 = the plain scheme, (0, 1]; 0 is read as 1 */
 } gsis_params;
 
 /* Structured mesh: cells (i, j, k), flat index c = i + ni*(j + nj*k).
@@ -189,6 +191,43 @@ gsis_status gsis_get_vdf(gsis_ctx* ctx, double* dst, int* cells, long long capac
  * Used to compare with a reference whose threshold decisions are taken
  * elsewhere.  Must be called before the first gsis_iterate. */
 gsis_status gsis_debug_set_region(gsis_ctx* ctx, const uint8_t* flags);
+
+/* Advance n independent solves together by `iterations` GSIS iterations each
+ * (the batched form: many small solves, e.g. 1D shocks with uneven meshes,
+ * velocity grids and VDF storage types, in one device pass per iteration).
+ * Per iteration the per-solve stages run for every solve, the kinetic sweeps
+ * of ALL solves run in one persistent launch that draws (solve, velocity
+ * tile) work items from a device counter, and the synthetic solves of all
+ * meshes up to 4096 cells run in one launch (one CTA each); one iteration of
+ * the whole batch is recorded once into a CUDA graph and replayed.  The tile
+ * shape of the persistent sweep is picked by timing the candidates on the
+ * batch itself (on a snapshot of the VDFs, restored afterwards; skipped
+ * without memory for the snapshot) and cached per batch shape for the life
+ * of the process.  Results are identical to iterating each solve alone.
+ *
+ * ctxs: n distinct contexts on one device, each with mesh and velocity grid
+ *       set, adaptive = 0 (or a region forced by gsis_debug_set_region);
+ *       contexts not yet started are started (presolve included).
+ * iterations: >= 0; exactly this many iterations run (no early stop: the
+ *       residual is only read at the end); reports[i] (may be NULL) receives
+ *       the residual of the last iteration and the sizes of solve i.
+ * The batch runs on ctxs[0]'s stream (a private stream when that is the
+ * legacy default stream) after synchronising every context's stream, and
+ * synchronises before returning.  The recorded graph is kept for the same
+ * ordered context list and re-recorded when a context was iterated alone in
+ * between; gsis_free of any member drops it.
+ * Errors: GSIS_ERR_ARG (NULL, n <= 0, duplicates, mixed devices),
+ * GSIS_ERR_UNSUPPORTED (adaptive context), GSIS_ERR_STATE, GSIS_ERR_OOM,
+ * GSIS_ERR_CUDA; GSIS_ERR_NONFINITE if a solve ends non-finite (that context
+ * becomes unusable).  The paper has no counterpart: it runs one solve at a
+ * time. */
+gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_report* reports);
+
+/* Human-readable description of the recorded batch plan for this ordered
+ * context list (work items, autotuned tile shape and the timings of every
+ * candidate, grid, graph nodes), or "" if none.  The string lives until the
+ * next call from the same thread. */
+const char* gsis_batch_info(gsis_ctx** ctxs, int n);
 
 /* Human-readable description of the last error on this context (never NULL). */
 const char* gsis_last_error(const gsis_ctx* ctx);

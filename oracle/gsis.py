@@ -169,7 +169,7 @@ class OracleSolver:
     def kinetic_inputs(self):
         W = self.W
         vg = self.vg
-        gt, tau, ghost, ff, mw, rho_w = {}, {}, {}, {}, {}, {}
+        gt, tau, ghost, ff, mw = {}, {}, {}, {}, {}
         for c in range(self.N):
             if not self.dvm[c]:
                 continue
@@ -196,13 +196,7 @@ class OracleSolver:
                 ff[s] = M.corrected_maxwellian(st[0], st[1:4], st[4], vg)
             elif self.case.mesh.bc_type[s] == BC_WALL:
                 mw[s] = M.maxwellian(1.0, np.zeros(3), st[4], vg.xi)
-        for c in range(self.N):
-            if not self.dvm[c]:
-                continue
-            for sd in self.topo.sides[c]:
-                if sd.nbr < 0 and sd.bc == BC_WALL:
-                    rho_w[(c, sd.bc_side)] = wall_density(self.f[c], sd.S_out, mw[sd.bc_side], vg)
-        return KineticInputs(gt, tau, ghost, ff, mw, rho_w)
+        return KineticInputs(gt, tau, ghost, ff, mw)
 
     def wall_correction(self, W_half, mw):
         """Per wall face (order of the wall faces of the macro geometry): for a
@@ -250,6 +244,8 @@ class OracleSolver:
                         self.mu0, self.omega, case.cfl, case.k_sub, case.macro_steps,
                         case.dt, prim_to_U(self.W), bcorr)
         W_new = U_to_prim(U)
+        if case.relax != 1.0:
+            W_new = W_half + case.relax * (W_new - W_half)
         for c in range(self.N):
             if self.dvm[c]:
                 a = M.corrected_maxwellian(W_new[c, 0], W_new[c, 1:4], W_new[c, 4], vg)

@@ -19,8 +19,9 @@ reading taken (stated once, used everywhere):
 Boundary and interface face values for incoming velocities (xi . n < 0):
 far field -> conservation-corrected Maxwellian M~ of the boundary state (so a
 uniform stream is an exact fixed point); diffuse wall -> rho_w M(0, T_w) with
-rho_w from zero net mass flux through the face, using the outgoing half of f at
-the start of the step; NS neighbour -> Grad-13 VDF of Eq. G13_VDF from the
+rho_w from zero net mass flux through the face, using the outgoing half of the
+cell's latest f (its value before its own update in the current pass, like
+every other explicit term); NS neighbour -> Grad-13 VDF of Eq. G13_VDF from the
 neighbour's W and NSF stress/heat flux, conservation-corrected to its W.
 """
 import numpy as np
@@ -36,13 +37,12 @@ def minmod(a, b):
 class KineticInputs:
     """Per-step inputs frozen at the start of the kinetic step."""
 
-    def __init__(self, gt, tau, ghost, ff_maxwellian, wall_maxwellian, rho_w):
+    def __init__(self, gt, tau, ghost, ff_maxwellian, wall_maxwellian):
         self.gt = gt                    # {cell: g~ vector} for DVM cells
         self.tau = tau                  # {cell: tau}
         self.ghost = ghost              # {cell: Grad-13 VDF} for NS cells next to DVM cells
         self.ff = ff_maxwellian         # {bc_side: Maxwellian of the far-field state}
         self.mw = wall_maxwellian       # {bc_side: M(0, T_w) with unit density}
-        self.rho_w = rho_w              # {(cell, bc_side): wall density}
 
 
 def wall_density(f_cell, S_out, Mw, vg):
@@ -100,7 +100,7 @@ def update_cell(topo, vg, f, dvm, inp, c):
         elif sd.bc == BC_FARFIELD:
             fin = inp.ff[sd.bc_side]
         elif sd.bc == BC_WALL:
-            fin = inp.rho_w[(c, sd.bc_side)] * inp.mw[sd.bc_side]
+            fin = wall_density(f[c], sd.S_out, inp.mw[sd.bc_side], vg) * inp.mw[sd.bc_side]
         else:
             raise ValueError("unknown boundary")
         num = num - np.where(out, 0.0, xn * fin)

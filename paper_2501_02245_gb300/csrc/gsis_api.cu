@@ -3,10 +3,13 @@
 // adaptive start).  Every numerical step runs in the kernels of the other
 // translation units; this file only moves descriptors and launches them.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
-#include "gsis_device.cuh"
+#include "sweep_device.cuh"
 
 using namespace gsis;
 
@@ -190,8 +193,53 @@ gsis_status start(gsis_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------- one GSIS iteration
-gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
+// The iteration is split in stages so that the batched driver can record the
+// same launches for many solves into one CUDA graph.
+
+// 1. reference distributions, tau, interface ghosts, wall densities
+void stage_cell_eq(gsis_ctx* c) {
+    if (c->n_ghost > 0) {
+        launch_nsf(c, c->W, c->nsf);
+        launch_ghost_records(c);
+    }
+    launch_cell_eq(c);
+}
+
+// 3. moments of f^{n+1/2} -> W^{n+1/2}, wall fluxes, HoT; set up the synthetic solve
+void stage_moments(gsis_ctx* c) {
     const int N = c->m.N;
+    launch_moments(c, c->W, 0, c->momh);
+    launch_wall_flux(c);
+    launch_half_state(c);
+    launch_nsf(c, c->Wh, c->nsf);   // leaves the gradients of W^{n+1/2} in gu, gT
+    launch_hot(c);
+    if (c->has_wall) launch_wall_corr(c);
+    launch_prim_to_cons(c, c->Wh, c->U);
+    launch_prim_to_cons(c, c->W, c->Un);
+    cudaMemcpyAsync(c->Wm, c->Wh, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+}
+
+// 6. under-relaxation of the synthetic correction and the residual between
+// W^{n+1} (Wm) and W^n (W); with fixed_buffers the new state is copied into W
+// (the buffers a recorded graph refers to stay the same), else swapped.
+void stage_residual(gsis_ctx* c, bool fixed_buffers) {
+    if (c->p.relax != 1.0) launch_blend(c, c->Wh, c->p.relax, c->Wm);
+    launch_eps(c, c->Wm, c->W);
+    if (fixed_buffers) {
+        cudaMemcpyAsync(c->W, c->Wm, (size_t)c->m.N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+        cudaMemcpyAsync(c->h_eps, c->eps_buf, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        std::swap(c->W, c->Wm);   // W = W^{n+1}
+    }
+}
+
+// 5. Eq. updatef in DVM cells, and moments of f^{n+1} about u^{n+1}
+void stage_correct(gsis_ctx* c) {
+    launch_correction_records(c);
+    launch_moments(c, c->W, 1, c->mom);
+}
+
+gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     if (c->p.adaptive && c->iteration == c->p.adapt_every && !c->have_forced) {
         used[GSIS_PH_ADAPT] = true;
         phase_begin(c, GSIS_PH_ADAPT);
@@ -200,51 +248,33 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
         launch_moments(c, c->W, 0, c->mom);
         phase_end(c, GSIS_PH_ADAPT);
     }
-    // 1. reference distributions, tau, interface ghosts, wall densities
     used[GSIS_PH_CELLEQ] = true;
     phase_begin(c, GSIS_PH_CELLEQ);
-    if (c->n_ghost > 0) {
-        launch_nsf(c, c->W, c->nsf);
-        launch_ghost_records(c);
-    }
-    launch_cell_eq(c);
+    stage_cell_eq(c);
     phase_end(c, GSIS_PH_CELLEQ);
     // 2. kinetic step: forward and backward Gauss-Seidel passes
     used[GSIS_PH_SWEEP] = true;
     phase_begin(c, GSIS_PH_SWEEP);
     launch_sweep(c, 0);
+    launch_wall_rho(c);
     launch_sweep(c, 1);
     phase_end(c, GSIS_PH_SWEEP);
-    // 3. moments of f^{n+1/2}, W^{n+1/2}, HoT
     used[GSIS_PH_MOMENTS] = true;
     phase_begin(c, GSIS_PH_MOMENTS);
-    launch_moments(c, c->W, 0, c->momh);
-    launch_wall_flux(c);
-    launch_half_state(c);
-    launch_nsf(c, c->Wh, c->nsf);   // leaves the gradients of W^{n+1/2} in gu, gT
-    launch_hot(c);
-    if (c->has_wall) launch_wall_corr(c);
+    stage_moments(c);
     phase_end(c, GSIS_PH_MOMENTS);
     // 4. synthetic solve over all cells from W^{n+1/2}
     used[GSIS_PH_MACRO] = true;
     phase_begin(c, GSIS_PH_MACRO);
-    launch_prim_to_cons(c, c->Wh, c->U);
-    launch_prim_to_cons(c, c->W, c->Un);
-    cudaMemcpyAsync(c->Wm, c->Wh, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0);
     phase_end(c, GSIS_PH_MACRO);
-    // 6. residual between W^{n+1} (Wm) and W^n (W)
     used[GSIS_PH_RESID] = true;
     phase_begin(c, GSIS_PH_RESID);
-    launch_eps(c, c->Wm, c->W);
-    cudaMemcpyAsync(c->h_eps, c->eps_buf, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    stage_residual(c, false);
     phase_end(c, GSIS_PH_RESID);
-    std::swap(c->W, c->Wm);   // W = W^{n+1}
-    // 5. Eq. updatef in DVM cells, and moments of f^{n+1} about u^{n+1}
     used[GSIS_PH_CORRECT] = true;
     phase_begin(c, GSIS_PH_CORRECT);
-    launch_correction_records(c);
-    launch_moments(c, c->W, 1, c->mom);
+    stage_correct(c);
     phase_end(c, GSIS_PH_CORRECT);
     if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "GSIS iteration")) return GSIS_ERR_CUDA;
     if (!cuda_ok(c, cudaGetLastError(), "kernel launch")) return GSIS_ERR_CUDA;
@@ -254,6 +284,270 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     *eps_out = c->h_eps[0];
     c->iteration++;
     return GSIS_OK;
+}
+
+
+// ---------------------------------------------------------------------------- batched solves
+// Many independent solves advanced together: per GSIS iteration, the
+// per-solve stages of every solve, ONE persistent sweep launch over all
+// (solve, velocity tile) items, and ONE fused synthetic-solve launch (one CTA
+// per solve), recorded once into a CUDA graph and replayed.  The graph refers
+// to fixed buffers, so in batched mode the new state is copied into W instead
+// of swapping the W / Wm buffers.
+struct BatchPlan {
+    std::vector<gsis_ctx*> ctxs;
+    std::vector<const double*> W_at_capture;   // W buffer of each solve when the graph was recorded
+    gsis_ctx* owner = nullptr;                  // plan allocations go through this context
+    cudaStream_t stream = nullptr;              // capture and replay stream
+    bool own_stream = false;                    // created here (the solves run on the legacy default stream)
+    BatchSolve* d_solves = nullptr;
+    int2* d_items = nullptr;
+    int n_items = 0;
+    int* d_ticket = nullptr;
+    MacroJob* d_jobs = nullptr;
+    int n_jobs = 0;
+    std::vector<int> big;                       // solves too large for the fused synthetic-solve kernel
+    int nc = 1, shape = 1, grid = 0;
+    bool tuned = false;
+    std::vector<double> tune_ms;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches_per_iter = 0;
+    std::string info;
+};
+
+std::mutex& batch_mutex() {
+    static std::mutex m;
+    return m;
+}
+std::map<std::vector<gsis_ctx*>, BatchPlan*>& batch_plans() {
+    static std::map<std::vector<gsis_ctx*>, BatchPlan*> m;
+    return m;
+}
+std::map<std::string, int>& tuned_shapes() {   // autotuner cache: batch signature -> tile shape
+    static std::map<std::string, int> m;
+    return m;
+}
+
+void destroy_plan(BatchPlan* P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->own_stream && P->stream) {
+        cudaStreamSynchronize(P->stream);
+        cudaStreamDestroy(P->stream);
+    }
+    gsis_ctx* o = P->owner;
+    for (void* p : {(void*)P->d_solves, (void*)P->d_items, (void*)P->d_ticket, (void*)P->d_jobs})
+        if (p) dev_free(o, p);
+    delete P;
+}
+
+// Items of the batch for a tile shape: all velocity tiles of each solve, the
+// solves with the most DVM cells (the longest items) first.
+std::vector<int2> batch_items(const std::vector<gsis_ctx*>& cs, int shape) {
+    const int vt = batch_shape_vtile(shape);
+    std::vector<int> order(cs.size());
+    for (size_t i = 0; i < cs.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cs[a]->Nd > cs[b]->Nd; });
+    std::vector<int2> items;
+    for (int s : order) {
+        if (cs[s]->Nd == 0) continue;
+        const long long nt = (cs[s]->vg.Nv + vt - 1) / vt;
+        for (long long t = 0; t < nt; ++t) items.push_back(make_int2(s, (int)t));
+    }
+    return items;
+}
+
+std::string batch_signature(const std::vector<gsis_ctx*>& cs, int nc) {
+    std::vector<std::string> parts;
+    for (gsis_ctx* c : cs)
+        parts.push_back(std::to_string(c->Nd) + "x" + std::to_string(c->vg.Nv) + "x" + std::to_string(c->p.vdf_dtype) +
+                        "x" + std::to_string(c->m.H));
+    std::sort(parts.begin(), parts.end());
+    std::string s = "nc" + std::to_string(nc);
+    for (auto& p : parts) s += "|" + p;
+    return s;
+}
+
+// Autotuner: time every tile shape on the batch itself (one warm-up and two
+// timed launches each) on a snapshot of the VDFs, restore them, keep the
+// fastest.  Cached per batch signature for the life of the process.
+gsis_status tune_batch(BatchPlan* P) {
+    gsis_ctx* o = P->owner;
+    const std::string sig = batch_signature(P->ctxs, P->nc);
+    auto hit = tuned_shapes().find(sig);
+    if (hit != tuned_shapes().end()) {
+        P->shape = hit->second;
+        P->tuned = true;
+        return GSIS_OK;
+    }
+    std::vector<void*> snap(P->ctxs.size(), nullptr);
+    std::vector<size_t> bytes(P->ctxs.size(), 0);
+    bool ok = true;
+    for (size_t i = 0; i < P->ctxs.size() && ok; ++i) {
+        gsis_ctx* c = P->ctxs[i];
+        bytes[i] = (size_t)c->Nd * c->vg.Nv * vdf_elem_bytes(c->p.vdf_dtype);
+        if (bytes[i] == 0) continue;
+        snap[i] = dev_alloc(o, bytes[i]);
+        if (!snap[i]) { ok = false; break; }
+        cudaMemcpyAsync(snap[i], c->f, bytes[i], cudaMemcpyDeviceToDevice, P->stream);
+    }
+    if (!ok) {   // not enough memory for a snapshot: keep the default shape
+        for (void* p : snap) if (p) dev_free(o, p);
+        P->shape = 1;
+        P->tuned = false;
+        return GSIS_OK;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int ns = batch_num_shapes();
+    P->tune_ms.assign(ns, 0.0);
+    int best = 1;
+    double best_ms = 1e300;
+    int2* d_it = nullptr;
+    for (int sh = 0; sh < ns; ++sh) {
+        std::vector<int2> it = batch_items(P->ctxs, sh);
+        d_it = (int2*)dev_alloc(o, std::max<size_t>(1, it.size()) * sizeof(int2));
+        if (!d_it) break;
+        cudaMemcpyAsync(d_it, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, P->stream);
+        const int grid = batch_grid(sh, P->nc);
+        launch_sweep_batch(sh, P->nc, P->d_solves, d_it, (int)it.size(), P->d_ticket, grid, P->stream, 0, 2);
+        cudaEventRecord(e0, P->stream);
+        for (int r = 0; r < 2; ++r)
+            launch_sweep_batch(sh, P->nc, P->d_solves, d_it, (int)it.size(), P->d_ticket, grid, P->stream, 0, 2);
+        cudaEventRecord(e1, P->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        P->tune_ms[sh] = ms / 2.0;
+        if (ms / 2.0 < best_ms) { best_ms = ms / 2.0; best = sh; }
+        dev_free(o, d_it);
+        d_it = nullptr;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t i = 0; i < P->ctxs.size(); ++i)
+        if (snap[i]) cudaMemcpyAsync(P->ctxs[i]->f, snap[i], bytes[i], cudaMemcpyDeviceToDevice, P->stream);
+    cudaStreamSynchronize(P->stream);
+    for (void* p : snap) if (p) dev_free(o, p);
+    if (!cuda_ok(o, cudaGetLastError(), "batch autotuning")) return GSIS_ERR_CUDA;
+    P->shape = best;
+    P->tuned = true;
+    tuned_shapes()[sig] = best;
+    return GSIS_OK;
+}
+
+gsis_status build_plan(BatchPlan* P) {
+    gsis_ctx* o = P->owner;
+    const int n = (int)P->ctxs.size();
+    for (gsis_ctx* c : P->ctxs) stage_cell_eq(c);   // valid records for the autotuning sweeps
+    for (gsis_ctx* c : P->ctxs)
+        if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "batch set-up")) return GSIS_ERR_CUDA;
+    std::vector<BatchSolve> hs(n);
+    std::vector<MacroJob> jobs;
+    P->nc = 1;
+    for (int i = 0; i < n; ++i) {
+        gsis_ctx* c = P->ctxs[i];
+        hs[i].a = sweep_args(c);
+        hs[i].f = c->f;
+        hs[i].dtype = c->p.vdf_dtype;
+        if (c->normal_components > 1) P->nc = 3;
+        if (c->m.N <= MACRO_FUSED_MAX_CELLS)
+            jobs.push_back(macro_job(c, c->p.macro_steps, c->p.dt > 0.0));
+        else
+            P->big.push_back(i);
+        P->W_at_capture.push_back(c->W);
+    }
+    P->n_jobs = (int)jobs.size();
+    P->d_solves = (BatchSolve*)dev_alloc(o, n * sizeof(BatchSolve));
+    P->d_ticket = (int*)dev_alloc(o, sizeof(int));
+    P->d_jobs = (MacroJob*)dev_alloc(o, std::max(1, P->n_jobs) * sizeof(MacroJob));
+    if (!P->d_solves || !P->d_ticket || !P->d_jobs) return set_err(o, GSIS_ERR_OOM, "batch plan allocation failed");
+    cudaMemcpyAsync(P->d_solves, hs.data(), n * sizeof(BatchSolve), cudaMemcpyHostToDevice, P->stream);
+    if (P->n_jobs)
+        cudaMemcpyAsync(P->d_jobs, jobs.data(), jobs.size() * sizeof(MacroJob), cudaMemcpyHostToDevice, P->stream);
+    if (!cuda_ok(o, cudaStreamSynchronize(P->stream), "batch plan upload")) return GSIS_ERR_CUDA;
+    gsis_status st = tune_batch(P);
+    if (st != GSIS_OK) return st;
+    std::vector<int2> items = batch_items(P->ctxs, P->shape);
+    P->n_items = (int)items.size();
+    P->d_items = (int2*)dev_alloc(o, std::max<size_t>(1, items.size()) * sizeof(int2));
+    if (!P->d_items) return set_err(o, GSIS_ERR_OOM, "batch item list allocation failed");
+    cudaMemcpyAsync(P->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, P->stream);
+    P->grid = batch_grid(P->shape, P->nc);
+    if (!cuda_ok(o, cudaStreamSynchronize(P->stream), "batch item upload")) return GSIS_ERR_CUDA;
+    // record one GSIS iteration of every solve
+    std::vector<cudaStream_t> saved(n);
+    long long l0 = 0;
+    for (int i = 0; i < n; ++i) {
+        saved[i] = P->ctxs[i]->stream;
+        P->ctxs[i]->stream = P->stream;
+        l0 += P->ctxs[i]->launches;
+    }
+    cudaError_t ce = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        for (gsis_ctx* c : P->ctxs) stage_cell_eq(c);
+        bool walls = false;
+        for (gsis_ctx* c : P->ctxs) walls = walls || c->has_wall;
+        if (walls) {   // wall densities refreshed between the passes
+            launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
+                               0, 1);
+            for (gsis_ctx* c : P->ctxs) launch_wall_rho(c);
+            launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
+                               1, 2);
+        } else {
+            launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
+                               0, 2);
+        }
+        for (gsis_ctx* c : P->ctxs) stage_moments(c);
+        if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream);
+        for (int i : P->big) {
+            gsis_ctx* c = P->ctxs[i];
+            macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0);
+        }
+        for (gsis_ctx* c : P->ctxs) {
+            stage_residual(c, true);
+            stage_correct(c);
+        }
+        ce = cudaStreamEndCapture(P->stream, &P->graph);
+    }
+    long long l1 = 0;
+    for (int i = 0; i < n; ++i) {
+        l1 += P->ctxs[i]->launches;
+        P->ctxs[i]->stream = saved[i];
+    }
+    if (ce != cudaSuccess) return set_err(o, GSIS_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&P->exec, P->graph, 0);
+    if (ce != cudaSuccess)
+        return set_err(o, GSIS_ERR_CUDA, std::string("batch graph instantiation: ") + cudaGetErrorString(ce));
+    P->launches_per_iter = (l1 - l0) + 1 + (P->n_jobs ? 1 : 0);
+    size_t nodes = 0;
+    cudaGraphGetNodes(P->graph, nullptr, &nodes);
+    P->info = std::string("solves=") + std::to_string(n) + " items=" + std::to_string(P->n_items) +
+              " tile=" + batch_shape_name(P->shape) + (P->tuned ? " (autotuned" : " (default") +
+              ") grid=" + std::to_string(P->grid) + " fused_macro=" + std::to_string(P->n_jobs) +
+              " graph_nodes=" + std::to_string(nodes) + " kernels_per_iteration=" + std::to_string(P->launches_per_iter);
+    if (!P->tune_ms.empty()) {
+        P->info += " tune_ms=";
+        for (int sh = 0; sh < (int)P->tune_ms.size(); ++sh)
+            P->info += std::string(sh ? "," : "") + batch_shape_name(sh) + ":" + std::to_string(P->tune_ms[sh]);
+    }
+    return GSIS_OK;
+}
+
+void drop_plans_with(gsis_ctx* c) {
+    std::lock_guard<std::mutex> lk(batch_mutex());
+    auto& m = batch_plans();
+    for (auto it = m.begin(); it != m.end();) {
+        if (std::find(it->first.begin(), it->first.end(), c) != it->first.end()) {
+            destroy_plan(it->second);
+            it = m.erase(it);
+        } else {
+            ++it;
+        }
+    }
 }
 
 }  // namespace
@@ -269,7 +563,8 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
     const gsis_params& p = *params;
     if (!(p.Kn > 0.0) || !std::isfinite(p.Kn) || !(p.omega >= 0.0) || p.macro_steps < 0 || p.k_sub < 0 ||
         !(p.cfl > 0.0) || !(p.dt >= 0.0) || p.vdf_dtype < GSIS_F64 || p.vdf_dtype > GSIS_F16 ||
-        p.presolve_max_blocks < 0 || p.wall_layers < 0 || p.adapt_every < 0 || !(p.tol >= 0.0))
+        p.presolve_max_blocks < 0 || p.wall_layers < 0 || p.adapt_every < 0 || !(p.tol >= 0.0) ||
+        !(p.relax >= 0.0 && p.relax <= 1.0))
         return GSIS_ERR_ARG;
     if (alloc && (!alloc->alloc || !alloc->free)) return GSIS_ERR_ARG;
     int dev = 0;
@@ -280,6 +575,7 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
     gsis_ctx* c = new (std::nothrow) gsis_ctx();
     if (!c) return GSIS_ERR_OOM;
     c->p = p;
+    if (c->p.relax == 0.0) c->p.relax = 1.0;
     if (c->p.spin_limit == 0) c->p.spin_limit = 1ull << 26;
     if (alloc) { c->alloc = *alloc; c->have_alloc = true; }
     c->stream = (cudaStream_t)cuda_stream;
@@ -479,10 +775,12 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->hp_off = (int*)dev_alloc(c, (m.H + 1) * sizeof(int));
     c->hp_cnt = (int*)dev_alloc(c, (m.H + 1) * sizeof(int));
     c->d_count = (int*)dev_alloc(c, 4 * sizeof(int));
+    c->d_job = (gsis::MacroJob*)dev_alloc(c, sizeof(gsis::MacroJob));
     c->specs = (RecSpec*)dev_alloc(c, (size_t)std::max(N, 6) * sizeof(RecSpec));
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
-    if (!m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wh ||
+    if (!c->d_job || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W ||
+        !c->Wh ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
         !c->lamf || !c->gu || !c->gT ||
         !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->wall_in ||
@@ -681,8 +979,108 @@ const char* gsis_last_error(const gsis_ctx* c) {
     return c->err.c_str();
 }
 
+gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_report* reports) {
+    if (!ctxs || n <= 0 || iterations < 0) return GSIS_ERR_ARG;
+    std::vector<gsis_ctx*> cs(ctxs, ctxs + n);
+    for (int i = 0; i < n; ++i) {
+        if (!cs[i]) return GSIS_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (cs[j] == cs[i]) return set_err(cs[i], GSIS_ERR_ARG, "a context appears twice in the batch");
+    }
+    int dev0 = cs[0]->device;
+    for (gsis_ctx* c : cs) {
+        gsis_status st = check_ctx(c);
+        if (st != GSIS_OK) return st;
+        if (!c->mesh_set || !c->vgrid_set) return set_err(c, GSIS_ERR_STATE, "set the mesh and velocity grid first");
+        if (c->device != dev0) return set_err(c, GSIS_ERR_ARG, "batched solves must share one device");
+        if (c->p.adaptive && !c->have_forced)
+            return set_err(c, GSIS_ERR_UNSUPPORTED, "batched solves run with a fixed DVM region (adaptive = 0)");
+    }
+    for (gsis_ctx* c : cs) {
+        if (!c->started) {
+            gsis_status st = start(c);
+            if (st != GSIS_OK) return st;
+        }
+    }
+    for (gsis_ctx* c : cs)   // the batch stream is ordered after each solve's own work
+        if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "batch start")) return GSIS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(batch_mutex());
+    auto& plans = batch_plans();
+    BatchPlan* P = nullptr;
+    auto found = plans.find(cs);
+    if (found != plans.end()) {
+        P = found->second;
+        bool stale = false;   // a solve stepped on its own since the graph was recorded (buffers swapped)
+        for (int i = 0; i < n; ++i) stale = stale || (P->W_at_capture[i] != cs[i]->W);
+        if (stale) {
+            destroy_plan(P);
+            plans.erase(found);
+            P = nullptr;
+        }
+    }
+    if (!P) {
+        P = new (std::nothrow) BatchPlan();
+        if (!P) return GSIS_ERR_OOM;
+        P->ctxs = cs;
+        P->owner = cs[0];
+        P->stream = cs[0]->stream;
+        if (!P->stream) {   // the legacy default stream cannot be captured
+            if (!cuda_ok(cs[0], cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking), "batch stream")) {
+                delete P;
+                return GSIS_ERR_CUDA;
+            }
+            P->own_stream = true;
+        }
+        gsis_status st = build_plan(P);
+        if (st != GSIS_OK) {
+            destroy_plan(P);
+            return st;
+        }
+        plans[cs] = P;
+    }
+    for (int it = 0; it < iterations; ++it)
+        if (!cuda_ok(P->owner, cudaGraphLaunch(P->exec, P->stream), "batch graph launch")) return GSIS_ERR_CUDA;
+    if (!cuda_ok(P->owner, cudaStreamSynchronize(P->stream), "batched GSIS iterations")) return GSIS_ERR_CUDA;
+    gsis_status result = GSIS_OK;
+    for (int i = 0; i < n; ++i) {
+        gsis_ctx* c = cs[i];
+        double e[2] = {0.0, 0.0};
+        if (!cuda_ok(c, cudaMemcpy(e, c->eps_buf, 2 * sizeof(double), cudaMemcpyDeviceToHost), "read epsilon"))
+            return GSIS_ERR_CUDA;
+        c->iteration += iterations;
+        c->launches += P->launches_per_iter * iterations / n;
+        if (iterations > 0 && e[1] != 0.0 && result == GSIS_OK)
+            result = set_err(c, GSIS_ERR_NONFINITE, "non-finite or non-positive density/temperature in a batched solve");
+        if (reports) {
+            gsis_report& r = reports[i];
+            std::memset(&r, 0, sizeof(r));
+            r.iterations = iterations;
+            r.total_iterations = c->iteration;
+            r.eps = e[0];
+            r.converged = (iterations > 0 && e[0] < c->p.tol) ? 1 : 0;
+            r.n_dvm = c->Nd;
+            r.n_v = c->vg.Nv;
+            r.vdf_bytes = c->Nd * c->vg.Nv * (long long)vdf_elem_bytes(c->p.vdf_dtype);
+            r.presolve_blocks = c->presolve_blocks;
+            r.sweep_launches = iterations;   // one persistent launch per iteration for the whole batch
+            r.kernel_launches = P->launches_per_iter * iterations;
+        }
+    }
+    return result;
+}
+
+const char* gsis_batch_info(gsis_ctx** ctxs, int n) {
+    static thread_local std::string out;
+    if (!ctxs || n <= 0) return "";
+    std::lock_guard<std::mutex> lk(batch_mutex());
+    auto it = batch_plans().find(std::vector<gsis_ctx*>(ctxs, ctxs + n));
+    out = it == batch_plans().end() ? std::string() : it->second->info;
+    return out.c_str();
+}
+
 void gsis_free(gsis_ctx* c) {
     if (!c) return;
+    drop_plans_with(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     cudaGetLastError();

@@ -65,6 +65,33 @@ struct Mesh {
 };
 
 struct Ctx;
+
+// Mesh view of the synthetic solve.
+struct MacroArgs {
+    int N;
+    const int* nbr;
+    const int* side_bc;
+    const double* Sout;
+    const double* xf;
+    const double* cen;
+    const double* vol;
+    const double* lsq_w;
+    const double* bc_state;   // [6][5]
+    double mu0, omega;
+};
+
+// One block of pseudo-time steps of one solve, for the fused one-CTA kernel.
+struct MacroJob {
+    MacroArgs a;
+    int steps, ndir, k_sub;
+    double cfl, dt;
+    double *Wm, *U;
+    const double *Un, *hot, *wall_corr;
+    double *gu, *gT, *Ff, *lamf, *R, *D, *lamS, *dU, *dU2;
+};
+
+constexpr int MACRO_FUSED_THREADS = 256;
+constexpr int MACRO_FUSED_MAX_CELLS = 4096;
 }  // namespace gsis
 
 struct gsis_ctx {
@@ -125,6 +152,7 @@ struct gsis_ctx {
     int* enter_list = nullptr;     // [N] scratch: DVM indices entering the region
     int* enter_of = nullptr;       // [Nd] entering slot of each DVM cell or -1
     int* d_count = nullptr;        // scratch counters
+    gsis::MacroJob* d_job = nullptr;   // device copy of this solve's fused macro job
     int* h_count = nullptr;
 
     // bookkeeping
@@ -149,18 +177,30 @@ void launch_correction_records(gsis_ctx* c);
 void launch_seed_records(gsis_ctx* c, int n_enter, int grad13);
 // sweep.cu
 void launch_sweep(gsis_ctx* c, int pass);
+// batch.cu (persistent batched sweep; BatchSolve is declared in sweep_device.cuh)
+struct BatchSolve;
+int batch_num_shapes();
+const char* batch_shape_name(int shape);
+int batch_shape_vtile(int shape);
+int batch_grid(int shape, int nc);
+void launch_sweep_batch(int shape, int nc, const BatchSolve* d_solves, const int2* d_items, int n_items,
+                        int* d_ticket, int grid, cudaStream_t st, int pass0, int pass1);
 // moments.cu
 void launch_moments(gsis_ctx* c, const double* Wref, int correct_pass, double* out);
 void launch_half_state(gsis_ctx* c);
 void launch_hot(gsis_ctx* c);
 void launch_wall_flux(gsis_ctx* c);
+void launch_wall_rho(gsis_ctx* c);
 void launch_wall_corr(gsis_ctx* c);
 // macro.cu
 void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U);
 void launch_nsf(gsis_ctx* c, const double* Wprim, double* out);
 void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons);
 void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim);
+void launch_blend(gsis_ctx* c, const double* Wh, double w, double* W);
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term);
+MacroJob macro_job(gsis_ctx* c, int steps, bool time_term);
+void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream);
 void launch_eps(gsis_ctx* c, const double* Wn, const double* Wp);
 // adapt.cu
 void launch_kn_gll(gsis_ctx* c, const double* Wprim);

@@ -21,18 +21,6 @@
 
 namespace gsis {
 
-struct MacroArgs {
-    int N;
-    const int* nbr;
-    const int* side_bc;
-    const double* Sout;
-    const double* xf;
-    const double* cen;
-    const double* vol;
-    const double* lsq_w;
-    const double* bc_state;   // [6][5]
-    double mu0, omega;
-};
 
 static MacroArgs margs(gsis_ctx* c) {
     MacroArgs a;
@@ -54,10 +42,8 @@ static MacroArgs margs(gsis_ctx* c) {
 // Least-squares gradient (face neighbours plus boundary face centres with the
 // boundary value: far field -> boundary state; wall -> u = 0, |u| = 0, T = T_w,
 // rho = cell value).  gu[c][j][i] = d u_j / d x_i.
-__global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with_rho_U, double* __restrict__ gu,
-                            double* __restrict__ gT, double* __restrict__ grho, double* __restrict__ gU) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.N) return;
+__device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double* Wp, int with_rho_U, double* gu,
+                                               double* gT, double* grho, double* gU, int c) {
     const double* wc = Wp + c * 5;
     const double Uc = sqrt(wc[1] * wc[1] + wc[2] * wc[2] + wc[3] * wc[3]);
     double g[6][3];
@@ -99,6 +85,12 @@ __global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with
             gU[(long long)c * 3 + i] = g[5][i];
         }
     }
+}
+
+__global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with_rho_U, double* __restrict__ gu,
+                            double* __restrict__ gT, double* __restrict__ grho, double* __restrict__ gU) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < a.N) gradients_cell(a, Wp, with_rho_U, gu, gT, grho, gU, c);
 }
 
 void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U) {
@@ -167,6 +159,20 @@ __global__ void k_cons_to_prim(int N, const double* __restrict__ U, double* __re
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     cons_to_prim(U + c * 5, Wp + c * 5);
+}
+
+// W <- Wh + w (W - Wh): under-relaxed synthetic correction of the primitives.
+__global__ void k_blend(int N, const double* __restrict__ Wh, double w, double* __restrict__ W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * 5) return;
+    const double h = Wh[i];
+    W[i] = h + w * (W[i] - h);
+}
+
+void launch_blend(gsis_ctx* c, const double* Wh, double w, double* W) {
+    const int n = c->m.N * 5;
+    k_blend<<<(n + 255) / 256, 256, 0, c->stream>>>(c->m.N, Wh, w, W);
+    c->launches++;
 }
 
 void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons) {
@@ -238,11 +244,9 @@ __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u
 // (area vector S pointing L -> R).  Writes the total face flux (inviscid +
 // viscous + HoT) F.S to Ff[c][d][5] and lambda |S| to lamf[c][d]; faces that
 // do not exist (boundary) get lamf = -1.
-__global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ gu,
-                            const double* __restrict__ gT, const double* __restrict__ hot, int ndir,
-                            double* __restrict__ Ff, double* __restrict__ lamf) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.N * ndir) return;
+__device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* Wm, const double* gu,
+                                              const double* gT, const double* hot, int ndir, double* Ff,
+                                              double* lamf, int t) {
     const int L = t / ndir, d = t % ndir;
     const int Rr = a.nbr[L * 6 + 2 * d + 1];
     double* F = Ff + ((long long)L * 3 + d) * 5;
@@ -321,6 +325,13 @@ __global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const do
     lamf[(long long)L * 3 + d] = lam * Sabs;
 }
 
+__global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ gu,
+                            const double* __restrict__ gT, const double* __restrict__ hot, int ndir,
+                            double* __restrict__ Ff, double* __restrict__ lamf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.N * ndir) face_flux_one(a, Wm, gu, gT, hot, ndir, Ff, lamf, t);
+}
+
 // NSF flux through wall side s of cell c at state w (prim) with cell gradients
 // gu, gT: no mass flux, cell pressure, NSF stress and heat flux at u = 0,
 // T = T_w from the cell gradient corrected along the cell-to-face line.
@@ -386,15 +397,11 @@ void launch_wall_corr(gsis_ctx* c) {
 // Cell residual R_c = -sum_F F.S_out (gathering the interior face fluxes in
 // side order, boundary faces evaluated here), lambda|S| per side, the
 // diagonal D and dU0 = R/D.
-__global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ U,
-                                const double* __restrict__ Un, const double* __restrict__ gu,
-                                const double* __restrict__ gT, const double* __restrict__ hot,
-                                const double* __restrict__ Ff, const double* __restrict__ lamf,
-                                const double* __restrict__ wall_corr, double cfl, double dt,
-                                double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
-                                double* __restrict__ dU) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.N) return;
+__device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const double* Wm, const double* U,
+                                                  const double* Un, const double* gu, const double* gT,
+                                                  const double* hot, const double* Ff, const double* lamf,
+                                                  const double* wall_corr, double cfl, double dt, double* R, double* D,
+                                                  double* lamS, double* dU, int c) {
     const double* wc = Wm + c * 5;
     const double rho_c = wc[0], T_c = wc[4], p_c = rho_c * T_c;
     const double u_c[3] = {wc[1], wc[2], wc[3]};
@@ -464,12 +471,20 @@ __global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, cons
     }
 }
 
-// One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D.
-__global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double* __restrict__ R,
-                        const double* __restrict__ D, const double* __restrict__ lamS, const double* __restrict__ dUin,
-                        double* __restrict__ dUout) {
+__global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ U,
+                                const double* __restrict__ Un, const double* __restrict__ gu,
+                                const double* __restrict__ gT, const double* __restrict__ hot,
+                                const double* __restrict__ Ff, const double* __restrict__ lamf,
+                                const double* __restrict__ wall_corr, double cfl, double dt,
+                                double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
+                                double* __restrict__ dU) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.N) return;
+    if (c < a.N) cell_residual_one(a, Wm, U, Un, gu, gT, hot, Ff, lamf, wall_corr, cfl, dt, R, D, lamS, dU, c);
+}
+
+// One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D.
+__device__ __forceinline__ void relax_one(const MacroArgs& a, const double* U, const double* R, const double* D,
+                                          const double* lamS, const double* dUin, double* dUout, int c) {
     double off[5] = {0, 0, 0, 0, 0};
     for (int s = 0; s < 6; ++s) {
         const int n = a.nbr[c * 6 + s];
@@ -485,18 +500,87 @@ __global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double*
     for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) / D[c];
 }
 
-__global__ void k_update(int N, double* __restrict__ U, const double* __restrict__ dU, double* __restrict__ Wm) {
+__global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double* __restrict__ R,
+                        const double* __restrict__ D, const double* __restrict__ lamS, const double* __restrict__ dUin,
+                        double* __restrict__ dUout) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    if (c < a.N) relax_one(a, U, R, D, lamS, dUin, dUout, c);
+}
+
+__device__ __forceinline__ void update_one(double* U, const double* dU, double* Wm, int c) {
     for (int q = 0; q < 5; ++q) U[c * 5 + q] += dU[c * 5 + q];
     cons_to_prim(U + c * 5, Wm + c * 5);
 }
 
+__global__ void k_update(int N, double* __restrict__ U, const double* __restrict__ dU, double* __restrict__ Wm) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) update_one(U, dU, Wm, c);
+}
+
+// The whole pseudo-time block of one solve in one CTA (meshes up to a few
+// thousand cells: the 1D shocks, solve batches).  The same per-cell and
+// per-face functions as the multi-block kernels, separated by block barriers,
+// so the result is identical.  One CTA per job of the job array.
+__global__ void __launch_bounds__(MACRO_FUSED_THREADS) k_macro_fused(const MacroJob* __restrict__ jobs) {
+    const MacroJob& J = jobs[blockIdx.x];
+    const MacroArgs a = J.a;
+    const int N = a.N;
+    for (int it = 0; it < J.steps; ++it) {
+        for (int c = threadIdx.x; c < N; c += blockDim.x)
+            gradients_cell(a, J.Wm, 0, J.gu, J.gT, nullptr, nullptr, c);
+        __syncthreads();
+        for (int t = threadIdx.x; t < N * J.ndir; t += blockDim.x)
+            face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.ndir, J.Ff, J.lamf, t);
+        __syncthreads();
+        for (int c = threadIdx.x; c < N; c += blockDim.x)
+            cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.wall_corr, J.cfl, J.dt, J.R,
+                              J.D, J.lamS, J.dU, c);
+        __syncthreads();
+        double* din = J.dU;
+        double* dout = J.dU2;
+        for (int s = 0; s < J.k_sub; ++s) {
+            for (int c = threadIdx.x; c < N; c += blockDim.x) relax_one(a, J.U, J.R, J.D, J.lamS, din, dout, c);
+            __syncthreads();
+            double* t = din; din = dout; dout = t;
+        }
+        for (int c = threadIdx.x; c < N; c += blockDim.x) update_one(J.U, din, J.Wm, c);
+        __syncthreads();
+    }
+}
+
+MacroJob macro_job(gsis_ctx* c, int steps, bool time_term) {
+    MacroJob J;
+    J.a = margs(c);
+    J.steps = steps;
+    J.ndir = c->normal_components;
+    J.k_sub = c->p.k_sub;
+    J.cfl = c->p.cfl;
+    J.dt = time_term ? c->p.dt : 0.0;
+    J.Wm = c->Wm; J.U = c->U; J.Un = c->Un; J.gu = c->gu; J.gT = c->gT; J.hot = c->hot; J.Ff = c->Ff;
+    J.lamf = c->lamf; J.wall_corr = c->wall_corr; J.R = c->R; J.D = c->D; J.lamS = c->lamS; J.dU = c->dU;
+    J.dU2 = c->dU2;
+    return J;
+}
+
+void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream) {
+    k_macro_fused<<<njobs, MACRO_FUSED_THREADS, 0, stream>>>(d_jobs);
+}
+
 // `steps` DP-LUR pseudo-steps on c->U / c->Wm (prim kept in step), HoT from c->hot,
-// time term against c->Un when time_term.
+// time term against c->Un when time_term.  Small meshes run the fused
+// one-CTA kernel (one launch per block of steps); larger ones launch the
+// per-phase kernels over the whole grid.
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term) {
     (void)with_hot;
     const int N = c->m.N;
+    if (steps <= 0) return;
+    if (N <= MACRO_FUSED_MAX_CELLS) {
+        MacroJob J = macro_job(c, steps, time_term);
+        cudaMemcpyAsync(c->d_job, &J, sizeof(MacroJob), cudaMemcpyHostToDevice, c->stream);
+        launch_macro_fused(c->d_job, 1, c->stream);
+        c->launches++;
+        return;
+    }
     const int TB = 64;
     const int nb = (N + TB - 1) / TB;
     const int ndir = c->normal_components;   // index directions that carry flux

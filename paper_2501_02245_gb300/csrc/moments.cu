@@ -130,6 +130,80 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     }
 }
 
+// Diffuse-wall densities from the current VDF of each DVM wall cell:
+// rho_w[k][s] = sum_{xi.S_s > 0} w (xi.S_s) f / wall_den[c][s].  Run between
+// the forward and the backward pass, so that each pass emits from the wall
+// with the latest outgoing half of f (the forward pass takes the values of
+// the cell-equilibrium step, computed from f^n).  One block per DVM cell;
+// cells without a wall side return at once.
+template <typename S>
+__global__ void __launch_bounds__(256) k_wall_rho(int Nd, const int* __restrict__ dvm_cell,
+                                                  const int* __restrict__ side_bc, const double* __restrict__ Sout,
+                                                  const S* __restrict__ f, VGridDev vg,
+                                                  const double* __restrict__ wall_den, double* __restrict__ rho_w,
+                                                  float* __restrict__ rho_wf) {
+    const int k = blockIdx.x;
+    if (k >= Nd) return;
+    const int c = dvm_cell[k];
+    int wall_mask = 0;
+    for (int s = 0; s < 6; ++s)
+        if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
+    if (!wall_mask) return;
+    __shared__ double red[32 * 6];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const S* fk = f + (long long)k * vg.Nv;
+    for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
+        int ix, iy, iz;
+        vsplit(v, vg.nx, vg.ny, ix, iy, iz);
+        const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
+        const double fv = Store<S>::ld(fk + v);
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            if ((wall_mask >> s) & 1) {
+                const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+                const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
+                if (xn > 0.0) acc[s] += xn * fv;
+            }
+        }
+    }
+    block_sum<6>(acc, red);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 6; ++s) {
+            if ((wall_mask >> s) & 1) {
+                const double v = acc[s] * vg.w / wall_den[c * 6 + s];
+                rho_w[(long long)k * 6 + s] = v;
+                if (rho_wf) rho_wf[(long long)k * 6 + s] = (float)v;
+            }
+        }
+    }
+}
+
+void launch_wall_rho(gsis_ctx* c) {
+    const int Nd = (int)c->Nd;
+    if (Nd == 0 || !c->has_wall) return;
+    switch (c->p.vdf_dtype) {
+        case GSIS_F64:
+            k_wall_rho<double><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout, (const double*)c->f,
+                                                          c->vg, c->wall_den, c->rho_w, c->rho_wf);
+            break;
+        case GSIS_F32:
+            k_wall_rho<float><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout, (const float*)c->f,
+                                                         c->vg, c->wall_den, c->rho_w, c->rho_wf);
+            break;
+        case GSIS_BF16:
+            k_wall_rho<__nv_bfloat16><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                                 (const __nv_bfloat16*)c->f, c->vg, c->wall_den,
+                                                                 c->rho_w, c->rho_wf);
+            break;
+        default:
+            k_wall_rho<__half><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                          (const __half*)c->f, c->vg, c->wall_den, c->rho_w,
+                                                          c->rho_wf);
+            break;
+    }
+    c->launches++;
+}
+
 template <typename S, typename T>
 static void moments_t(gsis_ctx* c, const double* Wref, bool correct, double* out) {
     const int Nd = (int)c->Nd;

@@ -24,7 +24,7 @@ PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual"
 
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
-            "gsis_corrected_maxwellian_noalloc"]
+            "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info"]
 
 
 class GsisError(RuntimeError):
@@ -38,7 +38,8 @@ class Params(ctypes.Structure):
                 ("Kn_ref", ctypes.c_double), ("adapt_every", ctypes.c_int), ("wall_layers", ctypes.c_int),
                 ("vdf_dtype", ctypes.c_int), ("macro_steps", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("k_sub", ctypes.c_int), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
-                ("presolve_max_blocks", ctypes.c_int), ("spin_limit", ctypes.c_ulonglong)]
+                ("presolve_max_blocks", ctypes.c_int), ("spin_limit", ctypes.c_ulonglong),
+                ("relax", ctypes.c_double)]
 
 
 class Allocator(ctypes.Structure):
@@ -94,8 +95,11 @@ def load():
     lib.gsis_version.restype = ctypes.c_char_p
     lib.gsis_corrected_maxwellian_noalloc.argtypes = [vp, c_int, ctypes.POINTER(VGridDesc), vp, vp]
     lib.gsis_corrected_maxwellian_noalloc.restype = c_int
+    lib.gsis_iterate_batch.argtypes = [ctypes.POINTER(vp), c_int, c_int, ctypes.POINTER(Report)]
+    lib.gsis_batch_info.argtypes = [ctypes.POINTER(vp), c_int]
+    lib.gsis_batch_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
-                 "gsis_get_vdf", "gsis_debug_set_region"):
+                 "gsis_get_vdf", "gsis_debug_set_region", "gsis_iterate_batch"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -152,7 +156,8 @@ class Solver:
                    float(params.get("Kn_ref", 0.0)), int(params.get("adapt_every", 5)),
                    int(params.get("wall_layers", 2)), DTYPES[vdf_dtype], int(params.get("macro_steps", 200)),
                    float(params.get("cfl", 5.0)), int(params.get("k_sub", 2)), float(params.get("dt", 0.0)),
-                   float(params.get("tol", 1e-6)), int(params.get("presolve_max_blocks", 0)), 0)
+                   float(params.get("tol", 1e-6)), int(params.get("presolve_max_blocks", 0)), 0,
+                   float(params.get("relax", 1.0)))
         self._alloc = None
         alloc_ptr = None
         stream_ptr = None
@@ -183,7 +188,7 @@ class Solver:
         params = dict(Kn=case.Kn, omega=case.omega, adaptive=int(case.adaptive), Kn_ref=case.Kn_ref,
                       adapt_every=case.adapt_every, wall_layers=case.wall_layers, macro_steps=case.macro_steps,
                       cfl=case.cfl, k_sub=case.k_sub, dt=case.dt, tol=case.tol,
-                      presolve_max_blocks=case.presolve_max_blocks)
+                      presolve_max_blocks=case.presolve_max_blocks, relax=case.relax)
         params.update(overrides)
         return cls(params, case.mesh, case.W0, case.vgrid, vdf_dtype=vdf_dtype, stream=stream,
                    forced_flags=forced_flags)
@@ -268,6 +273,39 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _ctx_array(solvers):
+    arr = (ctypes.c_void_p * len(solvers))()
+    for i, s in enumerate(solvers):
+        arr[i] = s.ctx.value
+    return arr
+
+
+def iterate_batch(solvers, n):
+    """Advance every solver by n GSIS iterations in one batched pass per
+    iteration (gsis_iterate_batch); returns one report dict per solver."""
+    lib = load()
+    reps = (Report * len(solvers))()
+    st = lib.gsis_iterate_batch(_ctx_array(solvers), len(solvers), int(n), reps)
+    if st != GSIS_OK:
+        msg = ""
+        for s in solvers:
+            e = lib.gsis_last_error(s.ctx)
+            if e:
+                msg = e.decode()
+                break
+        raise GsisError(st, msg)
+    out = []
+    for rep in reps:
+        d = {f: getattr(rep, f) for f, _ in Report._fields_ if f != "phase_ms"}
+        out.append(d)
+    return out
+
+
+def batch_info(solvers):
+    """Description of the recorded batch plan of this solver list."""
+    return load().gsis_batch_info(_ctx_array(solvers), len(solvers)).decode()
 
 
 def version():

@@ -48,6 +48,7 @@ class Case:
     tol: float = 1e-6
     presolve_max_blocks: int = 0   # NS presolve: blocks of macro_steps pseudo-steps
     dt: float = 0.0                # time step of Eq. macro; 0 means the steady form (dt -> inf)
+    relax: float = 1.0             # weight of the synthetic correction of W (1 = plain scheme)
     extra: dict = field(default_factory=dict)
 
 
