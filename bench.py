@@ -6,7 +6,12 @@ A step is one GSIS iteration (cell equilibrium, kinetic sweep, moments and
 HoT, synthetic solve, VDF correction, residual) over the resident state.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsis|reference]
-                    [--config cylinder|shock|cylinder_full|sphere] [--dtype f64|f32|bf16|f16]
+                    [--config cylinder|shock|cylinder_full|sphere|batch] [--dtype f64|f32|bf16|f16]
+
+--config batch: 64 independent 1D shocks (seeded Ma in [1.5, 8], 100-800
+cells, 24^3..64^3 velocity grids, even solves FP32 and odd BF16 VDFs) advanced
+together by gsis_iterate_batch (one persistent sweep launch, one fused
+synthetic-solve launch, one CUDA graph per iteration; autotuned tile shape).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 a bounded sample of the same workload (a 12 x 12 O-grid with the same velocity
@@ -43,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsis", choices=["gsis", "reference"])
     ap.add_argument("--config", default="cylinder",
-                    choices=["cylinder", "shock", "cylinder_full", "sphere", "cylinder32"])
+                    choices=["cylinder", "shock", "cylinder_full", "sphere", "cylinder32", "batch"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "f16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -51,7 +56,13 @@ def parse():
 
 
 def make_case(config, small=False):
-    from workloads import shock_1d_case, cylinder_case, sphere_case
+    from workloads import shock_1d_case, cylinder_case, sphere_case, shock_batch_cases
+    if config == "batch":   # the first shock of the seeded batch (small: reduced to 20 cells)
+        c0 = shock_batch_cases(n=1)[0]
+        if not small:
+            return c0
+        return shock_1d_case(Ma=c0.extra["Ma"], n_cells=20, half_width=2.5, nv=c0.vgrid.n, vmax=c0.vgrid.hi[0],
+                             macro_steps=c0.macro_steps)
     if config == "shock":
         return shock_1d_case(n_cells=200 if not small else 40)
     if config == "cylinder32":   # reduced mesh, same velocity grid (for profiler captures)
@@ -73,7 +84,9 @@ def workload_name(config, dtype):
         "cylinder32": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 32x32, velocity grid 48x48x24, adaptive Kn_ref=0.01",
         "shock": "1D normal shock Ma=2, 200 cells on [-25,25] mfp, velocity grid 48x24x24, all kinetic",
         "sphere": "3D sphere Ma=5 Kn=0.005 Tw=2, O-grid 96x64x64, velocity grid 48^3, adaptive Kn_ref=0.01",
-    }[config] + ", VDF " + dtype
+        "batch": "batch of 64 1D shocks, Ma~U[1.5,8], 100-800 cells, velocity grids 24^3..64^3, "
+                 "one persistent launch + CUDA graph",
+    }[config] + (", VDF " + dtype if config != "batch" else ", VDF f32 (even) / bf16 (odd)")
 
 
 def dist_env():
@@ -287,6 +300,94 @@ def run_gsis(args):
     return 0
 
 
+def run_batch(args):
+    """64 independent shocks advanced together through gsis_iterate_batch."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from workloads import shock_batch_cases
+    from paper_2501_02245_gb300 import Solver, iterate_batch, batch_info
+    cases = shock_batch_cases()
+    stream = torch.cuda.Stream()
+    solvers = [Solver.from_case(c, vdf_dtype=c.extra["vdf_dtype"], stream=stream) for c in cases]
+    iterate_batch(solvers, max(args.warmup, 1))   # first call: start, autotune, record the graph
+    clocks = Clocks(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = iterate_batch(solvers, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    pts_iter = sum(r["n_dvm"] * r["n_v"] for r in reps)
+    value = pts_iter * args.steps * ws / (t_max * 1e-3)
+    sweep_ms = reps[0]["phase_ms"]["sweep"]
+    eb = {"f32": 4, "bf16": 2}
+    bytes_alg = sum(2 * 2 * eb[c.extra["vdf_dtype"]] * r["n_dvm"] * r["n_v"] for c, r in zip(cases, reps))
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        peaks = json.load(fh)
+    achieved = bytes_alg / (sweep_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profile("batch", "mixed"),
+            "kernel": "k_sweep_batch (both Gauss-Seidel passes of all 64 solves, one launch)",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+            "algorithmic": "2 passes x 2 x b bytes per (cell, velocity), b = 4 (FP32) / 2 (BF16)"}
+    info = batch_info(solvers)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/bf16", "data": "synthetic",
+            "config": {"workload": workload_name("batch", "mixed"), "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "n_solves": len(cases), "points_per_iteration": pts_iter,
+                       "vdf_bytes": sum(r["vdf_bytes"] for r in reps),
+                       "l2": "VDFs (%.1f GB) larger than L2" % (sum(r["vdf_bytes"] for r in reps) / 1e9),
+                       "plan": info, "eps_max_last": max(r["eps"] for r in reps),
+                       "sweep_ms_per_step": sweep_ms},
+            "roofline": roof, "clocks": ck, "gpu_launches": reps[0]["kernel_launches"]}
+    for sv in solvers:
+        sv.close()
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sol2 = [Solver.from_case(c, vdf_dtype=c.extra["vdf_dtype"], stream=stream) for c in cases]
+        r2 = iterate_batch(sol2, args.steps)
+        Ws = [sv.W() for sv in sol2]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        for sv in sol2:
+            sv.close()
+        line["e2e"] = {"value": sum(r["n_dvm"] * r["n_v"] for r in r2) * args.steps / dt, "unit": UNIT,
+                       "h2d_bytes_per_step": sum(mesh_bytes(c) for c in cases) // args.steps,
+                       "d2h_bytes_per_step": sum(W.nbytes for W in Ws) // args.steps,
+                       "includes": "set-up upload of 64 solves, autotuning and graph recording, %d iterations, "
+                                   "result read-back" % args.steps}
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, nd, nv, nc = cpu_baseline("batch")
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one GSIS iteration of the FP64 oracle on one shock of the batch reduced "
+                                          "to %d cells (%d velocities), %.1f s" % (nc, nv, dt)}
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def e2e(args, case, stream):
     """The same metric through the public API from host data: context creation,
     mesh and velocity-grid upload (host -> device), the adaptive start, the
@@ -312,6 +413,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "batch":
+        return run_batch(args)
     return run_gsis(args)
 
 

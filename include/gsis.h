@@ -210,7 +210,10 @@ gsis_status gsis_debug_set_region(gsis_ctx* ctx, const uint8_t* flags);
  *       contexts not yet started are started (presolve included).
  * iterations: >= 0; exactly this many iterations run (no early stop: the
  *       residual is only read at the end); reports[i] (may be NULL) receives
- *       the residual of the last iteration and the sizes of solve i.
+ *       the residual of the last iteration and the sizes of solve i; its
+ *       phase_ms[GSIS_PH_SWEEP] is the duration of the batched sweep launch of
+ *       the last iteration (the whole batch, not solve i alone) and
+ *       phase_ms[GSIS_PH_MACRO] the rest of that iteration.
  * The batch runs on ctxs[0]'s stream (a private stream when that is the
  * legacy default stream) after synchronising every context's stream, and
  * synchronises before returning.  The recorded graph is kept for the same

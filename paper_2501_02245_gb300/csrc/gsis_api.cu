@@ -312,6 +312,7 @@ struct BatchPlan {
     std::vector<double> tune_ms;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // around the sweep and the whole iteration
     long long launches_per_iter = 0;
     std::string info;
 };
@@ -333,6 +334,8 @@ void destroy_plan(BatchPlan* P) {
     if (!P) return;
     if (P->exec) cudaGraphExecDestroy(P->exec);
     if (P->graph) cudaGraphDestroy(P->graph);
+    for (cudaEvent_t& e : P->ev)
+        if (e) cudaEventDestroy(e);
     if (P->own_stream && P->stream) {
         cudaStreamSynchronize(P->stream);
         cudaStreamDestroy(P->stream);
@@ -486,9 +489,13 @@ gsis_status build_plan(BatchPlan* P) {
         P->ctxs[i]->stream = P->stream;
         l0 += P->ctxs[i]->launches;
     }
+    for (cudaEvent_t& e : P->ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) return set_err(o, GSIS_ERR_CUDA, "batch timing events");
     cudaError_t ce = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
+        cudaEventRecordWithFlags(P->ev[2], P->stream, cudaEventRecordExternal);
         for (gsis_ctx* c : P->ctxs) stage_cell_eq(c);
+        cudaEventRecordWithFlags(P->ev[0], P->stream, cudaEventRecordExternal);
         bool walls = false;
         for (gsis_ctx* c : P->ctxs) walls = walls || c->has_wall;
         if (walls) {   // wall densities refreshed between the passes
@@ -501,6 +508,7 @@ gsis_status build_plan(BatchPlan* P) {
             launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
                                0, 2);
         }
+        cudaEventRecordWithFlags(P->ev[1], P->stream, cudaEventRecordExternal);
         for (gsis_ctx* c : P->ctxs) stage_moments(c);
         if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream);
         for (int i : P->big) {
@@ -511,6 +519,7 @@ gsis_status build_plan(BatchPlan* P) {
             stage_residual(c, true);
             stage_correct(c);
         }
+        cudaEventRecordWithFlags(P->ev[3], P->stream, cudaEventRecordExternal);
         ce = cudaStreamEndCapture(P->stream, &P->graph);
     }
     long long l1 = 0;
@@ -1041,6 +1050,13 @@ gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_repo
     for (int it = 0; it < iterations; ++it)
         if (!cuda_ok(P->owner, cudaGraphLaunch(P->exec, P->stream), "batch graph launch")) return GSIS_ERR_CUDA;
     if (!cuda_ok(P->owner, cudaStreamSynchronize(P->stream), "batched GSIS iterations")) return GSIS_ERR_CUDA;
+    float sweep_ms = 0.f, iter_ms = 0.f;   // of the last replayed iteration (event-record nodes of the graph)
+    if (iterations > 0) {
+        if (!cuda_ok(P->owner, cudaEventElapsedTime(&sweep_ms, P->ev[0], P->ev[1]), "batch sweep timing") ||
+            !cuda_ok(P->owner, cudaEventElapsedTime(&iter_ms, P->ev[2], P->ev[3]), "batch iteration timing"))
+            return GSIS_ERR_CUDA;
+    }
+    if (!cuda_ok(P->owner, cudaGetLastError(), "batched iteration")) return GSIS_ERR_CUDA;
     gsis_status result = GSIS_OK;
     for (int i = 0; i < n; ++i) {
         gsis_ctx* c = cs[i];
@@ -1064,6 +1080,8 @@ gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_repo
             r.presolve_blocks = c->presolve_blocks;
             r.sweep_launches = iterations;   // one persistent launch per iteration for the whole batch
             r.kernel_launches = P->launches_per_iter * iterations;
+            r.phase_ms[GSIS_PH_SWEEP] = sweep_ms;           // the batched sweep of the last iteration
+            r.phase_ms[GSIS_PH_MACRO] = iter_ms - sweep_ms;  // everything else of the last iteration
         }
     }
     return result;

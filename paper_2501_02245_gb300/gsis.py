@@ -299,6 +299,7 @@ def iterate_batch(solvers, n):
     out = []
     for rep in reps:
         d = {f: getattr(rep, f) for f, _ in Report._fields_ if f != "phase_ms"}
+        d["phase_ms"] = {PHASES[i]: rep.phase_ms[i] for i in range(8)}
         out.append(d)
     return out
 
