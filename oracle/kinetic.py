@@ -12,9 +12,13 @@ reading taken (stated once, used everywhere):
   are DVM cells, 0 otherwise (first order next to boundaries and NS cells);
 * the outgoing part of the upwind cell value is implicit, every other term
   (own slope, neighbour face values) takes the latest value available;
-* one symmetric Gauss-Seidel pass: forward over hyperplanes h = i + j + k,
-  then backward.  Cells of one hyperplane never appear in each other's
-  stencil, so the order inside a hyperplane does not matter.
+* one symmetric Gauss-Seidel pass: backward over hyperplanes h = i + j + k
+  (towards the low-index side, where the body walls of the O-grids lie),
+  then forward.  Molecules travelling towards a wall are swept first, the
+  wall density is then taken from their outgoing flux, and the re-emitted
+  molecules are swept out in the same kinetic step.  Cells of one hyperplane
+  never appear in each other's stencil, so the order inside a hyperplane does
+  not matter.
 
 Boundary and interface face values for incoming velocities (xi . n < 0):
 far field -> conservation-corrected Maxwellian M~ of the boundary state (so a
@@ -108,13 +112,13 @@ def update_cell(topo, vg, f, dvm, inp, c):
 
 
 def sweep(topo, vg, f, dvm, inp):
-    """One forward and one backward Gauss-Seidel pass over the DVM cells in
+    """One backward and one forward Gauss-Seidel pass over the DVM cells in
     hyperplane order; f is updated in place (rows of NS cells are untouched)."""
     cells = [c for c in range(topo.ncell) if dvm[c]]
     cells.sort(key=lambda c: (topo.hyperplane(c), c))
-    for c in cells:
-        update_cell(topo, vg, f, dvm, inp, c)
     for c in reversed(cells):
+        update_cell(topo, vg, f, dvm, inp, c)
+    for c in cells:
         update_cell(topo, vg, f, dvm, inp, c)
     return f
 

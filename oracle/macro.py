@@ -6,15 +6,22 @@ The paper defers the fluxes F and sources Q of Eq. macro to an appendix of
 another paper.  The reading taken, for the monatomic gas (no source):
 
 * conserved U = (rho, rho u, rho E), E = 3/2 T + |u|^2/2, p = rho T;
-* inviscid face flux: HLLC (Toro) with Davis wave-speed estimates on
-  MUSCL states of (rho, u, p) reconstructed in index space with minmod
-  (first order at boundaries);
+* inviscid face flux: kinetic flux-vector splitting (the flux of the left
+  face state's Maxwellian molecules moving along +n plus the right one's
+  moving along -n, in closed form) on MUSCL states of (rho, u, p)
+  reconstructed in index space with minmod (first order at boundaries).
+  This is the Euler flux the discrete-velocity upwind scheme itself carries
+  for Maxwellian states, so the synthetic equations and the kinetic step
+  dissipate alike; with a contact-preserving Riemann solver (HLLC) an
+  entropy mode at the stagnation line, which the kinetic step damps and the
+  synthetic solve does not, grew from one GSIS iteration to the next;
 * viscous face flux: NSF stress and heat flux (Eq. NSF_constitutive) from
   the mean of the two cells' least-squares gradients, corrected along the
   line of centres, at the mean cell velocity and temperature; plus the mean
   of the two cells' high-order terms (HoT, zero in NS cells);
-* boundaries: far field = HLLC against the boundary state plus the cell's
-  HoT (no NSF part: the far field is taken as gradient-free);
+* boundaries: far field = the same splitting against the boundary state
+  (the kinetic step's incoming far-field Maxwellian) plus the cell's HoT (no
+  NSF part: the far field is taken as gradient-free);
   wall of an NS cell (and in the NS presolve) = cell pressure, no mass flux,
   NSF at u = 0, T = T_w from a one-sided gradient; wall of a DVM cell = the
   kinetic wall flux of f^{n+1/2} plus the change of that NSF wall flux since
@@ -26,6 +33,7 @@ another paper.  The reading taken, for the monatomic gas (no source):
   and k_sub Jacobi sweeps over the off-diagonal Rusanov-split Euler fluxes.
 """
 import numpy as np
+from scipy.special import erf
 
 from .mesh import BC_NONE, BC_FARFIELD, BC_WALL
 from .model import GAMMA, viscosity, kappa_monatomic
@@ -145,39 +153,31 @@ def minmod(a, b):
                     np.where((a < 0) & (b < 0), np.maximum(a, b), 0.0))
 
 
-def hllc(rL, uL, pL, rR, uR, pR, n):
-    """HLLC flux per unit area through unit normal n (Toro, Riemann Solvers, ch. 10)."""
-    g = GAMMA
-    unL = np.sum(uL * n, axis=1)
-    unR = np.sum(uR * n, axis=1)
-    aL = np.sqrt(g * pL / rL)
-    aR = np.sqrt(g * pR / rR)
-    EL = pL / (g - 1.0) + 0.5 * rL * np.sum(uL * uL, axis=1)
-    ER = pR / (g - 1.0) + 0.5 * rR * np.sum(uR * uR, axis=1)
-    SL = np.minimum(unL - aL, unR - aR)
-    SR = np.maximum(unL + aL, unR + aR)
-    Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR))
+def _half_range(r, u, T, n, sign):
+    """Flux of mass, momentum and energy carried by the molecules of the
+    Maxwellian (r, u, T) that cross a face of unit normal n in the direction
+    sign * n: the half-range moments of the normal Gaussian N(u.n, T),
+    M0 = int_+ xi_n g, M1 = int_+ xi_n^2 g, M2 = int_+ xi_n^3 g, with the
+    tangential thermal motion averaged in closed form."""
+    un = np.sum(u * n, axis=1)
+    st = np.sqrt(T)
+    P = 0.5 * (1.0 + sign * erf(un / (np.sqrt(2.0) * st)))
+    D = sign * st * np.exp(-0.5 * un * un / T) / np.sqrt(2.0 * np.pi)
+    M0 = un * P + D
+    M1 = (un * un + T) * P + un * D
+    M2 = (un ** 3 + 3.0 * un * T) * P + (un * un + 2.0 * T) * D
+    ut = u - un[:, None] * n
+    mom = r[:, None] * (M1[:, None] * n + ut * M0[:, None])
+    en = 0.5 * r * (M2 + (np.sum(ut * ut, axis=1) + 2.0 * T) * M0)
+    return np.concatenate([(r * M0)[:, None], mom, en[:, None]], axis=1)
 
-    def flux(r, u, p, E, un):
-        return np.concatenate([(r * un)[:, None], r[:, None] * u * un[:, None] + p[:, None] * n,
-                               ((E + p) * un)[:, None]], axis=1)
 
-    def state(r, u, E):
-        return np.concatenate([r[:, None], r[:, None] * u, E[:, None]], axis=1)
-
-    def star(r, u, p, E, un, S):
-        coef = r * (S - un) / (S - Ss)
-        us = u + (Ss - un)[:, None] * n
-        e = E / r + (Ss - un) * (Ss + p / (r * (S - un)))
-        return coef[:, None] * np.concatenate([np.ones((len(r), 1)), us, e[:, None]], axis=1)
-
-    FL = flux(rL, uL, pL, EL, unL)
-    FR = flux(rR, uR, pR, ER, unR)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        FsL = FL + SL[:, None] * (star(rL, uL, pL, EL, unL, SL) - state(rL, uL, EL))
-        FsR = FR + SR[:, None] * (star(rR, uR, pR, ER, unR, SR) - state(rR, uR, ER))
-    return np.where((SL >= 0)[:, None], FL,
-                    np.where((Ss >= 0)[:, None], FsL, np.where((SR >= 0)[:, None], FsR, FR)))
+def kfvs(rL, uL, pL, rR, uR, pR, n):
+    """Kinetic flux-vector splitting: the flux of the left Maxwellian's
+    molecules moving along +n plus that of the right Maxwellian's molecules
+    moving along -n (the Euler flux the discrete-velocity upwind scheme carries
+    for Maxwellian states), per unit area through unit normal n."""
+    return _half_range(rL, uL, pL / rL, n, 1.0) + _half_range(rR, uR, pR / rR, n, -1.0)
 
 
 def euler_flux_dot(U, S):
@@ -245,7 +245,7 @@ def residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, bface_corr=None):
     L, Rr, d = geo.L, geo.R, geo.dirs
     qL = prim[L] + 0.5 * slopes[L, d, :]
     qR = prim[Rr] - 0.5 * slopes[Rr, d, :]
-    Fi = hllc(qL[:, 0], qL[:, 1:4], qL[:, 4], qR[:, 0], qR[:, 1:4], qR[:, 4], geo.n) * geo.Sabs[:, None]
+    Fi = kfvs(qL[:, 0], qL[:, 1:4], qL[:, 4], qR[:, 0], qR[:, 1:4], qR[:, 4], geo.n) * geo.Sabs[:, None]
     uf = 0.5 * (u[L] + u[Rr])
     Tf = 0.5 * (T[L] + T[Rr])
     muf = viscosity(Tf, mu0, omega)
@@ -284,7 +284,7 @@ def residual(geo, bc_state, U, hot_sigma, hot_q, mu0, omega, bface_corr=None):
         idx = np.nonzero(ff)[0]
         c = C[idx]
         sr = st[idx]
-        Fb[idx] = hllc(rho[c], u[c], p[c], sr[:, 0], sr[:, 1:4], sr[:, 0] * sr[:, 4],
+        Fb[idx] = kfvs(rho[c], u[c], p[c], sr[:, 0], sr[:, 1:4], sr[:, 0] * sr[:, 4],
                        geo.bn[idx]) * geo.bSabs[idx, None]
         # the cell's high-order terms cross the far-field face unchanged (no NSF part)
         Sb = geo.bS[idx]

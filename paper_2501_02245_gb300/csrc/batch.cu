@@ -27,7 +27,8 @@ __device__ __forceinline__ void batch_item(const BatchSolve& B, int vtile, int l
     Vel<T, VPT> V;
     make_vel<T, VPT>(a.vg, (long long)vtile * (32 * VPT), lane, V);
     S* f = (S*)B.f;
-    for (int pass = pass0; pass < pass1; ++pass) {
+    for (int step = pass0; step < pass1; ++step) {   // step 0: backward pass, step 1: forward pass
+        const int pass = 1 - step;
         for (int hh = 0; hh < a.H; ++hh) {
             const int h = pass ? (a.H - 1 - hh) : hh;
             const int kb = __ldg(a.hp_off + h), ke = __ldg(a.hp_off + h + 1);
@@ -126,7 +127,7 @@ static int grid_nc(int shape) {
 
 int batch_grid(int shape, int nc) { return nc == 1 ? grid_nc<1>(shape) : grid_nc<3>(shape); }
 
-// Passes pass0 .. pass1-1 (0 = forward, 1 = backward) of every item.
+// Steps pass0 .. pass1-1 of every item: step 0 is the backward pass, step 1 the forward pass.
 void launch_sweep_batch(int shape, int nc, const BatchSolve* d_solves, const int2* d_items, int n_items,
                         int* d_ticket, int grid, cudaStream_t st, int pass0, int pass1) {
     cudaMemsetAsync(d_ticket, 0, sizeof(int), st);

@@ -252,12 +252,12 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     phase_begin(c, GSIS_PH_CELLEQ);
     stage_cell_eq(c);
     phase_end(c, GSIS_PH_CELLEQ);
-    // 2. kinetic step: forward and backward Gauss-Seidel passes
+    // 2. kinetic step: backward (towards the low-index walls) then forward Gauss-Seidel pass
     used[GSIS_PH_SWEEP] = true;
     phase_begin(c, GSIS_PH_SWEEP);
-    launch_sweep(c, 0);
-    launch_wall_rho(c);
     launch_sweep(c, 1);
+    launch_wall_rho(c);
+    launch_sweep(c, 0);
     phase_end(c, GSIS_PH_SWEEP);
     used[GSIS_PH_MOMENTS] = true;
     phase_begin(c, GSIS_PH_MOMENTS);
@@ -504,7 +504,7 @@ gsis_status build_plan(BatchPlan* P) {
             for (gsis_ctx* c : P->ctxs) launch_wall_rho(c);
             launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
                                1, 2);
-        } else {
+        } else {   // both passes in one launch
             launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
                                0, 2);
         }

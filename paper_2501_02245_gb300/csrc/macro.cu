@@ -3,14 +3,19 @@
 //
 // Flux and relaxation choices (the paper defers them to another work; the
 // same choices are made in the CPU reference):
-//  * inviscid: HLLC with Davis wave speeds on index-space MUSCL-minmod states
-//    of (rho, u, p), first order next to boundaries;
+//  * inviscid: kinetic flux-vector splitting (the Euler flux the
+//    discrete-velocity upwind scheme carries for Maxwellian states, in closed
+//    form) on index-space MUSCL-minmod states of (rho, u, p), first order
+//    next to boundaries;
 //  * viscous: NSF from the mean of the two cells' least-squares gradients
 //    corrected along the line of centres, at the mean cell u and T, plus the
 //    mean of the two cells' HoT;
-//  * far field: HLLC against the boundary state plus the cell's HoT;
+//  * far field: the same splitting against the boundary state plus the
+//    cell's HoT;
 //    wall: cell pressure, no mass flux, NSF at u = 0 and T = T_w from a
-//    one-sided gradient, plus the cell's HoT;
+//    one-sided gradient; at the wall of a DVM cell plus the frozen difference
+//    between the kinetic wall flux of f^{n+1/2} and that NSF wall flux at
+//    W^{n+1/2};
 //  * DP-LUR pseudo-time relaxation (Wright, Candler & Bose 1998): scalar
 //    diagonal (1/CFL + 1/2) sum lambda |S| (+ V/dt with the time term of
 //    Eq. macro), k_sub Jacobi sweeps over Rusanov-split Euler flux changes.
@@ -188,40 +193,34 @@ void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim) {
 }
 
 // ---------------------------------------------------------------------------- fluxes
-// HLLC flux per unit area through the unit normal n (Toro, ch. 10).
-__device__ void hllc(double rL, const double* uL, double pL, double rR, const double* uR, double pR,
+// Flux carried by the molecules of the Maxwellian (r, u, T) that cross a
+// face of unit normal n in the direction sign*n (half-range moments of the
+// normal Gaussian N(u.n, T); tangential thermal motion in closed form),
+// added to F.
+__device__ __forceinline__ void half_range_add(double r, const double* u, double T, const double* n, double sign,
+                                               double* F) {
+    const double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    const double st = sqrt(T);
+    const double P = 0.5 * (1.0 + sign * erf(un / (1.4142135623730951 * st)));
+    const double D = sign * st * exp(-0.5 * un * un / T) * 0.3989422804014327;   // 1/sqrt(2 pi)
+    const double M0 = un * P + D;
+    const double M1 = (un * un + T) * P + un * D;
+    const double M2 = (un * un * un + 3.0 * un * T) * P + (un * un + 2.0 * T) * D;
+    const double ut[3] = {u[0] - un * n[0], u[1] - un * n[1], u[2] - un * n[2]};
+    F[0] += r * M0;
+    for (int i = 0; i < 3; ++i) F[1 + i] += r * (M1 * n[i] + ut[i] * M0);
+    F[4] += 0.5 * r * (M2 + (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2] + 2.0 * T) * M0);
+}
+
+// Kinetic flux-vector splitting per unit area through the unit normal n: the
+// left Maxwellian's molecules moving along +n plus the right one's moving
+// along -n -- the Euler flux that the discrete-velocity upwind scheme carries
+// for Maxwellian states.
+__device__ void kfvs(double rL, const double* uL, double pL, double rR, const double* uR, double pR,
                      const double* n, double* F) {
-    const double g = GAMMA;
-    const double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
-    const double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
-    const double aL = sqrt(g * pL / rL), aR = sqrt(g * pR / rR);
-    const double EL = pL / (g - 1.0) + 0.5 * rL * (uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2]);
-    const double ER = pR / (g - 1.0) + 0.5 * rR * (uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2]);
-    const double SL = fmin(unL - aL, unR - aR);
-    const double SR = fmax(unL + aL, unR + aR);
-    const double Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR));
-    // F_L if S_L >= 0; else F*_L if S* >= 0; else F*_R if S_R >= 0; else F_R
-    const bool left = (SL >= 0.0) || (Ss >= 0.0);
-    const bool use_plain = (SL >= 0.0) || !(left || SR >= 0.0);
-    const double r = left ? rL : rR;
-    const double* u = left ? uL : uR;
-    const double p = left ? pL : pR;
-    const double E = left ? EL : ER;
-    const double un = left ? unL : unR;
-    const double S = left ? SL : SR;
-    double Fk[5];
-    Fk[0] = r * un;
-    for (int d = 0; d < 3; ++d) Fk[1 + d] = r * u[d] * un + p * n[d];
-    Fk[4] = (E + p) * un;
-    if (use_plain) {
-        for (int q = 0; q < 5; ++q) F[q] = Fk[q];
-        return;
-    }
-    const double coef = r * (S - un) / (S - Ss);
-    const double e = E / r + (Ss - un) * (Ss + p / (r * (S - un)));
-    F[0] = Fk[0] + S * (coef - r);
-    for (int d = 0; d < 3; ++d) F[1 + d] = Fk[1 + d] + S * (coef * (u[d] + (Ss - un) * n[d]) - r * u[d]);
-    F[4] = Fk[4] + S * (coef * e - E);
+    for (int q = 0; q < 5; ++q) F[q] = 0.0;
+    half_range_add(rL, uL, pL / rL, n, 1.0, F);
+    half_range_add(rR, uR, pR / rR, n, -1.0, F);
 }
 
 __device__ __forceinline__ void euler_flux_dot(const double* U, const double* S, double* F) {
@@ -266,6 +265,7 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
             double ql[5];
             prim5(Wm + lo * 5, ql);
             for (int q = 0; q < 5; ++q) slL[q] = minmod(qL[q] - ql[q], qR[q] - qL[q]);
+
             (void)hi;
         }
     }
@@ -275,12 +275,13 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
             double qh[5];
             prim5(Wm + hi * 5, qh);
             for (int q = 0; q < 5; ++q) slR[q] = minmod(qR[q] - qL[q], qh[q] - qR[q]);
+
         }
     }
     double fl[5], fr[5];
     for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + 0.5 * slL[q]; fr[q] = qR[q] - 0.5 * slR[q]; }
     double Fv[5];
-    hllc(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, Fv);
+    kfvs(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, Fv);
     for (int q = 0; q < 5; ++q) Fv[q] *= Sabs;
     // viscous + HoT
     const double* wL = Wm + L * 5;
@@ -431,7 +432,7 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
             for (int i = 0; i < 3; ++i) eb[i] = a.xf[((long long)c * 6 + s) * 3 + i] - a.cen[c * 3 + i];
             const double bdist = sqrt(eb[0] * eb[0] + eb[1] * eb[1] + eb[2] * eb[2]);
             if (bc == GSIS_BC_FARFIELD) {
-                hllc(rho_c, u_c, p_c, st[0], st + 1, st[0] * st[4], nn, Fb);
+                kfvs(rho_c, u_c, p_c, st[0], st + 1, st[0] * st[4], nn, Fb);
                 for (int q = 0; q < 5; ++q) Fb[q] *= Sabs;
                 const double SigS[3] = {h[0] * So[0] + h[3] * So[1] + h[4] * So[2],
                                         h[3] * So[0] + h[1] * So[1] + h[5] * So[2],

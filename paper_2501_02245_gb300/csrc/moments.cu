@@ -357,8 +357,9 @@ __global__ void k_hot(int N, const int* __restrict__ cell2dvm, const double* __r
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const bool dvm = cell2dvm[c] >= 0;
-    for (int q = 0; q < HOTN; ++q)
+    for (int q = 0; q < HOTN; ++q) {
         hot[(long long)c * HOTN + q] = dvm ? kin[(long long)c * HOTN + q] - nsf[(long long)c * HOTN + q] : 0.0;
+    }
 }
 
 void launch_hot(gsis_ctx* c) {

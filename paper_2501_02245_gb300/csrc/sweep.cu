@@ -8,8 +8,10 @@
 // with slope = minmod(f_c - f_{c-d}, f_{c+d} - f_c) in index space when both
 // neighbours along d are DVM cells (else 0), and f_F^in the neighbour's MUSCL
 // face value, a Grad-13 interface distribution (NS neighbour), the far-field
-// corrected Maxwellian, or rho_w M_w (diffuse wall).  One forward and one
-// backward Gauss-Seidel pass over hyperplanes h = i+j+k.
+// corrected Maxwellian, or rho_w M_w (diffuse wall).  One backward (pass = 1,
+// decreasing hyperplane h = i+j+k, towards the low-index walls of the
+// O-grids) and one forward (pass = 0) Gauss-Seidel pass; the wall densities
+// are refreshed from the latest f between them.
 //
 // Parallel structure.  Every dependency of the update at (c, xi) is on the
 // same velocity xi, and cells of one hyperplane never depend on each other.

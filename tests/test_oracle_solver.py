@@ -7,7 +7,7 @@ from workloads.meshes import BC_FARFIELD, BC_WALL, BC_PERIODIC, BC_NONE
 from oracle import model as M
 from oracle import kinetic as K
 from oracle.mesh import Topology
-from oracle.macro import MacroGeometry, hllc, euler_flux_dot, residual, lsq_grad
+from oracle.macro import MacroGeometry, kfvs, _half_range, euler_flux_dot, residual, lsq_grad
 from oracle.gsis import OracleSolver, residual_eps, prim_to_U
 
 
@@ -55,17 +55,46 @@ def test_lsq_gradient_exact_for_linear_fields(mesh):
 
 
 # ----------------------------------------------------------------------------- macro fluxes
-def test_hllc_consistency_and_upwinding():
+def test_kfvs_consistency_and_supersonic_limit():
+    """Kinetic flux-vector splitting: a uniform state gives the Euler flux
+    exactly (the two half-range fluxes add up to the full-range moments); a
+    state moving along n at 9 thermal speeds sends no molecules back (the
+    backward half-range weight erfc(9/sqrt 2)/2 ~ 1e-19), so the flux is the
+    left state's Euler flux whatever the right state is."""
     rng = np.random.default_rng(1)
     F = 20
     r = rng.uniform(0.5, 2, F); u = rng.uniform(-1, 1, (F, 3)); p = rng.uniform(0.5, 2, F)
     n = rng.normal(size=(F, 3)); n /= np.linalg.norm(n, axis=1)[:, None]
     U = np.concatenate([r[:, None], r[:, None] * u, (1.5 * p + 0.5 * r * np.sum(u * u, 1))[:, None]], 1)
-    assert np.allclose(hllc(r, u, p, r, u, p, n), euler_flux_dot(U, n), rtol=1e-13, atol=1e-13)
-    # supersonic left-to-right: the flux is the left state's flux
-    u2 = 5.0 * n
-    U2 = np.concatenate([r[:, None], r[:, None] * u2, (1.5 * p + 0.5 * r * 25.0)[:, None]], 1)
-    assert np.allclose(hllc(r, u2, p, r * 2, u2 * 0.9, p * 3, n), euler_flux_dot(U2, n), rtol=1e-13)
+    assert np.allclose(kfvs(r, u, p, r, u, p, n), euler_flux_dot(U, n), rtol=1e-13, atol=1e-13)
+    T = p / r
+    u2 = (9.0 * np.sqrt(T))[:, None] * n
+    U2 = np.concatenate([r[:, None], r[:, None] * u2, (1.5 * p + 0.5 * r * np.sum(u2 * u2, 1))[:, None]], 1)
+    rR, uR2 = r * 2, (9.0 * np.sqrt(3 * p / (r * 2)))[:, None] * n   # right state also at 9 thermal speeds along +n
+    assert np.allclose(kfvs(r, u2, p, rR, uR2, 3 * p, n), euler_flux_dot(U2, n), rtol=1e-13, atol=1e-14)
+
+
+def test_kfvs_effusion_closed_form_and_quadrature():
+    """Gas at rest: the one-way flux through a face is the effusion flux
+    rho sqrt(T / (2 pi)) of mass and rho T sqrt(2 T / pi) of energy (kinetic
+    theory), and the normal momentum flux is p / 2.  A moving state: the
+    closed-form half-range moments equal a brute-force sum over a fine
+    uniform velocity grid of the Maxwellian's molecules with xi.n > 0."""
+    r, T = np.array([1.7]), np.array([2.3])
+    n = np.array([[0.0, 0.0, 1.0]])
+    F = _half_range(r, np.zeros((1, 3)), T, n, 1.0)[0]
+    assert abs(F[0] / (r[0] * np.sqrt(T[0] / (2 * np.pi))) - 1) < 1e-14
+    assert abs(F[3] / (0.5 * r[0] * T[0]) - 1) < 1e-14
+    assert abs(F[4] / (r[0] * T[0] * np.sqrt(2 * T[0] / np.pi)) - 1) < 1e-14
+    u = np.array([[0.7, -0.4, 0.3]]); nn = np.array([[0.6, 0.0, 0.8]]); T = np.array([1.4])
+    vg = M.VelocityGrid((96, 96, 96), (-9, -9, -9), (9, 9, 9))
+    f = M.maxwellian(1.0, u[0], T[0], vg.xi)
+    xn = vg.xi @ nn[0]
+    g = vg.w * np.where(xn > 0, xn * f, 0.0)
+    brute = np.array([g.sum(), g @ vg.xi[:, 0], g @ vg.xi[:, 1], g @ vg.xi[:, 2],
+                      0.5 * g @ np.sum(vg.xi ** 2, 1)])
+    F = _half_range(np.array([1.0]), u, T, nn, 1.0)[0]
+    assert np.max(np.abs(F - brute)) < 2e-3 * np.max(np.abs(F))   # midpoint rule across the xi.n = 0 kink
 
 
 def test_macro_residual_vanishes_for_uniform_stream_on_ogrid():

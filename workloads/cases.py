@@ -88,12 +88,13 @@ def shock_1d_case(Ma=2.0, n_cells=200, half_width=25.0, nv=(48, 24, 24), vmax=6.
 def cylinder_case(Ma=5.0, Kn=0.01, n_r=128, n_theta=128, nv=(48, 48, 24),
                   vbox=((-14.0, 14.0), (-12.0, 12.0), (-12.0, 12.0)), wall_T=2.0,
                   adaptive=True, Kn_ref=0.01, r_out=5.0, first_cell_mfp=0.1,
-                  macro_steps=400, cfl=5.0, k_sub=2, iterations=60, presolve_max_blocks=50):
+                  macro_steps=400, cfl=5.0, k_sub=2, iterations=60, presolve_max_blocks=50, relax=0.7):
     """Hypersonic flow past a cylinder of unit diameter on a body-fitted O-grid.
 
     First radial cell = first_cell_mfp free-stream mean free paths (= Kn * D).
-    The initial field is the uniform free stream; adaptive runs start with a
-    Navier-Stokes presolve.
+    The initial field is the uniform free stream; runs start with a
+    Navier-Stokes presolve.  The synthetic correction is under-relaxed (relax)
+    against the entropy mode of the stagnation region.
     """
     u = Ma * np.sqrt(GAMMA)
     Winf = np.array([1.0, u, 0.0, 0.0, 1.0])
@@ -102,15 +103,16 @@ def cylinder_case(Ma=5.0, Kn=0.01, n_r=128, n_theta=128, nv=(48, 48, 24),
     vg = VGrid(tuple(nv), tuple(b[0] for b in vbox), tuple(b[1] for b in vbox))
     return Case(f"cylinder_Ma{Ma:g}_Kn{Kn:g}_{n_r}x{n_theta}", mesh, vg, W0, Kn=Kn,
                 adaptive=adaptive, Kn_ref=Kn_ref, macro_steps=macro_steps, cfl=cfl, k_sub=k_sub,
-                iterations=iterations, presolve_max_blocks=presolve_max_blocks,
+                iterations=iterations, presolve_max_blocks=presolve_max_blocks, relax=relax,
                 extra={"Winf": Winf, "Ma": Ma, "wall_T": wall_T})
 
 
 def sphere_case(Ma=5.0, Kn=0.005, n_r=96, n_pol=64, n_az=64, nv=(48, 48, 48),
                 vbox=((-14.0, 14.0), (-12.0, 12.0), (-12.0, 12.0)), wall_T=2.0,
                 adaptive=True, Kn_ref=0.01, r_out=5.0, first_cell_mfp=0.1,
-                macro_steps=400, cfl=5.0, k_sub=2, iterations=60, presolve_max_blocks=50):
-    """Hypersonic flow past a sphere of unit diameter on a spherical O-grid."""
+                macro_steps=400, cfl=5.0, k_sub=2, iterations=60, presolve_max_blocks=50, relax=0.7):
+    """Hypersonic flow past a sphere of unit diameter on a spherical O-grid
+    (under-relaxed synthetic correction, as for the cylinder)."""
     u = Ma * np.sqrt(GAMMA)
     Winf = np.array([1.0, u, 0.0, 0.0, 1.0])
     mesh = sphere_ogrid(n_r, n_pol, n_az, 0.5, r_out, first_cell_mfp * Kn, wall_T, Winf)
@@ -118,7 +120,7 @@ def sphere_case(Ma=5.0, Kn=0.005, n_r=96, n_pol=64, n_az=64, nv=(48, 48, 48),
     vg = VGrid(tuple(nv), tuple(b[0] for b in vbox), tuple(b[1] for b in vbox))
     return Case(f"sphere_Ma{Ma:g}_Kn{Kn:g}_{n_r}x{n_pol}x{n_az}", mesh, vg, W0, Kn=Kn,
                 adaptive=adaptive, Kn_ref=Kn_ref, macro_steps=macro_steps, cfl=cfl, k_sub=k_sub,
-                iterations=iterations, presolve_max_blocks=presolve_max_blocks,
+                iterations=iterations, presolve_max_blocks=presolve_max_blocks, relax=relax,
                 extra={"Winf": Winf, "Ma": Ma, "wall_T": wall_T})
 
 
