@@ -155,7 +155,8 @@ def traffic_from_profile(config, dtype):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    sha = source_sha(["paper_2501_02245_gb300/csrc/sweep.cu", "paper_2501_02245_gb300/csrc/gsis_device.cuh"])
+    sha = source_sha(["paper_2501_02245_gb300/csrc/sweep.cu", "paper_2501_02245_gb300/csrc/sweep_device.cuh",
+                      "paper_2501_02245_gb300/csrc/gsis_device.cuh"])
     if d.get("sweep_src_sha") != sha:
         return None
     return d.get("dram_bytes_per_launch_full")
@@ -282,6 +283,7 @@ def run_gsis(args):
                        "n_dvm": rep["n_dvm"], "n_cells": case.mesh.ncell, "n_v": rep["n_v"],
                        "vdf_bytes": rep["vdf_bytes"], "l2": "VDF (%.1f GB) larger than L2" % (rep["vdf_bytes"] / 1e9),
                        "presolve_blocks": rep0["presolve_blocks"], "eps_last": rep["eps"],
+                       "sweep_tile": s.tuning_info(),
                        "phase_ms_per_step": {k: v / args.steps for k, v in rep["phase_ms"].items() if v > 0}},
             "roofline": roof, "clocks": ck, "gpu_launches": rep["kernel_launches"]}
     s.close()

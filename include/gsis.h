@@ -226,6 +226,14 @@ gsis_status gsis_debug_set_region(gsis_ctx* ctx, const uint8_t* flags);
  * time. */
 gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_report* reports);
 
+/* Human-readable result of the sweep's tile-shape autotuning for this
+ * context (chosen shape and the timing of every candidate), or "" before the
+ * first iteration.  Each context times the candidate shapes of its kinetic
+ * sweep once per DVM region (on a snapshot of its VDF, restored afterwards;
+ * results cached per problem shape for the life of the process).  The string
+ * is owned by the context. */
+const char* gsis_tuning_info(gsis_ctx* ctx);
+
 /* Human-readable description of the recorded batch plan for this ordered
  * context list (work items, autotuned tile shape and the timings of every
  * candidate, grid, graph nodes), or "" if none.  The string lives until the

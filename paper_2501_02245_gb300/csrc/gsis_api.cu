@@ -252,6 +252,10 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     phase_begin(c, GSIS_PH_CELLEQ);
     stage_cell_eq(c);
     phase_end(c, GSIS_PH_CELLEQ);
+    if (c->sweep_shape < 0 || c->tuned_Nd != c->Nd) {   // (re)tune the sweep tile shape for this region
+        gsis_status st = tune_sweep(c);
+        if (st != GSIS_OK) return st;
+    }
     // 2. kinetic step: backward (towards the low-index walls) then forward Gauss-Seidel pass
     used[GSIS_PH_SWEEP] = true;
     phase_begin(c, GSIS_PH_SWEEP);
@@ -1085,6 +1089,11 @@ gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_repo
         }
     }
     return result;
+}
+
+const char* gsis_tuning_info(gsis_ctx* c) {
+    if (!c) return "";
+    return c->sweep_info.c_str();
 }
 
 const char* gsis_batch_info(gsis_ctx** ctxs, int n) {

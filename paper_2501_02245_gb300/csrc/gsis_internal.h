@@ -153,6 +153,9 @@ struct gsis_ctx {
     int* enter_of = nullptr;       // [Nd] entering slot of each DVM cell or -1
     int* d_count = nullptr;        // scratch counters
     gsis::MacroJob* d_job = nullptr;   // device copy of this solve's fused macro job
+    int sweep_shape = -1;          // autotuned sweep tile shape (-1: not tuned yet)
+    long long tuned_Nd = -1;       // DVM cell count the shape was tuned for
+    std::string sweep_info;        // tuning result, for gsis_tuning_info
     int* h_count = nullptr;
 
     // bookkeeping
@@ -177,6 +180,7 @@ void launch_correction_records(gsis_ctx* c);
 void launch_seed_records(gsis_ctx* c, int n_enter, int grad13);
 // sweep.cu
 void launch_sweep(gsis_ctx* c, int pass);
+gsis_status tune_sweep(gsis_ctx* c);
 // batch.cu (persistent batched sweep; BatchSolve is declared in sweep_device.cuh)
 struct BatchSolve;
 int batch_num_shapes();

@@ -30,6 +30,8 @@
 // FP32 for FP32 / BF16 / FP16 storage.  NC = number of index directions that
 // carry flux and of face-normal components that can be nonzero (1, 2 or 3 for
 // 1D, 2D and 3D meshes); the rest is skipped.
+#include <map>
+#include <string>
 #include "sweep_device.cuh"
 
 namespace gsis {
@@ -70,6 +72,61 @@ static void sweep_t(gsis_ctx* c, const SweepArgs& a, int pass) {
     }
 }
 
+// ---------------------------------------------------------------------------- tile shapes
+// Candidate (warps per block G, velocities per thread VPT, cells per warp
+// step CB) of the 2D/3D sweep, timed by the autotuner on the solve itself.
+// 1D meshes (one cell per hyperplane) use one warp per block.
+struct SweepShape {
+    int g, vpt, cb;
+    const char* name;
+};
+static const SweepShape kShapesF64[] = {
+    {2, 1, 2, "g2_v1_c2"}, {1, 1, 2, "g1_v1_c2"}, {4, 1, 1, "g4_v1_c1"}, {2, 1, 1, "g2_v1_c1"}};
+static const SweepShape kShapesF32[] = {
+    {4, 2, 2, "g4_v2_c2"}, {4, 1, 2, "g4_v1_c2"}, {8, 1, 1, "g8_v1_c1"},
+    {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"}, {2, 2, 2, "g2_v2_c2"}};
+
+int sweep_num_shapes(int dtype) {
+    return dtype == GSIS_F64 ? (int)(sizeof(kShapesF64) / sizeof(kShapesF64[0]))
+                             : (int)(sizeof(kShapesF32) / sizeof(kShapesF32[0]));
+}
+const char* sweep_shape_name(int dtype, int shape) {
+    if (shape < 0 || shape >= sweep_num_shapes(dtype)) return "?";
+    return dtype == GSIS_F64 ? kShapesF64[shape].name : kShapesF32[shape].name;
+}
+
+template <typename S>
+static void sweep_f32_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape) {
+    if (c->normal_components == 1) { sweep_t<S, float, 1, 2, 1>(c, a, pass); return; }
+    switch (shape) {
+        case 1: sweep_t<S, float, 4, 1, 2>(c, a, pass); break;
+        case 2: sweep_t<S, float, 8, 1, 1>(c, a, pass); break;
+        case 3: sweep_t<S, float, 4, 1, 1>(c, a, pass); break;
+        case 4: sweep_t<S, float, 8, 2, 1>(c, a, pass); break;
+        case 5: sweep_t<S, float, 2, 2, 2>(c, a, pass); break;
+        default: sweep_t<S, float, 4, 2, 2>(c, a, pass); break;
+    }
+}
+
+static void sweep_f64_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape) {
+    if (c->normal_components == 1) { sweep_t<double, double, 1, 1, 1>(c, a, pass); return; }
+    switch (shape) {
+        case 1: sweep_t<double, double, 1, 1, 2>(c, a, pass); break;
+        case 2: sweep_t<double, double, 4, 1, 1>(c, a, pass); break;
+        case 3: sweep_t<double, double, 2, 1, 1>(c, a, pass); break;
+        default: sweep_t<double, double, 2, 1, 2>(c, a, pass); break;
+    }
+}
+
+static void launch_sweep_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape) {
+    switch (c->p.vdf_dtype) {
+        case GSIS_F64: sweep_f64_shape(c, a, pass, shape); break;
+        case GSIS_F32: sweep_f32_shape<float>(c, a, pass, shape); break;
+        case GSIS_BF16: sweep_f32_shape<__nv_bfloat16>(c, a, pass, shape); break;
+        default: sweep_f32_shape<__half>(c, a, pass, shape); break;
+    }
+}
+
 SweepArgs sweep_args(gsis_ctx* c) {
     SweepArgs a;
     a.H = c->m.H;
@@ -93,14 +150,75 @@ SweepArgs sweep_args(gsis_ctx* c) {
 void launch_sweep(gsis_ctx* c, int pass) {
     if (c->Nd == 0) return;
     const SweepArgs a = sweep_args(c);
-    switch (c->p.vdf_dtype) {
-        case GSIS_F64: sweep_t<double, double, 2, 1, 2>(c, a, pass); break;
-        case GSIS_F32: sweep_t<float, float, 4, 2, 2>(c, a, pass); break;
-        case GSIS_BF16: sweep_t<__nv_bfloat16, float, 4, 2, 2>(c, a, pass); break;
-        default: sweep_t<__half, float, 4, 2, 2>(c, a, pass); break;
-    }
+    launch_sweep_shape(c, a, pass, c->sweep_shape < 0 ? 0 : c->sweep_shape);
     c->launches++;
     c->sweep_launches++;
+}
+
+// Autotuner of the sweep's tile shape: each candidate runs one backward and
+// one forward pass (after one untimed warm-up pair) on a snapshot of the VDF,
+// which is restored afterwards; the fastest is kept and cached for the life
+// of the process per (storage type, mesh dimension, DVM cells, velocities,
+// hyperplanes).  Without memory for the snapshot the first shape is used.
+static std::map<std::string, int>& sweep_cache() {
+    static std::map<std::string, int> m;
+    return m;
+}
+
+gsis_status tune_sweep(gsis_ctx* c) {
+    c->tuned_Nd = c->Nd;
+    if (c->Nd == 0 || c->normal_components == 1) {
+        c->sweep_shape = 0;
+        c->sweep_info = "1D or empty: fixed shape";
+        return GSIS_OK;
+    }
+    const std::string key = std::to_string(c->p.vdf_dtype) + "/" + std::to_string(c->normal_components) + "/" +
+                            std::to_string(c->Nd) + "/" + std::to_string(c->vg.Nv) + "/" + std::to_string(c->m.H);
+    auto hit = sweep_cache().find(key);
+    if (hit != sweep_cache().end()) {
+        c->sweep_shape = hit->second;
+        c->sweep_info = std::string("tile ") + sweep_shape_name(c->p.vdf_dtype, c->sweep_shape) + " (cached)";
+        return GSIS_OK;
+    }
+    const size_t bytes = (size_t)c->Nd * c->vg.Nv * vdf_elem_bytes(c->p.vdf_dtype);
+    void* snap = dev_alloc(c, bytes);
+    if (!snap) {
+        c->sweep_shape = 0;
+        c->sweep_info = std::string("tile ") + sweep_shape_name(c->p.vdf_dtype, 0) + " (not tuned: no memory for a snapshot)";
+        return GSIS_OK;
+    }
+    cudaMemcpyAsync(snap, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const SweepArgs a = sweep_args(c);
+    const int ns = sweep_num_shapes(c->p.vdf_dtype);
+    int best = 0;
+    float best_ms = 1e30f;
+    std::string info = "tile timings (ms per pass pair):";
+    for (int sh = 0; sh < ns; ++sh) {
+        launch_sweep_shape(c, a, 1, sh);
+        launch_sweep_shape(c, a, 0, sh);
+        cudaEventRecord(e0, c->stream);
+        launch_sweep_shape(c, a, 1, sh);
+        launch_sweep_shape(c, a, 0, sh);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        info += std::string(" ") + sweep_shape_name(c->p.vdf_dtype, sh) + "=" + std::to_string(ms);
+        if (ms < best_ms) { best_ms = ms; best = sh; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemcpyAsync(c->f, snap, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "sweep autotuning")) return GSIS_ERR_CUDA;
+    dev_free(c, snap);
+    if (!cuda_ok(c, cudaGetLastError(), "sweep autotuning")) return GSIS_ERR_CUDA;
+    c->sweep_shape = best;
+    sweep_cache()[key] = best;
+    c->sweep_info = std::string("tile ") + sweep_shape_name(c->p.vdf_dtype, best) + " (autotuned; " + info + ")";
+    return GSIS_OK;
 }
 
 }  // namespace gsis

@@ -30,6 +30,37 @@ __device__ __forceinline__ T minmod_t(T a, T b) {
     return a * b > T(0) ? m : T(0);
 }
 
+// minmod(a, b) and x > 0 with the decisions taken on the bit patterns: for
+// FP64 this keeps the comparisons and the sign product off the FP64 pipe
+// (GB300 issues FP64 at 1/64 of the FP32 rate), with the same result as
+// minmod_t for finite values (magnitudes of IEEE doubles order like their
+// bit patterns with the sign bit cleared; +-0 never shares a sign).
+template <typename T> __device__ __forceinline__ T mm_t(T a, T b);
+template <> __device__ __forceinline__ float mm_t<float>(float a, float b) { return minmod_t<float>(a, b); }
+template <> __device__ __forceinline__ double mm_t<double>(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    const bool same = (ia ^ ib) >= 0 && ma != 0 && mb != 0;
+    return same ? (ma < mb ? a : b) : 0.0;
+}
+template <typename T> __device__ __forceinline__ bool pos_t(T x);
+template <> __device__ __forceinline__ bool pos_t<float>(float x) { return x > 0.0f; }
+template <> __device__ __forceinline__ bool pos_t<double>(double x) { return __double_as_longlong(x) > 0; }
+
+// n / d for d > 0 in the normal range.  FP64: Newton-Raphson refinement of a
+// single-precision reciprocal seed (r <- r (2 - d r) doubles the correct
+// bits: ~24 -> ~48), the quotient q = n r and one residual correction
+// q <- q + r (n - d q); relative error a few units of 2^-53.  FP32: IEEE
+// division.
+template <typename T> __device__ __forceinline__ T div_t(T n, T d);
+template <> __device__ __forceinline__ float div_t<float>(float n, float d) { return n / d; }
+template <> __device__ __forceinline__ double div_t<double>(double n, double d) {
+    double r = (double)__frcp_rn(__double2float_rn(d));
+    r = r * fma(-d, r, 2.0);
+    double q = n * r;
+    return fma(fma(-d, q, n), r, q);
+}
+
 template <typename T>
 __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
@@ -123,50 +154,60 @@ __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__
             const int kl = m[b].kd[2 * d], kh = m[b].kd[2 * d + 1];
             if (kl == SK_NONE && kh == SK_NONE) continue;
             const bool both = kl == SK_DVM && kh == SK_DVM;
+            const bool l2 = m[b].n2[2 * d] >= 0, h2 = m[b].n2[2 * d + 1] >= 0;
+            // interface / boundary distributions of the non-DVM sides (the side
+            // kinds are the same for every lane of the warp: uniform branches)
+            const T *bsl = nullptr, *btl = nullptr, *bsh = nullptr, *bth = nullptr;
+            T scl = T(1), sch = T(1);
+            if (kl == SK_GHOST || kl == SK_FAR || kl == SK_WALL) {
+                const Records& R = kl == SK_GHOST ? a.recGhost : a.recBC;
+                bsl = RecT<T>::scal(R, m[b].rf[2 * d]);
+                btl = RecT<T>::tab(R, m[b].rf[2 * d], NT);
+                if (kl == SK_WALL) scl = m[b].wall[2 * d];
+            }
+            if (kh == SK_GHOST || kh == SK_FAR || kh == SK_WALL) {
+                const Records& R = kh == SK_GHOST ? a.recGhost : a.recBC;
+                bsh = RecT<T>::scal(R, m[b].rf[2 * d + 1]);
+                bth = RecT<T>::tab(R, m[b].rf[2 * d + 1], NT);
+                if (kh == SK_WALL) sch = m[b].wall[2 * d + 1];
+            }
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const int s = 2 * d + side;
-                const int kq = side ? kh : kl;
-                if (kq == SK_NONE) continue;
-                const T hs = side ? T(0.5) : T(-0.5);
-                const bool has2 = m[b].n2[s] >= 0;
-                const T* bs = nullptr;
-                const T* bt = nullptr;
-                T scale = T(1);
-                if (kq == SK_GHOST) {
-                    bs = RecT<T>::scal(a.recGhost, m[b].rf[s]);
-                    bt = RecT<T>::tab(a.recGhost, m[b].rf[s], NT);
-                } else if (kq == SK_FAR || kq == SK_WALL) {
-                    bs = RecT<T>::scal(a.recBC, m[b].rf[s]);
-                    bt = RecT<T>::tab(a.recBC, m[b].rf[s], NT);
-                    if (kq == SK_WALL) scale = m[b].wall[s];
-                }
-#pragma unroll
-                for (int u = 0; u < VPT; ++u) {
-                    T xn = V.x0[u] * m[b].S[s][0];
-                    if (NC >= 2) xn += V.x1[u] * m[b].S[s][NC >= 2 ? 1 : 0];
-                    if (NC >= 3) xn += V.x2[u] * m[b].S[s][NC >= 3 ? 2 : 0];
-                    const T own = both ? minmod_t<T>(fc[b][u] - lo[b][d][u], hi[b][d][u] - fc[b][u]) : T(0);
+            for (int u = 0; u < VPT; ++u) {
+                const T c0 = fc[b][u], vl = lo[b][d][u], vh = hi[b][d][u];
+                // half the cell's own limited slope (outgoing face values c0 -+ hown)
+                const T hown = both ? T(0.5) * mm_t<T>(c0 - vl, vh - c0) : T(0);
+                if (kl != SK_NONE) {
+                    T xn = V.x0[u] * m[b].S[2 * d][0];
+                    if (NC >= 2) xn += V.x1[u] * m[b].S[2 * d][NC >= 2 ? 1 : 0];
+                    if (NC >= 3) xn += V.x2[u] * m[b].S[2 * d][NC >= 3 ? 2 : 0];
                     T fin;
-                    if (kq == SK_DVM) {
-                        const T fn = side ? hi[b][d][u] : lo[b][d][u];
-                        const T sn = has2 ? (side ? minmod_t<T>(fn - fc[b][u], hi2[b][d][u] - fn)
-                                                  : minmod_t<T>(fn - lo2[b][d][u], fc[b][u] - fn))
-                                          : T(0);
-                        fin = fn - hs * sn;
-                    } else {
-                        fin = scale * eval_recT<T>(bs, bt, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
-                    }
-                    const bool out = xn > T(0);
+                    if (kl == SK_DVM)   // neighbour's face value: its value plus half its limited slope
+                        fin = vl + (l2 ? T(0.5) * mm_t<T>(vl - lo2[b][d][u], c0 - vl) : T(0));
+                    else
+                        fin = scl * eval_recT<T>(bsl, btl, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
+                    const bool out = pos_t<T>(xn);
                     den[u] += out ? xn : T(0);
-                    num[u] -= out ? xn * hs * own : xn * fin;
+                    num[u] -= xn * (out ? -hown : fin);
+                }
+                if (kh != SK_NONE) {
+                    T xn = V.x0[u] * m[b].S[2 * d + 1][0];
+                    if (NC >= 2) xn += V.x1[u] * m[b].S[2 * d + 1][NC >= 2 ? 1 : 0];
+                    if (NC >= 3) xn += V.x2[u] * m[b].S[2 * d + 1][NC >= 3 ? 2 : 0];
+                    T fin;
+                    if (kh == SK_DVM)
+                        fin = vh - (h2 ? T(0.5) * mm_t<T>(vh - c0, hi2[b][d][u] - vh) : T(0));
+                    else
+                        fin = sch * eval_recT<T>(bsh, bth, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
+                    const bool out = pos_t<T>(xn);
+                    den[u] += out ? xn : T(0);
+                    num[u] -= xn * (out ? hown : fin);
                 }
             }
         }
         S* fk = f + (long long)k * Nv;
 #pragma unroll
         for (int u = 0; u < VPT; ++u)
-            if (V.on[u]) stT<T, S>(fk + V.v[u], num[u] / den[u]);
+            if (V.on[u]) stT<T, S>(fk + V.v[u], div_t<T>(num[u], den[u]));
     }
 }
 
