@@ -226,6 +226,15 @@ gsis_status gsis_debug_set_region(gsis_ctx* ctx, const uint8_t* flags);
  * time. */
 gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_report* reports);
 
+/* Test hook: run the kinetic sweep of this context with the named tile shape
+ * from now on instead of the autotuned one (names as reported by
+ * gsis_tuning_info, e.g. "g4_v1_c1", "ring_w8_v32"); starts the context
+ * (presolve, region) if needed.  Every shape computes the same result.
+ * GSIS_ERR_ARG for an unknown name or a shape that cannot run this problem
+ * (the shared-memory window shapes need a 2D mesh whose hyperplane window
+ * fits in shared memory).  The paper has no counterpart. */
+gsis_status gsis_debug_set_sweep_tile(gsis_ctx* ctx, const char* name);
+
 /* Human-readable result of the sweep's tile-shape autotuning for this
  * context (chosen shape and the timing of every candidate), or "" before the
  * first iteration.  Each context times the candidate shapes of its kinetic

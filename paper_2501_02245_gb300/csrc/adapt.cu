@@ -4,6 +4,8 @@
 // h = i + j + k (then by flat index), with the cell-indirection maps, the
 // per-side connectivity the sweep needs, the Grad-13 ghost list and the remap
 // of the VDF rows (survivors copied, entering cells seeded).
+#include <algorithm>
+#include <vector>
 #include "gsis_device.cuh"
 
 namespace gsis {
@@ -313,6 +315,15 @@ int build_region(gsis_ctx* c) {
     c->n_ghost = c->h_count[0];
     const int n_enter = c->h_count[1];
     c->Nd = Nd_new;
+    {   // most DVM cells in one hyperplane (shared-memory window of the sweep)
+        std::vector<int> off(H + 1);
+        if (!cuda_ok(c, cudaMemcpy(off.data(), c->hp_off, (H + 1) * sizeof(int), cudaMemcpyDeviceToHost),
+                     "hyperplane offsets"))
+            return -1;
+        int mx = 0;
+        for (int h = 0; h < H; ++h) mx = std::max(mx, off[h + 1] - off[h]);
+        c->max_hp = mx;
+    }
     if (n_enter > 0) {
         const int grad13 = c->p.adaptive ? 1 : 0;
         if (grad13) launch_nsf(c, c->W, c->nsf);

@@ -252,7 +252,7 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     phase_begin(c, GSIS_PH_CELLEQ);
     stage_cell_eq(c);
     phase_end(c, GSIS_PH_CELLEQ);
-    if (c->sweep_shape < 0 || c->tuned_Nd != c->Nd) {   // (re)tune the sweep tile shape for this region
+    if (!c->sweep_forced && (c->sweep_shape < 0 || c->tuned_Nd != c->Nd)) {   // (re)tune for this region
         gsis_status st = tune_sweep(c);
         if (st != GSIS_OK) return st;
     }
@@ -1089,6 +1089,18 @@ gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_repo
         }
     }
     return result;
+}
+
+gsis_status gsis_debug_set_sweep_tile(gsis_ctx* c, const char* name) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!name) return set_err(c, GSIS_ERR_ARG, "tile name is NULL");
+    if (!c->started) {
+        if (!c->mesh_set || !c->vgrid_set) return set_err(c, GSIS_ERR_STATE, "set the mesh and velocity grid first");
+        st = start(c);
+        if (st != GSIS_OK) return st;
+    }
+    return force_sweep_shape(c, name);
 }
 
 const char* gsis_tuning_info(gsis_ctx* c) {

@@ -154,6 +154,8 @@ struct gsis_ctx {
     int* d_count = nullptr;        // scratch counters
     gsis::MacroJob* d_job = nullptr;   // device copy of this solve's fused macro job
     int sweep_shape = -1;          // autotuned sweep tile shape (-1: not tuned yet)
+    int max_hp = 0;                // most DVM cells in one hyperplane (current region)
+    bool sweep_forced = false;     // tile shape fixed by gsis_debug_set_sweep_tile
     long long tuned_Nd = -1;       // DVM cell count the shape was tuned for
     std::string sweep_info;        // tuning result, for gsis_tuning_info
     int* h_count = nullptr;
@@ -181,6 +183,11 @@ void launch_seed_records(gsis_ctx* c, int n_enter, int grad13);
 // sweep.cu
 void launch_sweep(gsis_ctx* c, int pass);
 gsis_status tune_sweep(gsis_ctx* c);
+gsis_status force_sweep_shape(gsis_ctx* c, const char* name);
+// sweep_ring.cu (shared-memory hyperplane window, 2D meshes)
+struct SweepArgs;
+size_t ring_bytes(gsis_ctx* c, int vt);
+bool launch_sweep_ring(gsis_ctx* c, const SweepArgs& a, int pass, int which);
 // batch.cu (persistent batched sweep; BatchSolve is declared in sweep_device.cuh)
 struct BatchSolve;
 int batch_num_shapes();

@@ -86,12 +86,20 @@ static const SweepShape kShapesF32[] = {
     {4, 2, 2, "g4_v2_c2"}, {4, 1, 2, "g4_v1_c2"}, {8, 1, 1, "g8_v1_c1"},
     {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"}, {2, 2, 2, "g2_v2_c2"}};
 
-int sweep_num_shapes(int dtype) {
+// Candidates after the register-stencil shapes: the shared-memory window
+// sweep (sweep_ring.cu) with 8 warps x 32, 4 warps x 32 and 8 warps x 64
+// velocities (2D meshes whose hyperplane window fits in shared memory).
+static const char* kRingNames[] = {"ring_w8_v32", "ring_w4_v32", "ring_w8_v64"};
+constexpr int kRingShapes = 3;
+
+static int base_shapes(int dtype) {
     return dtype == GSIS_F64 ? (int)(sizeof(kShapesF64) / sizeof(kShapesF64[0]))
                              : (int)(sizeof(kShapesF32) / sizeof(kShapesF32[0]));
 }
+int sweep_num_shapes(int dtype) { return base_shapes(dtype) + kRingShapes; }
 const char* sweep_shape_name(int dtype, int shape) {
     if (shape < 0 || shape >= sweep_num_shapes(dtype)) return "?";
+    if (shape >= base_shapes(dtype)) return kRingNames[shape - base_shapes(dtype)];
     return dtype == GSIS_F64 ? kShapesF64[shape].name : kShapesF32[shape].name;
 }
 
@@ -119,6 +127,11 @@ static void sweep_f64_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape
 }
 
 static void launch_sweep_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape) {
+    const int nb = base_shapes(c->p.vdf_dtype);
+    if (shape >= nb) {
+        if (launch_sweep_ring(c, a, pass, shape - nb)) return;
+        shape = 0;   // does not fit: register-stencil sweep
+    }
     switch (c->p.vdf_dtype) {
         case GSIS_F64: sweep_f64_shape(c, a, pass, shape); break;
         case GSIS_F32: sweep_f32_shape<float>(c, a, pass, shape); break;
@@ -165,6 +178,27 @@ static std::map<std::string, int>& sweep_cache() {
     return m;
 }
 
+// Fix the sweep tile shape by name (a test hook: every shape must give the
+// same result); GSIS_ERR_ARG if the name is unknown or the shape cannot run
+// this problem.
+gsis_status force_sweep_shape(gsis_ctx* c, const char* name) {
+    const int ns = sweep_num_shapes(c->p.vdf_dtype), nb = base_shapes(c->p.vdf_dtype);
+    for (int sh = 0; sh < ns; ++sh) {
+        if (std::string(sweep_shape_name(c->p.vdf_dtype, sh)) != name) continue;
+        if (sh >= nb) {
+            const int which = sh - nb;
+            if (ring_bytes(c, which == 2 ? 64 : 32) == 0 || (c->p.vdf_dtype == GSIS_F64 && which == 2))
+                return set_err(c, GSIS_ERR_ARG, std::string("sweep tile ") + name + " does not fit this problem");
+        }
+        c->sweep_shape = sh;
+        c->tuned_Nd = c->Nd;
+        c->sweep_forced = true;
+        c->sweep_info = std::string("tile ") + name + " (forced)";
+        return GSIS_OK;
+    }
+    return set_err(c, GSIS_ERR_ARG, std::string("unknown sweep tile ") + (name ? name : "(null)"));
+}
+
 gsis_status tune_sweep(gsis_ctx* c) {
     c->tuned_Nd = c->Nd;
     if (c->Nd == 0 || c->normal_components == 1) {
@@ -197,6 +231,9 @@ gsis_status tune_sweep(gsis_ctx* c) {
     float best_ms = 1e30f;
     std::string info = "tile timings (ms per pass pair):";
     for (int sh = 0; sh < ns; ++sh) {
+        const int nb = base_shapes(c->p.vdf_dtype);
+        if (sh >= nb && ring_bytes(c, sh - nb == 2 ? 64 : 32) == 0) continue;   // window does not fit
+        if (sh >= nb && c->p.vdf_dtype == GSIS_F64 && sh - nb == 2) continue;
         launch_sweep_shape(c, a, 1, sh);
         launch_sweep_shape(c, a, 0, sh);
         cudaEventRecord(e0, c->stream);

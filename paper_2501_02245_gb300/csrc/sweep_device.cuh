@@ -100,43 +100,15 @@ __device__ __forceinline__ void load_meta(const SweepArgs& a, int k, CellMeta<T,
     m.it = __ldg(pick<T>(a.itau, a.itauf) + k);
 }
 
-template <typename S, typename T, int NC, int VPT, int CB>
-__device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
-                                             const Vel<T, VPT>& V) {
-    const long long Nv = a.vg.Nv;
+// The implicit update of CB cells x VPT velocities from their gathered
+// stencils (own value fc, neighbours lo/hi and second neighbours lo2/hi2 per
+// direction; a missing neighbour repeats the nearer value): new values in fo.
+template <typename T, int NC, int VPT, int CB>
+__device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk, const bool* kon,
+                                              const Vel<T, VPT>& V, const CellMeta<T, NC>* m, const T (*fc)[VPT],
+                                              const T (*lo)[NC][VPT], const T (*hi)[NC][VPT],
+                                              const T (*lo2)[NC][VPT], const T (*hi2)[NC][VPT], T (*fo)[VPT]) {
     const int NT = a.vg.NT, nx = a.vg.nx, ny = a.vg.ny;
-    CellMeta<T, NC> m[CB];
-#pragma unroll
-    for (int b = 0; b < CB; ++b)
-        if (kon[b]) load_meta<T, NC>(a, kk[b], m[b]);
-    // ---- gather
-    T fc[CB][VPT];
-    T lo[CB][NC][VPT], hi[CB][NC][VPT], lo2[CB][NC][VPT], hi2[CB][NC][VPT];
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-        if (!kon[b]) continue;
-        const S* fk = f + (long long)kk[b] * Nv;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) fc[b][u] = V.on[u] ? ldT<T, S>(fk + V.v[u]) : T(0);
-#pragma unroll
-        for (int d = 0; d < NC; ++d) {
-            const bool dl = m[b].kd[2 * d] == SK_DVM, dh = m[b].kd[2 * d + 1] == SK_DVM;
-            const bool dl2 = dl && m[b].n2[2 * d] >= 0, dh2 = dh && m[b].n2[2 * d + 1] >= 0;
-            const S* pl = f + (long long)m[b].rf[2 * d] * Nv;
-            const S* ph = f + (long long)m[b].rf[2 * d + 1] * Nv;
-            const S* pl2 = f + (long long)m[b].n2[2 * d] * Nv;
-            const S* ph2 = f + (long long)m[b].n2[2 * d + 1] * Nv;
-#pragma unroll
-            for (int u = 0; u < VPT; ++u) {
-                const bool on = V.on[u];
-                lo[b][d][u] = (dl && on) ? ldT<T, S>(pl + V.v[u]) : fc[b][u];
-                hi[b][d][u] = (dh && on) ? ldT<T, S>(ph + V.v[u]) : fc[b][u];
-                lo2[b][d][u] = (dl2 && on) ? ldT<T, S>(pl2 + V.v[u]) : lo[b][d][u];
-                hi2[b][d][u] = (dh2 && on) ? ldT<T, S>(ph2 + V.v[u]) : hi[b][d][u];
-            }
-        }
-    }
-    // ---- compute and store
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
         if (!kon[b]) continue;
@@ -204,10 +176,55 @@ __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__
                 }
             }
         }
-        S* fk = f + (long long)k * Nv;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) fo[b][u] = div_t<T>(num[u], den[u]);
+    }
+}
+
+template <typename S, typename T, int NC, int VPT, int CB>
+__device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
+                                             const Vel<T, VPT>& V) {
+    const long long Nv = a.vg.Nv;
+    CellMeta<T, NC> m[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+        if (kon[b]) load_meta<T, NC>(a, kk[b], m[b]);
+    // ---- gather
+    T fc[CB][VPT];
+    T lo[CB][NC][VPT], hi[CB][NC][VPT], lo2[CB][NC][VPT], hi2[CB][NC][VPT];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+        if (!kon[b]) continue;
+        const S* fk = f + (long long)kk[b] * Nv;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) fc[b][u] = V.on[u] ? ldT<T, S>(fk + V.v[u]) : T(0);
+#pragma unroll
+        for (int d = 0; d < NC; ++d) {
+            const bool dl = m[b].kd[2 * d] == SK_DVM, dh = m[b].kd[2 * d + 1] == SK_DVM;
+            const bool dl2 = dl && m[b].n2[2 * d] >= 0, dh2 = dh && m[b].n2[2 * d + 1] >= 0;
+            const S* pl = f + (long long)m[b].rf[2 * d] * Nv;
+            const S* ph = f + (long long)m[b].rf[2 * d + 1] * Nv;
+            const S* pl2 = f + (long long)m[b].n2[2 * d] * Nv;
+            const S* ph2 = f + (long long)m[b].n2[2 * d + 1] * Nv;
+#pragma unroll
+            for (int u = 0; u < VPT; ++u) {
+                const bool on = V.on[u];
+                lo[b][d][u] = (dl && on) ? ldT<T, S>(pl + V.v[u]) : fc[b][u];
+                hi[b][d][u] = (dh && on) ? ldT<T, S>(ph + V.v[u]) : fc[b][u];
+                lo2[b][d][u] = (dl2 && on) ? ldT<T, S>(pl2 + V.v[u]) : lo[b][d][u];
+                hi2[b][d][u] = (dh2 && on) ? ldT<T, S>(ph2 + V.v[u]) : hi[b][d][u];
+            }
+        }
+    }
+    T fo[CB][VPT];
+    compute_cells<T, NC, VPT, CB>(a, kk, kon, V, m, fc, lo, hi, lo2, hi2, fo);
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+        if (!kon[b]) continue;
+        S* fk = f + (long long)kk[b] * Nv;
 #pragma unroll
         for (int u = 0; u < VPT; ++u)
-            if (V.on[u]) stT<T, S>(fk + V.v[u], div_t<T>(num[u], den[u]));
+            if (V.on[u]) stT<T, S>(fk + V.v[u], fo[b][u]);
     }
 }
 

@@ -24,7 +24,8 @@ PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual"
 
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
-            "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info"]
+            "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
+            "gsis_debug_set_sweep_tile"]
 
 
 class GsisError(RuntimeError):
@@ -98,6 +99,8 @@ def load():
     lib.gsis_iterate_batch.argtypes = [ctypes.POINTER(vp), c_int, c_int, ctypes.POINTER(Report)]
     lib.gsis_batch_info.argtypes = [ctypes.POINTER(vp), c_int]
     lib.gsis_batch_info.restype = ctypes.c_char_p
+    lib.gsis_debug_set_sweep_tile.argtypes = [vp, ctypes.c_char_p]
+    lib.gsis_debug_set_sweep_tile.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
     lib.gsis_tuning_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
@@ -249,6 +252,10 @@ class Solver:
     def W(self):
         m = self.moments()
         return np.stack([m["rho"], m["ux"], m["uy"], m["uz"], m["T"]], axis=1)
+
+    def set_sweep_tile(self, name):
+        """Force the kinetic sweep's tile shape (test hook)."""
+        self._check(self.lib.gsis_debug_set_sweep_tile(self.ctx, name.encode()))
 
     def tuning_info(self):
         """Result of the sweep tile-shape autotuning of this solve."""
