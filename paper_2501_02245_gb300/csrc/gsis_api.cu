@@ -156,6 +156,7 @@ gsis_status start(gsis_ctx* c) {
                                     cudaMemcpyHostToDevice, c->stream), "upload W0"))
         return GSIS_ERR_CUDA;
     cudaMemsetAsync(c->hot, 0, (size_t)N * HOTN * sizeof(double), c->stream);
+    launch_face_geometry(c);
     if (c->p.vdf_dtype != GSIS_F64) {   // FP32 copies of the boundary and ghost records for the FP32 sweep
         const size_t NT = c->vg.NT;
         c->recBC.tabf = (float*)dev_alloc(c, 6 * NTAB * NT * sizeof(float));
@@ -764,6 +765,9 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->lamS = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
     c->Ff = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
     c->lamf = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
+    c->fgeo = (double*)dev_alloc(c, (size_t)N * 3 * 8 * sizeof(double));
+    c->bgeo = (double*)dev_alloc(c, (size_t)N * 6 * 8 * sizeof(double));
+    c->acell = (double*)dev_alloc(c, (size_t)N * sizeof(double));
     c->gu = (double*)dev_alloc(c, (size_t)N * 9 * sizeof(double));
     c->gT = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
     c->grho = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
@@ -793,7 +797,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
     if (!c->d_job || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W ||
-        !c->Wh ||
+        !c->Wh || !c->fgeo || !c->bgeo || !c->acell ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
         !c->lamf || !c->gu || !c->gT ||
         !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->wall_in ||

@@ -77,6 +77,8 @@ struct MacroArgs {
     const double* vol;
     const double* lsq_w;
     const double* bc_state;   // [6][5]
+    const double* fgeo;       // [N][3][8] high face of each direction: |S|, n (3), e (3), distance of centres
+    const double* bgeo;       // [N][6][8] each side: |S|, n (3), unit cell-to-face vector (3), its length
     double mu0, omega;
 };
 
@@ -87,10 +89,10 @@ struct MacroJob {
     double cfl, dt;
     double *Wm, *U;
     const double *Un, *hot, *wall_corr;
-    double *gu, *gT, *Ff, *lamf, *R, *D, *lamS, *dU, *dU2;
+    double *gu, *gT, *Ff, *lamf, *R, *D, *lamS, *dU, *dU2, *acell;
 };
 
-constexpr int MACRO_FUSED_THREADS = 256;
+constexpr int MACRO_FUSED_THREADS = 512;
 constexpr int MACRO_FUSED_MAX_CELLS = 4096;
 }  // namespace gsis
 
@@ -125,6 +127,8 @@ struct gsis_ctx {
     double *W = nullptr, *Wh = nullptr, *Wp = nullptr, *Wm = nullptr, *U = nullptr, *Un = nullptr;
     double *dU = nullptr, *dU2 = nullptr, *R = nullptr, *D = nullptr, *lamS = nullptr;
     double *Ff = nullptr, *lamf = nullptr;   // interior face fluxes [N][3][5] and lambda|S| [N][3] (high faces)
+    double *fgeo = nullptr, *bgeo = nullptr; // face geometry (see MacroArgs)
+    double* acell = nullptr;                 // [N] sound speed of the current pseudo-time state
     double *gu = nullptr, *gT = nullptr, *grho = nullptr, *gU = nullptr;
     double *hot = nullptr, *kin = nullptr, *nsf = nullptr, *kn_gll = nullptr;
     double *eps_buf = nullptr, *h_eps = nullptr;
@@ -209,6 +213,7 @@ void launch_nsf(gsis_ctx* c, const double* Wprim, double* out);
 void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons);
 void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim);
 void launch_blend(gsis_ctx* c, const double* Wh, double w, double* W);
+void launch_face_geometry(gsis_ctx* c);
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term);
 MacroJob macro_job(gsis_ctx* c, int steps, bool time_term);
 void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream);

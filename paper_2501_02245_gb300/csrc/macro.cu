@@ -38,6 +38,8 @@ static MacroArgs margs(gsis_ctx* c) {
     a.vol = c->m.vol;
     a.lsq_w = c->m.lsq_w;
     a.bc_state = c->d_bc_state;
+    a.fgeo = c->fgeo;
+    a.bgeo = c->bgeo;
     a.mu0 = c->mu0;
     a.omega = c->p.omega;
     return a;
@@ -48,8 +50,9 @@ static MacroArgs margs(gsis_ctx* c) {
 // boundary value: far field -> boundary state; wall -> u = 0, |u| = 0, T = T_w,
 // rho = cell value).  gu[c][j][i] = d u_j / d x_i.
 __device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double* Wp, int with_rho_U, double* gu,
-                                               double* gT, double* grho, double* gU, int c) {
+                                               double* gT, double* grho, double* gU, double* acell, int c) {
     const double* wc = Wp + c * 5;
+    if (acell) acell[c] = sqrt(GAMMA * wc[4]);
     const double Uc = sqrt(wc[1] * wc[1] + wc[2] * wc[2] + wc[3] * wc[3]);
     double g[6][3];
     for (int q = 0; q < 6; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
@@ -93,15 +96,16 @@ __device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double*
 }
 
 __global__ void k_gradients(MacroArgs a, const double* __restrict__ Wp, int with_rho_U, double* __restrict__ gu,
-                            double* __restrict__ gT, double* __restrict__ grho, double* __restrict__ gU) {
+                            double* __restrict__ gT, double* __restrict__ grho, double* __restrict__ gU,
+                            double* __restrict__ acell) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < a.N) gradients_cell(a, Wp, with_rho_U, gu, gT, grho, gU, c);
+    if (c < a.N) gradients_cell(a, Wp, with_rho_U, gu, gT, grho, gU, acell, c);
 }
 
 void launch_gradients(gsis_ctx* c, const double* Wprim, bool with_rho_U) {
     const int N = c->m.N;
     k_gradients<<<(N + 63) / 64, 64, 0, c->stream>>>(margs(c), Wprim, with_rho_U ? 1 : 0, c->gu, c->gT, c->grho,
-                                                     c->gU);
+                                                     c->gU, c->acell);
     c->launches++;
 }
 
@@ -164,6 +168,48 @@ __global__ void k_cons_to_prim(int N, const double* __restrict__ U, double* __re
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     cons_to_prim(U + c * 5, Wp + c * 5);
+}
+
+// Face geometry of the synthetic solve, computed once per mesh: for the high
+// face of each direction |S|, n = S/|S|, the unit vector e between the cell
+// centres and their distance; for every side |S|, n and the unit vector from
+// the cell centre to the face centre and its length.
+__global__ void k_face_geometry(MacroArgs a, double* __restrict__ fgeo, double* __restrict__ bgeo) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    for (int s = 0; s < 6; ++s) {
+        const double* So = a.Sout + ((long long)c * 6 + s) * 3;
+        const double Sabs = sqrt(So[0] * So[0] + So[1] * So[1] + So[2] * So[2]);
+        double eb[3];
+        for (int i = 0; i < 3; ++i) eb[i] = a.xf[((long long)c * 6 + s) * 3 + i] - a.cen[c * 3 + i];
+        const double bd = sqrt(eb[0] * eb[0] + eb[1] * eb[1] + eb[2] * eb[2]);
+        double* B = bgeo + ((long long)c * 6 + s) * 8;
+        B[0] = Sabs;
+        for (int i = 0; i < 3; ++i) B[1 + i] = Sabs > 0.0 ? So[i] / Sabs : 0.0;
+        for (int i = 0; i < 3; ++i) B[4 + i] = bd > 0.0 ? eb[i] / bd : 0.0;
+        B[7] = bd;
+        if (s & 1) {
+            const int d = s >> 1;
+            const int R = a.nbr[c * 6 + s];
+            double* G = fgeo + ((long long)c * 3 + d) * 8;
+            for (int q = 0; q < 8; ++q) G[q] = 0.0;
+            if (R >= 0) {
+                double e[3];
+                for (int i = 0; i < 3; ++i) e[i] = a.cen[R * 3 + i] - a.cen[c * 3 + i];
+                const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+                G[0] = Sabs;
+                for (int i = 0; i < 3; ++i) G[1 + i] = So[i] / Sabs;
+                for (int i = 0; i < 3; ++i) G[4 + i] = e[i] / dist;
+                G[7] = dist;
+            }
+        }
+    }
+}
+
+void launch_face_geometry(gsis_ctx* c) {
+    const int N = c->m.N;
+    k_face_geometry<<<(N + 127) / 128, 128, 0, c->stream>>>(margs(c), c->fgeo, c->bgeo);
+    c->launches++;
 }
 
 // W <- Wh + w (W - Wh): under-relaxed synthetic correction of the primitives.
@@ -244,8 +290,8 @@ __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u
 // viscous + HoT) F.S to Ff[c][d][5] and lambda |S| to lamf[c][d]; faces that
 // do not exist (boundary) get lamf = -1.
 __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* Wm, const double* gu,
-                                              const double* gT, const double* hot, int ndir, double* Ff,
-                                              double* lamf, int t) {
+                                              const double* gT, const double* hot, const double* acell, int ndir,
+                                              double* Ff, double* lamf, int t) {
     const int L = t / ndir, d = t % ndir;
     const int Rr = a.nbr[L * 6 + 2 * d + 1];
     double* F = Ff + ((long long)L * 3 + d) * 5;
@@ -254,8 +300,9 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
         return;
     }
     const double* S = a.Sout + ((long long)L * 6 + 2 * d + 1) * 3;
-    const double Sabs = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-    const double nn[3] = {S[0] / Sabs, S[1] / Sabs, S[2] / Sabs};
+    const double* G = a.fgeo + ((long long)L * 3 + d) * 8;
+    const double Sabs = G[0];
+    const double nn[3] = {G[1], G[2], G[3]};
     double qL[5], qR[5], slL[5] = {0, 0, 0, 0, 0}, slR[5] = {0, 0, 0, 0, 0};
     prim5(Wm + L * 5, qL);
     prim5(Wm + Rr * 5, qR);
@@ -289,10 +336,8 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     const double uf[3] = {0.5 * (wL[1] + wR[1]), 0.5 * (wL[2] + wR[2]), 0.5 * (wL[3] + wR[3])};
     const double Tf = 0.5 * (wL[4] + wR[4]);
     const double muf = viscosity(Tf, a.mu0, a.omega);
-    double e[3];
-    for (int i = 0; i < 3; ++i) e[i] = a.cen[Rr * 3 + i] - a.cen[L * 3 + i];
-    const double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-    for (int i = 0; i < 3; ++i) e[i] /= dist;
+    const double e[3] = {G[4], G[5], G[6]};
+    const double dist = G[7];
     double guf[9], gTf[3];
     for (int j = 0; j < 3; ++j) {
         double gav[3];
@@ -320,17 +365,18 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     F[2] = Fv[2] + SigS[1];
     F[3] = Fv[3] + SigS[2];
     F[4] = Fv[4] + ((SigS[0] * uf[0] + SigS[1] * uf[1] + SigS[2] * uf[2]) + (Q[0] * S[0] + Q[1] * S[1] + Q[2] * S[2]));
-    const double aL = sqrt(GAMMA * wL[4]), aR = sqrt(GAMMA * wR[4]);
+    const double aL = acell[L], aR = acell[Rr];
     const double lam = fabs(uf[0] * nn[0] + uf[1] * nn[1] + uf[2] * nn[2]) + 0.5 * (aL + aR) +
                        5.0 * muf / (0.5 * (wL[0] + wR[0]) * dist);
     lamf[(long long)L * 3 + d] = lam * Sabs;
 }
 
 __global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ gu,
-                            const double* __restrict__ gT, const double* __restrict__ hot, int ndir,
-                            double* __restrict__ Ff, double* __restrict__ lamf) {
+                            const double* __restrict__ gT, const double* __restrict__ hot,
+                            const double* __restrict__ acell, int ndir, double* __restrict__ Ff,
+                            double* __restrict__ lamf) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < a.N * ndir) face_flux_one(a, Wm, gu, gT, hot, ndir, Ff, lamf, t);
+    if (t < a.N * ndir) face_flux_one(a, Wm, gu, gT, hot, acell, ndir, Ff, lamf, t);
 }
 
 // NSF flux through wall side s of cell c at state w (prim) with cell gradients
@@ -340,10 +386,9 @@ __device__ void wall_nsf_flux(const MacroArgs& a, const double* w, const double*
                               double* Fb) {
     const double* So = a.Sout + ((long long)c * 6 + s) * 3;
     const double Tw = a.bc_state[s * 5 + 4];
-    double eb[3];
-    for (int i = 0; i < 3; ++i) eb[i] = a.xf[((long long)c * 6 + s) * 3 + i] - a.cen[c * 3 + i];
-    const double bdist = sqrt(eb[0] * eb[0] + eb[1] * eb[1] + eb[2] * eb[2]);
-    for (int i = 0; i < 3; ++i) eb[i] /= bdist;
+    const double* G = a.bgeo + ((long long)c * 6 + s) * 8;
+    const double eb[3] = {G[4], G[5], G[6]};
+    const double bdist = G[7];
     double guw[9], gTw[3];
     for (int j = 0; j < 3; ++j) {
         const double* gc = gu + j * 3;
@@ -424,13 +469,12 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
             lam_sum += ls;
         } else if (bc == GSIS_BC_FARFIELD || bc == GSIS_BC_WALL) {
             const double* st = a.bc_state + s * 5;
-            const double Sabs = sqrt(So[0] * So[0] + So[1] * So[1] + So[2] * So[2]);
-            const double nn[3] = {So[0] / Sabs, So[1] / Sabs, So[2] / Sabs};
+            const double* G = a.bgeo + ((long long)c * 6 + s) * 8;
+            const double Sabs = G[0];
+            const double nn[3] = {G[1], G[2], G[3]};
             const double* h = hot + (long long)c * HOTN;
             double Fb[5];
-            double eb[3];
-            for (int i = 0; i < 3; ++i) eb[i] = a.xf[((long long)c * 6 + s) * 3 + i] - a.cen[c * 3 + i];
-            const double bdist = sqrt(eb[0] * eb[0] + eb[1] * eb[1] + eb[2] * eb[2]);
+            const double bdist = G[7];
             if (bc == GSIS_BC_FARFIELD) {
                 kfvs(rho_c, u_c, p_c, st[0], st + 1, st[0] * st[4], nn, Fb);
                 for (int q = 0; q < 5; ++q) Fb[q] *= Sabs;
@@ -522,16 +566,16 @@ __global__ void k_update(int N, double* __restrict__ U, const double* __restrict
 // thousand cells: the 1D shocks, solve batches).  The same per-cell and
 // per-face functions as the multi-block kernels, separated by block barriers,
 // so the result is identical.  One CTA per job of the job array.
-__global__ void __launch_bounds__(MACRO_FUSED_THREADS) k_macro_fused(const MacroJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(MACRO_FUSED_THREADS, 1) k_macro_fused(const MacroJob* __restrict__ jobs) {
     const MacroJob& J = jobs[blockIdx.x];
     const MacroArgs a = J.a;
     const int N = a.N;
     for (int it = 0; it < J.steps; ++it) {
         for (int c = threadIdx.x; c < N; c += blockDim.x)
-            gradients_cell(a, J.Wm, 0, J.gu, J.gT, nullptr, nullptr, c);
+            gradients_cell(a, J.Wm, 0, J.gu, J.gT, nullptr, nullptr, J.acell, c);
         __syncthreads();
         for (int t = threadIdx.x; t < N * J.ndir; t += blockDim.x)
-            face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.ndir, J.Ff, J.lamf, t);
+            face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.acell, J.ndir, J.Ff, J.lamf, t);
         __syncthreads();
         for (int c = threadIdx.x; c < N; c += blockDim.x)
             cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.wall_corr, J.cfl, J.dt, J.R,
@@ -560,6 +604,7 @@ MacroJob macro_job(gsis_ctx* c, int steps, bool time_term) {
     J.Wm = c->Wm; J.U = c->U; J.Un = c->Un; J.gu = c->gu; J.gT = c->gT; J.hot = c->hot; J.Ff = c->Ff;
     J.lamf = c->lamf; J.wall_corr = c->wall_corr; J.R = c->R; J.D = c->D; J.lamS = c->lamS; J.dU = c->dU;
     J.dU2 = c->dU2;
+    J.acell = c->acell;
     return J;
 }
 
@@ -590,7 +635,7 @@ void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term) {
     const double dt = time_term ? c->p.dt : 0.0;
     for (int it = 0; it < steps; ++it) {
         launch_gradients(c, c->Wm, false);
-        k_face_flux<<<nf, TB, 0, c->stream>>>(a, c->Wm, c->gu, c->gT, c->hot, ndir, c->Ff, c->lamf);
+        k_face_flux<<<nf, TB, 0, c->stream>>>(a, c->Wm, c->gu, c->gT, c->hot, c->acell, ndir, c->Ff, c->lamf);
         k_cell_residual<<<nb, TB, 0, c->stream>>>(a, c->Wm, c->U, c->Un, c->gu, c->gT, c->hot, c->Ff, c->lamf,
                                                   c->wall_corr, c->p.cfl, dt, c->R, c->D, c->lamS, c->dU);
         c->launches += 2;
