@@ -39,6 +39,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk (4 flop) x 2
 # distribution and 1/tau 14, face normal speeds 4 x 5, two outgoing faces 2 x 4,
 # two own limited slopes 2 x 4, two incoming MUSCL face values 2 x 8, division 1.
 SWEEP_FLOPS_PER_POINT_2D = 67
+# the same count on a 1D mesh (2 active faces): reference distribution and 1/tau 14, two
+# normal speeds 2 x 3, one outgoing face 4, one own slope 4, one incoming MUSCL value 8, division 1.
+SWEEP_FLOPS_PER_POINT_1D = 37
 
 
 def parse():
@@ -50,6 +53,8 @@ def parse():
     ap.add_argument("--config", default="cylinder",
                     choices=["cylinder", "shock", "cylinder_full", "sphere", "cylinder32", "batch"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "f16"])
+    ap.add_argument("--tile", default=None,
+                    help="run the sweep with this tile shape instead of the autotuned one (for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -228,6 +233,8 @@ def run_gsis(args):
     stream = torch.cuda.current_stream()
     s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
     rep0 = s.iterate(0)
+    if args.tile:
+        s.set_sweep_tile(args.tile)
     for _ in range(args.warmup):
         s.iterate(1)
     clocks = Clocks(local)
@@ -260,13 +267,14 @@ def run_gsis(args):
     eb = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[args.dtype]
     traffic = traffic_from_profile(args.config, args.dtype)
     if args.dtype == "f64":
-        flops = SWEEP_FLOPS_PER_POINT_2D * pts_per_launch
+        fpp = SWEEP_FLOPS_PER_POINT_1D if args.config == "shock" else SWEEP_FLOPS_PER_POINT_2D
+        flops = fpp * pts_per_launch
         achieved = flops / (sweep_ms_per_launch * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "k_sweep<double> (one Gauss-Seidel pass)",
                 "peak_source": "FP64 unit counts x clock: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
-                "algorithmic": "%d FP64 flop per (cell, velocity) per pass" % SWEEP_FLOPS_PER_POINT_2D}
+                "algorithmic": "%d FP64 flop per (cell, velocity) per pass" % fpp}
     else:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peaks = json.load(fh)

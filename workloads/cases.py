@@ -62,14 +62,16 @@ def rankine_hugoniot(Ma, gamma=GAMMA):
 
 
 def shock_1d_case(Ma=2.0, n_cells=200, half_width=25.0, nv=(48, 24, 24), vmax=6.0 * np.sqrt(2.0),
-                  delta=2.0, iterations=60, macro_steps=200, cfl=100.0, k_sub=8, dt=1.0):
+                  delta=2.0, iterations=60, macro_steps=50, cfl=100.0, k_sub=4, dt=1.0):
     """Normal shock structure: upstream mean free path = length unit (Kn = 1).
 
     Initial state: tanh blend of the Rankine-Hugoniot end states with width
     delta; both ends are far-field boundaries with those end states.  The
     synthetic solve keeps a finite time step dt: a standing shock between two
     fixed end states can translate freely, and the time term holds the mass in
-    the domain fixed up to the boundary fluxes.
+    the domain fixed up to the boundary fluxes.  50 pseudo-steps with 4
+    relaxation sweeps per GSIS iteration: the residual history is the same as
+    with 200 steps and 8 sweeps.
     """
     r2, u2, T2 = rankine_hugoniot(Ma)
     u1 = Ma * np.sqrt(GAMMA)
@@ -146,7 +148,7 @@ def batch_vgrid_half_width(Ma):
 
 
 def shock_batch_cases(n=64, seed=2501, ma_range=(1.5, 8.0), cells_range=(100, 800), iterations=60,
-                      macro_steps=200):
+                      macro_steps=50):
     """Seeded batch of independent 1D shocks with uneven meshes and velocity grids."""
     rng = np.random.default_rng(seed)
     cases = []
