@@ -67,7 +67,8 @@ enum {
     GSIS_FIELD_HOT_SXY = 1 << 8, GSIS_FIELD_HOT_SXZ = 1 << 9, GSIS_FIELD_HOT_SYZ = 1 << 10,
     GSIS_FIELD_HOT_QX = 1 << 11, GSIS_FIELD_HOT_QY = 1 << 12, GSIS_FIELD_HOT_QZ = 1 << 13,
     GSIS_FIELD_KN_GLL = 1 << 14, GSIS_FIELD_DVM = 1 << 15,
-    GSIS_NFIELDS = 16
+    GSIS_FIELD_WALL_Q = 1 << 16,   /* heat flux into the wall, per unit area (0 off the wall) */
+    GSIS_NFIELDS = 17
 };
 
 /* Device-memory callbacks (for example a framework's caching allocator).
@@ -178,7 +179,12 @@ gsis_status gsis_iterate(gsis_ctx* ctx, int max_iter, gsis_report* report);
 /* Write the selected per-cell fields (GSIS_FIELD_* bits, in bit order) of the
  * current state: [ncell][popcount(mask)] doubles to dst (host memory when
  * dst_is_device = 0, device memory on the context's device otherwise).  HoT
- * fields are those of the last kinetic step (zero in NS cells). */
+ * fields are those of the last kinetic step (zero in NS cells).
+ * GSIS_FIELD_WALL_Q, for a cell with diffuse-wall sides: the energy flux
+ * through those sides into the wall divided by their area -- for a DVM cell
+ * carried by its current distribution (outgoing half of f, the re-emitted
+ * half rho_w M(0, T_w) with zero net mass flux), for an NS cell the Fourier
+ * heat flux of the NSF wall flux at the current state; 0 for other cells. */
 gsis_status gsis_moments(gsis_ctx* ctx, unsigned field_mask, double* dst, int dst_is_device);
 
 /* Copy the compacted VDF of the DVM cells to host memory as FP64:

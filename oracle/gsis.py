@@ -218,6 +218,31 @@ class OracleSolver:
                 corr[r] = F_kin - F_nsf[r]
         return corr
 
+    def wall_heat_flux(self):
+        """Heat flux into the wall per unit area, per cell (0 without wall
+        sides): the energy flux through the cell's diffuse-wall sides divided
+        by their area, carried by the current distribution for a DVM cell
+        (outgoing half of f, re-emitted rho_w M(0, T_w) with zero net mass
+        flux) and by the NSF wall flux at the current state for an NS cell."""
+        geo = self.geo
+        idx = np.nonzero(geo.bT == BC_WALL)[0]
+        out_num = np.zeros(self.N); out_area = np.zeros(self.N)
+        if len(idx) == 0:
+            return out_num
+        gu, gT = self.gradients(self.W)
+        F_nsf = wall_nsf_flux(geo, self.bc_state, self.W[:, 0], self.W[:, 1:4], self.W[:, 4], gu, gT,
+                              self.mu0, self.omega)
+        for r, f_i in enumerate(idx):
+            c = geo.bC[f_i]
+            if self.dvm[c]:
+                Mw = M.maxwellian(1.0, np.zeros(3), self.bc_state[geo.bSide[f_i], 4], self.vg.xi)
+                e = wall_kinetic_flux(self.f[c], geo.bS[f_i], Mw, self.vg)[4]
+            else:
+                e = F_nsf[r, 4]
+            out_num[c] += e
+            out_area[c] += geo.bSabs[f_i]
+        return np.where(out_area > 0, out_num / np.where(out_area > 0, out_area, 1.0), 0.0)
+
     def step(self):
         """One GSIS iteration; returns epsilon."""
         case = self.case

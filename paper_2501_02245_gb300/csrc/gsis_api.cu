@@ -768,6 +768,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->fgeo = (double*)dev_alloc(c, (size_t)N * 3 * 8 * sizeof(double));
     c->bgeo = (double*)dev_alloc(c, (size_t)N * 6 * 8 * sizeof(double));
     c->acell = (double*)dev_alloc(c, (size_t)N * sizeof(double));
+    c->wallq = (double*)dev_alloc(c, (size_t)N * sizeof(double));
     c->gu = (double*)dev_alloc(c, (size_t)N * 9 * sizeof(double));
     c->gT = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
     c->grho = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
@@ -797,7 +798,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
     if (!c->d_job || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W ||
-        !c->Wh || !c->fgeo || !c->bgeo || !c->acell ||
+        !c->Wh || !c->fgeo || !c->bgeo || !c->acell || !c->wallq ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
         !c->lamf || !c->gu || !c->gT ||
         !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->wall_in ||
@@ -920,8 +921,12 @@ gsis_status gsis_moments(gsis_ctx* c, unsigned mask, double* dst, int dst_is_dev
     if (!c->mesh_set) return set_err(c, GSIS_ERR_STATE, "no mesh");
     if (mask == 0 || mask >= (1u << GSIS_NFIELDS)) return set_err(c, GSIS_ERR_ARG, "bad field mask");
     const int N = c->m.N;
-    std::vector<double> W((size_t)N * 5), hot((size_t)N * HOTN), kn(N, 0.0);
+    std::vector<double> W((size_t)N * 5), hot((size_t)N * HOTN), kn(N, 0.0), wq(N, 0.0);
     std::vector<int> c2d(N, -1);
+    if (c->started && (mask & GSIS_FIELD_WALL_Q) && c->has_wall) {
+        launch_wall_heat(c, c->wallq);
+        cudaMemcpyAsync(wq.data(), c->wallq, wq.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+    }
     if (c->started) {
         cudaMemcpyAsync(W.data(), c->W, W.size() * 8, cudaMemcpyDeviceToHost, c->stream);
         cudaMemcpyAsync(hot.data(), c->hot, hot.size() * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -946,7 +951,8 @@ gsis_status gsis_moments(gsis_ctx* c, unsigned mask, double* dst, int dst_is_dev
             if (b < 5) v = W[(size_t)cc * 5 + b];
             else if (b < 14) v = hot[(size_t)cc * HOTN + (b - 5)];
             else if (b == 14) v = kn[cc];
-            else v = c2d[cc] >= 0 ? 1.0 : 0.0;
+            else if (b == 15) v = c2d[cc] >= 0 ? 1.0 : 0.0;
+            else v = wq[cc];
             out[(size_t)cc * nsel + o++] = v;
         }
     }

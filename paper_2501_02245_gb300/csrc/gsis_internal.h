@@ -129,6 +129,7 @@ struct gsis_ctx {
     double *Ff = nullptr, *lamf = nullptr;   // interior face fluxes [N][3][5] and lambda|S| [N][3] (high faces)
     double *fgeo = nullptr, *bgeo = nullptr; // face geometry (see MacroArgs)
     double* acell = nullptr;                 // [N] sound speed of the current pseudo-time state
+    double* wallq = nullptr;                 // [N] wall heat flux output (gsis_moments)
     double *gu = nullptr, *gT = nullptr, *grho = nullptr, *gU = nullptr;
     double *hot = nullptr, *kin = nullptr, *nsf = nullptr, *kn_gll = nullptr;
     double *eps_buf = nullptr, *h_eps = nullptr;
@@ -214,6 +215,7 @@ void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons);
 void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim);
 void launch_blend(gsis_ctx* c, const double* Wh, double w, double* W);
 void launch_face_geometry(gsis_ctx* c);
+void launch_wall_heat(gsis_ctx* c, double* out);
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term);
 MacroJob macro_job(gsis_ctx* c, int steps, bool time_term);
 void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream);

@@ -440,6 +440,38 @@ void launch_wall_corr(gsis_ctx* c) {
     c->launches++;
 }
 
+// Heat flux into the wall per unit area for every cell with wall sides: the
+// energy component of the kinetic wall flux (DVM cells, wall_kin of the
+// current f) or of the NSF wall flux at the current state (NS cells), summed
+// over the wall sides and divided by their area.
+__global__ void k_wall_heat(MacroArgs a, const int* __restrict__ cell2dvm, const double* __restrict__ W,
+                            const double* __restrict__ gu, const double* __restrict__ gT,
+                            const double* __restrict__ wall_kin, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    double num = 0.0, area = 0.0;
+    for (int s = 0; s < 6; ++s) {
+        if (a.nbr[c * 6 + s] >= 0 || a.side_bc[c * 6 + s] != GSIS_BC_WALL) continue;
+        if (cell2dvm[c] >= 0) {
+            num += wall_kin[((long long)c * 6 + s) * 5 + 4];
+        } else {
+            double F[5];
+            wall_nsf_flux(a, W + c * 5, gu + (long long)c * 9, gT + (long long)c * 3, c, s, F);
+            num += F[4];
+        }
+        area += a.bgeo[((long long)c * 6 + s) * 8];
+    }
+    out[c] = area > 0.0 ? num / area : 0.0;
+}
+
+void launch_wall_heat(gsis_ctx* c, double* out) {
+    const int N = c->m.N;
+    launch_wall_flux(c);                  // kinetic wall fluxes of the current f
+    launch_gradients(c, c->W, false);     // gradients of the current state for the NSF wall flux
+    k_wall_heat<<<(N + 127) / 128, 128, 0, c->stream>>>(margs(c), c->cell2dvm, c->W, c->gu, c->gT, c->wall_kin, out);
+    c->launches++;
+}
+
 // Cell residual R_c = -sum_F F.S_out (gathering the interior face fluxes in
 // side order, boundary faces evaluated here), lambda|S| per side, the
 // diagonal D and dU0 = R/D.

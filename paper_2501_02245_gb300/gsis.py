@@ -19,7 +19,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_STATE", "ERR_OOM", "ERR_CUDA", "ERR_NONFIN
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 DTYPE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 FIELDS = ["rho", "ux", "uy", "uz", "T", "hot_sxx", "hot_syy", "hot_szz", "hot_sxy", "hot_sxz", "hot_syz",
-          "hot_qx", "hot_qy", "hot_qz", "kn_gll", "dvm"]
+          "hot_qx", "hot_qy", "hot_qz", "kn_gll", "dvm", "wall_q"]
 PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual", "presolve"]
 
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",

@@ -27,6 +27,11 @@ def _compare(case, n_iter, flags=None, f_tol=1e-10, hot_tol=1e-9):
     nd = int(o.dvm.sum())
     fg = vdf_by_cell(s, nd, o.N, o.vg.nv)
     assert rel_err(fg[o.dvm], o.f[o.dvm]) < f_tol
+    # heat flux into the wall (cells with wall sides), relative to its largest magnitude
+    qo = o.wall_heat_flux()
+    if np.any(qo != 0.0):
+        qg = s.moments(["wall_q"])["wall_q"]
+        assert rel_err(qg, qo) < 1e-9, "wall heat flux relative error %.3e" % rel_err(qg, qo)
     s.close()
     return o
 
