@@ -57,6 +57,7 @@ def parse():
                     help="run the sweep with this tile shape instead of the autotuned one (for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-converge", action="store_true", help="skip the time-to-converged measurement")
     return ap.parse_args()
 
 
@@ -297,6 +298,8 @@ def run_gsis(args):
     s.close()
     if not args.no_e2e:
         line["e2e"] = e2e(args, case, stream)
+    if not args.no_converge and args.config in ("cylinder", "cylinder_full", "shock"):
+        line["time_to_converged"] = time_to_converged(args, case, stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, nd, nv, nc = cpu_baseline(args.config)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -396,6 +399,39 @@ def run_batch(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def time_to_converged(args, case, stream, thresholds=(1e-3, 2e-4), cap=80):
+    """Wall-clock time (device synchronised) from a fresh context (host data,
+    presolve, region) until the residual of Sec. 4 first falls below each
+    threshold, at most `cap` GSIS iterations.  The 1e-6 criterion of the paper
+    is not reached by these runs (see the convergence status in the design
+    notes), so the precision forms are compared at these thresholds."""
+    import torch
+    from paper_2501_02245_gb300 import Solver
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
+    s.iterate(0)
+    torch.cuda.synchronize()
+    out = {"criterion": "epsilon of Sec. 4 between consecutive iterations", "cap": cap,
+           "start_s": time.perf_counter() - t0, "reached": {}}
+    eps_min = 1e300
+    it = 0
+    for it in range(cap):
+        r = s.iterate(1)
+        eps_min = min(eps_min, r["eps"])
+        for th in thresholds:
+            key = "%.0e" % th
+            if key not in out["reached"] and r["eps"] < th:
+                torch.cuda.synchronize()
+                out["reached"][key] = {"iterations": it + 1, "seconds": time.perf_counter() - t0}
+        if len(out["reached"]) == len(thresholds):
+            break
+    out["eps_min"] = eps_min
+    out["iterations_run"] = it + 1
+    s.close()
+    return out
 
 
 def e2e(args, case, stream):
