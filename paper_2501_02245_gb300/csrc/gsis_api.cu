@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -253,7 +254,11 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     phase_begin(c, GSIS_PH_CELLEQ);
     stage_cell_eq(c);
     phase_end(c, GSIS_PH_CELLEQ);
-    if (!c->sweep_forced && (c->sweep_shape < 0 || c->tuned_Nd != c->Nd)) {   // (re)tune for this region
+    // (re)tune the sweep tile for a new region; a re-identification that changes the DVM cell
+    // count by less than a quarter keeps the shape (the timings hardly move)
+    const bool retune = c->sweep_shape < 0 || c->tuned_Nd <= 0 ||
+                        std::llabs(c->Nd - c->tuned_Nd) * 4 > c->tuned_Nd;
+    if (!c->sweep_forced && retune) {
         gsis_status st = tune_sweep(c);
         if (st != GSIS_OK) return st;
     }
