@@ -222,6 +222,8 @@ static bool ensure_dvm_capacity(gsis_ctx* c, long long Nd) {
     dev_free(c, c->recG.scal); dev_free(c, c->recG.tab); dev_free(c, c->recHalf.scal); dev_free(c, c->recHalf.tab);
     dev_free(c, c->recNew.scal); dev_free(c, c->recNew.tab); dev_free(c, c->enter_of);
     dev_free(c, c->SoVf); dev_free(c, c->itauf); dev_free(c, c->rho_wf);
+    dev_free(c, c->yzd); dev_free(c, c->yzf);
+    c->yzd = nullptr; c->yzf = nullptr;
     dev_free(c, c->recG.tabf); dev_free(c, c->recG.scalf); dev_free(c, c->recHalf.tabf);
     dev_free(c, c->recHalf.scalf); dev_free(c, c->recNew.tabf); dev_free(c, c->recNew.scalf);
     c->SoVf = nullptr; c->itauf = nullptr; c->rho_wf = nullptr;
@@ -243,6 +245,14 @@ static bool ensure_dvm_capacity(gsis_ctx* c, long long Nd) {
     c->recNew.scal = (double*)dev_alloc(c, cap * RS * sizeof(double));
     c->recNew.tab = (double*)dev_alloc(c, cap * NTAB * NT * sizeof(double));
     c->enter_of = (int*)dev_alloc(c, cap * sizeof(int));
+    const long long nyz = (long long)c->vg.ny * c->vg.nz;
+    if (c->p.vdf_dtype == GSIS_F64) {
+        c->yzd = (double*)dev_alloc(c, cap * 5 * nyz * sizeof(double));
+        if (!c->yzd) return false;
+    } else {
+        c->yzf = (float*)dev_alloc(c, cap * 5 * nyz * sizeof(float));
+        if (!c->yzf) return false;
+    }
     if (c->p.vdf_dtype != GSIS_F64) {
         c->SoVf = (float*)dev_alloc(c, cap * 18 * sizeof(float));
         c->itauf = (float*)dev_alloc(c, cap * sizeof(float));

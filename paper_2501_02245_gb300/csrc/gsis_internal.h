@@ -142,6 +142,8 @@ struct gsis_ctx {
     int *dside_kind = nullptr, *dside_ref = nullptr, *dside_nb2 = nullptr;
     double* SoV = nullptr;
     float *SoVf = nullptr, *itauf = nullptr, *rho_wf = nullptr;   // FP32 mirrors for the FP32 sweep
+    double* yzd = nullptr;         // [Nd][5][ny*nz] y-z factors of g~ (FP64 sweep)
+    float* yzf = nullptr;          // the same for the FP32 sweep
     void* f = nullptr;
     double *itau = nullptr, *mom = nullptr, *rho_w = nullptr, *wall_den = nullptr;
     double *wall_in = nullptr;     // [N][6][5] incoming half-range moments of the wall Maxwellian

@@ -156,6 +156,8 @@ SweepArgs sweep_args(gsis_ctx* c) {
     a.recG = c->recG;
     a.recGhost = c->recGhost;
     a.recBC = c->recBC;
+    a.yzd = c->yzd;
+    a.yzf = c->yzf;
     a.vg = c->vg;
     return a;
 }

@@ -20,6 +20,8 @@ struct SweepArgs {
     const double* rho_w;  // [Nd][6]
     const float* rho_wf;
     Records recG, recGhost, recBC;
+    const double* yzd;    // [Nd][5][ny*nz] y-z factors of the reference distribution (FP64 sweep)
+    const float* yzf;     // the same in FP32 (FP32 sweep)
     VGridDev vg;
 };
 
@@ -66,11 +68,27 @@ __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
+// Reference distribution of a cell at velocity (ix, q = iy + ny iz) from the
+// x-tables of its record and its y-z factors (k_build_yz):
+//   g = E_x E_yz (D_yz + B_x + (R_x + R_yz)(C2_x + C2_yz) + C_x A_yz),
+// the record's E_x E_y E_z (p0 + sum B + sum R sum C2 + 2 sum_{i<j} P2_ij C_i C_j)
+// with the y-z sums formed once per cell instead of once per velocity.
+template <typename T>
+__device__ __forceinline__ T eval_g_yz(const T* __restrict__ tab, const T* __restrict__ yz, int NT, int nyz, int ix,
+                                       int q) {
+    const T E = __ldg(tab + ix), B = __ldg(tab + NT + ix), C = __ldg(tab + 2 * NT + ix);
+    const T C2 = __ldg(tab + 3 * NT + ix), R = __ldg(tab + 4 * NT + ix);
+    const T Eyz = __ldg(yz + q), D = __ldg(yz + nyz + q), Ryz = __ldg(yz + 2 * nyz + q);
+    const T Cyz = __ldg(yz + 3 * nyz + q), A = __ldg(yz + 4 * nyz + q);
+    const T poly = (D + B) + (R + Ryz) * (C2 + Cyz) + C * A;
+    return (E * Eyz) * poly;
+}
+
 // per-thread velocity data
 template <typename T, int VPT>
 struct Vel {
     long long v[VPT];
-    int ix[VPT], iy[VPT], iz[VPT];
+    int ix[VPT], iy[VPT], iz[VPT], q[VPT];   // q = iy + ny iz
     T x0[VPT], x1[VPT], x2[VPT];
     bool on[VPT];
 };
@@ -113,13 +131,14 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
     for (int b = 0; b < CB; ++b) {
         if (!kon[b]) continue;
         const int k = kk[b];
-        const T* gs = RecT<T>::scal(a.recG, k);
         const T* gt = RecT<T>::tab(a.recG, k, NT);
+        const int nyz = ny * a.vg.nz;
+        const T* yz = pick<T>(a.yzd, a.yzf) + (long long)k * 5 * nyz;
         T den[VPT], num[VPT];
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             den[u] = m[b].it;
-            num[u] = eval_recT<T>(gs, gt, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]) * m[b].it;
+            num[u] = eval_g_yz<T>(gt, yz, NT, nyz, V.ix[u], V.q[u]) * m[b].it;
         }
 #pragma unroll
         for (int d = 0; d < NC; ++d) {
@@ -238,7 +257,7 @@ __device__ __forceinline__ void make_vel(const VGridDev& vg, long long vbase, in
         V.on[u] = V.v[u] < vg.Nv;
         int ix = 0, iy = 0, iz = 0;
         if (V.on[u]) vsplit(V.v[u], vg.nx, vg.ny, ix, iy, iz);
-        V.ix[u] = ix; V.iy[u] = iy; V.iz[u] = iz;
+        V.ix[u] = ix; V.iy[u] = iy; V.iz[u] = iz; V.q[u] = iy + vg.ny * iz;
         V.x0[u] = (T)vg.xi[ix];
         V.x1[u] = (T)vg.xi[vg.nx + iy];
         V.x2[u] = (T)vg.xi[vg.nx + vg.ny + iz];
