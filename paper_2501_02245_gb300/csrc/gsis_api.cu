@@ -318,6 +318,7 @@ struct BatchPlan {
     int n_jobs = 0;
     std::vector<int> big;                       // solves too large for the fused synthetic-solve kernel
     int nc = 1, shape = 1, grid = 0;
+    int macro_cluster = 1;                      // CTAs per solve of the fused synthetic-solve launch
     bool tuned = false;
     std::vector<double> tune_ms;
     cudaGraph_t graph = nullptr;
@@ -474,6 +475,14 @@ gsis_status build_plan(BatchPlan* P) {
         P->W_at_capture.push_back(c->W);
     }
     P->n_jobs = (int)jobs.size();
+    {   // spread the fused synthetic solves over the SMs: clusters of up to 8 CTAs, at most one
+        // resident CTA per SM (its 512 threads use the register file)
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int want = P->n_jobs > 0 ? std::max(1, sms / P->n_jobs) : 1;
+        P->macro_cluster = fused_cluster_size(want);
+    }
     P->d_solves = (BatchSolve*)dev_alloc(o, n * sizeof(BatchSolve));
     P->d_ticket = (int*)dev_alloc(o, sizeof(int));
     P->d_jobs = (MacroJob*)dev_alloc(o, std::max(1, P->n_jobs) * sizeof(MacroJob));
@@ -520,7 +529,7 @@ gsis_status build_plan(BatchPlan* P) {
         }
         cudaEventRecordWithFlags(P->ev[1], P->stream, cudaEventRecordExternal);
         for (gsis_ctx* c : P->ctxs) stage_moments(c);
-        if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream);
+        if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream, P->macro_cluster);
         for (int i : P->big) {
             gsis_ctx* c = P->ctxs[i];
             macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0);
@@ -546,7 +555,8 @@ gsis_status build_plan(BatchPlan* P) {
     cudaGraphGetNodes(P->graph, nullptr, &nodes);
     P->info = std::string("solves=") + std::to_string(n) + " items=" + std::to_string(P->n_items) +
               " tile=" + batch_shape_name(P->shape) + (P->tuned ? " (autotuned" : " (default") +
-              ") grid=" + std::to_string(P->grid) + " fused_macro=" + std::to_string(P->n_jobs) +
+              ") grid=" + std::to_string(P->grid) + " fused_macro=" + std::to_string(P->n_jobs) + "x" +
+              std::to_string(P->macro_cluster) +
               " graph_nodes=" + std::to_string(nodes) + " kernels_per_iteration=" + std::to_string(P->launches_per_iter);
     if (!P->tune_ms.empty()) {
         P->info += " tune_ms=";

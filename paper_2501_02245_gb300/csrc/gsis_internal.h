@@ -220,7 +220,9 @@ void launch_face_geometry(gsis_ctx* c);
 void launch_wall_heat(gsis_ctx* c, double* out);
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term);
 MacroJob macro_job(gsis_ctx* c, int steps, bool time_term);
-void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream);
+void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream, int cs);
+int fused_cluster_size(int want);
+int fused_cluster_for(int N);
 void launch_eps(gsis_ctx* c, const double* Wn, const double* Wp);
 // adapt.cu
 void launch_kn_gll(gsis_ctx* c, const double* Wprim);
