@@ -83,8 +83,8 @@ struct SweepShape {
 static const SweepShape kShapesF64[] = {
     {2, 1, 2, "g2_v1_c2"}, {1, 1, 2, "g1_v1_c2"}, {4, 1, 1, "g4_v1_c1"}, {2, 1, 1, "g2_v1_c1"}};
 static const SweepShape kShapesF32[] = {
-    {4, 2, 2, "g4_v2_c2"}, {4, 1, 2, "g4_v1_c2"}, {8, 1, 1, "g8_v1_c1"},
-    {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"}, {2, 2, 2, "g2_v2_c2"}};
+    {8, 1, 1, "g8_v1_c1"}, {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"},
+    {4, 4, 1, "g4_v4_c1"}, {8, 4, 1, "g8_v4_c1"}, {4, 2, 2, "g4_v2_c2"}};
 
 // Candidates after the register-stencil shapes: the shared-memory window
 // sweep (sweep_ring.cu) with 8 warps x 32, 4 warps x 32 and 8 warps x 64
@@ -107,12 +107,12 @@ template <typename S>
 static void sweep_f32_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape) {
     if (c->normal_components == 1) { sweep_t<S, float, 1, 2, 1>(c, a, pass); return; }
     switch (shape) {
-        case 1: sweep_t<S, float, 4, 1, 2>(c, a, pass); break;
-        case 2: sweep_t<S, float, 8, 1, 1>(c, a, pass); break;
-        case 3: sweep_t<S, float, 4, 1, 1>(c, a, pass); break;
-        case 4: sweep_t<S, float, 8, 2, 1>(c, a, pass); break;
-        case 5: sweep_t<S, float, 2, 2, 2>(c, a, pass); break;
-        default: sweep_t<S, float, 4, 2, 2>(c, a, pass); break;
+        case 1: sweep_t<S, float, 4, 1, 1>(c, a, pass); break;
+        case 2: sweep_t<S, float, 8, 2, 1>(c, a, pass); break;
+        case 3: sweep_t<S, float, 4, 4, 1>(c, a, pass); break;
+        case 4: sweep_t<S, float, 8, 4, 1>(c, a, pass); break;
+        case 5: sweep_t<S, float, 4, 2, 2>(c, a, pass); break;
+        default: sweep_t<S, float, 8, 1, 1>(c, a, pass); break;
     }
 }
 
