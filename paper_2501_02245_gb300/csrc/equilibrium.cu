@@ -115,24 +115,35 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
         for (int k = 0; k < 6; ++k) Cs[d][k] = warp_sum(part[d][k]);
 
     double coef[12];   // p0', p'(3), P2'(diag 3), alpha(5)
+    // the 5 right-hand sides and 25 matrix entries of the correction system,
+    // one per lane (lanes 0-4: rhs, 5-29: A), gathered on lane 0
+    double mine = 0.0;
+    if (s.correct) {   // the same for every lane of the warp
+        Term tp[7], tq[19];
+        const double wa = vg.w * A;
+        if (lane < 5) {
+            const int na = psi_terms(lane, s.u, tp, 1.0);
+            const int nb = base_terms(s, tq);
+            mine = s.U[lane] - wa * poly_moment(tp, na, tq, nb, Cs);
+        } else if (lane < 30) {
+            const int ra = (lane - 5) / 5, rb = (lane - 5) % 5;
+            const int na = psi_terms(ra, s.u, tp, 1.0);
+            const int nbb = psi_terms(rb, s.u, tq, rb == 4 ? 2.0 : 1.0);
+            mine = wa * poly_moment(tp, na, tq, nbb, Cs);
+        }
+    }
+    double Am[5][5], rhs[5];
+    for (int t = 0; t < 30; ++t) {
+        const double v = __shfl_sync(0xffffffffu, mine, t);
+        if (t < 5) rhs[t] = v;
+        else Am[(t - 5) / 5][(t - 5) % 5] = v;
+    }
     if (lane == 0) {
         double pp[3] = {s.p[0], s.p[1], s.p[2]};
         double p2d[3] = {s.P2[0], s.P2[1], s.P2[2]};
         double p0 = s.p0;
         double alpha[5] = {0, 0, 0, 0, 0};
         if (s.correct) {
-            Term tp[7], tq[7], tb[19];
-            const int nb = base_terms(s, tb);
-            const double wa = vg.w * A;
-            double Am[5][5], rhs[5];
-            for (int a = 0; a < 5; ++a) {
-                const int na = psi_terms(a, s.u, tp, 1.0);
-                rhs[a] = s.U[a] - wa * poly_moment(tp, na, tb, nb, Cs);
-                for (int b = 0; b < 5; ++b) {
-                    const int nbb = psi_terms(b, s.u, tq, b == 4 ? 2.0 : 1.0);
-                    Am[a][b] = wa * poly_moment(tp, na, tq, nbb, Cs);
-                }
-            }
             solve5(Am, rhs, alpha);
             const double ua = alpha[1] * s.u[0] + alpha[2] * s.u[1] + alpha[3] * s.u[2];
             const double u2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
