@@ -95,6 +95,21 @@ def workload_name(config, dtype):
     }[config] + (", VDF " + dtype if config != "batch" else ", VDF f32 (even) / bf16 (odd)")
 
 
+def combine_ranks(points, ms, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the points all ranks
+    processed over the slowest rank's time (max over ranks).  Returns
+    (points per second, max milliseconds); dist is torch.distributed or None."""
+    if dist is None:
+        return points / (ms * 1e-3), ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    p = torch.tensor([float(points)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return float(p.item()) / (t_max * 1e-3), t_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,12 +271,7 @@ def run_gsis(args):
         pg.barrier()
     ms = e0.elapsed_time(e1)
     pts = rep["n_dvm"] * rep["n_v"] * args.steps
-    t_max = ms
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = pts * ws / (t_max * 1e-3)
+    value, t_max = combine_ranks(pts, ms, pg, "cuda")
     # dominant kernel: the sweep; its launches are bracketed by CUDA events on the context stream
     sweep_ms_per_launch = rep["phase_ms"]["sweep"] / max(rep["sweep_launches"], 1)
     pts_per_launch = rep["n_dvm"] * rep["n_v"]
@@ -342,13 +352,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
     pts_iter = sum(r["n_dvm"] * r["n_v"] for r in reps)
-    value = pts_iter * args.steps * ws / (t_max * 1e-3)
+    value, t_max = combine_ranks(pts_iter * args.steps, ms, pg, "cuda")
     sweep_ms = reps[0]["phase_ms"]["sweep"]
     eb = {"f32": 4, "bf16": 2}
     bytes_alg = sum(2 * 2 * eb[c.extra["vdf_dtype"]] * r["n_dvm"] * r["n_v"] for c, r in zip(cases, reps))
