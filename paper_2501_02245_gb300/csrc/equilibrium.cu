@@ -248,21 +248,23 @@ __global__ void k_cell_eq(int Nd, const int* __restrict__ dvm_cell, const double
 }
 
 // y-z factors of each DVM cell's reference distribution (see eval_g_yz):
-// yz[k][0..4][iy + ny iz] = E_y E_z, p0 + B_y + B_z + 2 P2_yz C_y C_z,
-// R_y + R_z, C2_y + C2_z, 2 (P2_xy C_y + P2_xz C_z), from the FP64 record.
+// yz[k][0..4][iy + ny iz] = E_y E_z / tau, p0 + B_y + B_z + 2 P2_yz C_y C_z,
+// R_y + R_z, C2_y + C2_z, 2 (P2_xy C_y + P2_xz C_z), from the FP64 record;
+// the first factor carries 1/tau, so eval_g_yz gives g~/tau directly.
 template <typename T>
-__global__ void k_build_yz(int Nd, Records rec, VGridDev vg, T* __restrict__ yz) {
+__global__ void k_build_yz(int Nd, Records rec, VGridDev vg, const double* __restrict__ itau, T* __restrict__ yz) {
     const int k = blockIdx.x;
     if (k >= Nd) return;
     const int NT = vg.NT, nx = vg.nx, ny = vg.ny, nyz = vg.ny * vg.nz;
     const double* tab = rec.tab + (long long)k * NTAB * NT;
     const double* sc = rec.scal + (long long)k * RS;
     const double p0 = sc[RS_P0], pxy = sc[RS_P2XY], pxz = sc[RS_P2XZ], pyz = sc[RS_P2YZ];
+    const double it = itau[k];
     T* out = yz + (long long)k * 5 * nyz;
     for (int q = threadIdx.x; q < nyz; q += blockDim.x) {
         const int jy = nx + q % ny, jz = nx + ny + q / ny;
         const double Cy = tab[2 * NT + jy], Cz = tab[2 * NT + jz];
-        out[q] = (T)(tab[jy] * tab[jz]);
+        out[q] = (T)(tab[jy] * tab[jz] * it);
         out[nyz + q] = (T)(p0 + (tab[NT + jy] + tab[NT + jz]) + 2.0 * pyz * Cy * Cz);
         out[2 * nyz + q] = (T)(tab[4 * NT + jy] + tab[4 * NT + jz]);
         out[3 * nyz + q] = (T)(tab[3 * NT + jy] + tab[3 * NT + jz]);
@@ -279,9 +281,9 @@ void launch_cell_eq(gsis_ctx* c) {
     c->launches++;
     launch_build_records(c, c->recG, Nd, c->specs);
     if (c->p.vdf_dtype == GSIS_F64)
-        k_build_yz<double><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->yzd);
+        k_build_yz<double><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, c->yzd);
     else
-        k_build_yz<float><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->yzf);
+        k_build_yz<float><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, c->yzf);
     c->launches++;
 }
 

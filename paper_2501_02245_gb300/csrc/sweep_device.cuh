@@ -49,18 +49,17 @@ template <typename T> __device__ __forceinline__ bool pos_t(T x);
 template <> __device__ __forceinline__ bool pos_t<float>(float x) { return x > 0.0f; }
 template <> __device__ __forceinline__ bool pos_t<double>(double x) { return __double_as_longlong(x) > 0; }
 
-// n / d for d > 0 in the normal range.  FP64: Newton-Raphson refinement of a
-// single-precision reciprocal seed (r <- r (2 - d r) doubles the correct
-// bits: ~24 -> ~48), the quotient q = n r and one residual correction
-// q <- q + r (n - d q); relative error a few units of 2^-53.  FP32: IEEE
-// division.
+// n / d for d > 0 in the normal range.  FP64: one Newton-Raphson step
+// r <- r (2 - d r) on a single-precision reciprocal seed (relative error
+// ~2^-23 -> ~2^-46) and q = n r: relative error below 2e-14, far inside the
+// tolerance of the scheme's FP64 results, for three FP64 operations.  FP32:
+// IEEE division.
 template <typename T> __device__ __forceinline__ T div_t(T n, T d);
 template <> __device__ __forceinline__ float div_t<float>(float n, float d) { return n / d; }
 template <> __device__ __forceinline__ double div_t<double>(double n, double d) {
     double r = (double)__frcp_rn(__double2float_rn(d));
     r = r * fma(-d, r, 2.0);
-    double q = n * r;
-    return fma(fma(-d, q, n), r, q);
+    return n * r;
 }
 
 template <typename T>
@@ -68,9 +67,10 @@ __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
-// Reference distribution of a cell at velocity (ix, q = iy + ny iz) from the
-// x-tables of its record and its y-z factors (k_build_yz):
-//   g = E_x E_yz (D_yz + B_x + (R_x + R_yz)(C2_x + C2_yz) + C_x A_yz),
+// Reference distribution of a cell at velocity (ix, q = iy + ny iz), divided
+// by tau, from the x-tables of its record and its y-z factors (k_build_yz,
+// whose E_yz carries 1/tau):
+//   g/tau = E_x E_yz (D_yz + B_x + (R_x + R_yz)(C2_x + C2_yz) + C_x A_yz),
 // the record's E_x E_y E_z (p0 + sum B + sum R sum C2 + 2 sum_{i<j} P2_ij C_i C_j)
 // with the y-z sums formed once per cell instead of once per velocity.
 template <typename T>
@@ -138,7 +138,7 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             den[u] = m[b].it;
-            num[u] = eval_g_yz<T>(gt, yz, NT, nyz, V.ix[u], V.q[u]) * m[b].it;
+            num[u] = eval_g_yz<T>(gt, yz, NT, nyz, V.ix[u], V.q[u]);   // g~ / tau
         }
 #pragma unroll
         for (int d = 0; d < NC; ++d) {
@@ -173,7 +173,7 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
                     if (NC >= 3) xn += V.x2[u] * m[b].S[2 * d][NC >= 3 ? 2 : 0];
                     T fin;
                     if (kl == SK_DVM)   // neighbour's face value: its value plus half its limited slope
-                        fin = vl + (l2 ? T(0.5) * mm_t<T>(vl - lo2[b][d][u], c0 - vl) : T(0));
+                        fin = fma(T(0.5), l2 ? mm_t<T>(vl - lo2[b][d][u], c0 - vl) : T(0), vl);
                     else
                         fin = scl * eval_recT<T>(bsl, btl, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
                     const bool out = pos_t<T>(xn);
@@ -186,7 +186,7 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
                     if (NC >= 3) xn += V.x2[u] * m[b].S[2 * d + 1][NC >= 3 ? 2 : 0];
                     T fin;
                     if (kh == SK_DVM)
-                        fin = vh - (h2 ? T(0.5) * mm_t<T>(vh - c0, hi2[b][d][u] - vh) : T(0));
+                        fin = fma(T(-0.5), h2 ? mm_t<T>(vh - c0, hi2[b][d][u] - vh) : T(0), vh);
                     else
                         fin = sch * eval_recT<T>(bsh, bth, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
                     const bool out = pos_t<T>(xn);
