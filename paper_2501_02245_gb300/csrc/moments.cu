@@ -75,20 +75,20 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
         const int jy = nx + iy, jz = nx + ny + iz;
         const double xy = vg.xi[jy], xz = vg.xi[jz];
         const double cy = xy - uy, cz = xz - uz;
-        T eN = T(0), bN = T(0), c2N = T(0), rN = T(0), eH = T(0), bH = T(0), c2H = T(0), rH = T(0);
+        T eN = T(0), bN = T(0), eH = T(0), bH = T(0);
         if (CORRECT) {
             eN = TN[jy] * TN[jz]; bN = TN[NT + jy] + TN[NT + jz];
-            c2N = TN[3 * NT + jy] + TN[3 * NT + jz]; rN = TN[4 * NT + jy] + TN[4 * NT + jz];
             eH = TH[jy] * TH[jz]; bH = TH[NT + jy] + TH[NT + jz];
-            c2H = TH[3 * NT + jy] + TH[3 * NT + jz]; rH = TH[4 * NT + jy] + TH[4 * NT + jz];
         }
         S* row = fk + (long long)r * nx;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         for (int ix = 0; ix < nx; ++ix) {
             T fv = ldT<T, S>(row + ix);
             if (CORRECT) {
-                const T vN = (tN[ix] * eN) * (p0N + (tN[nx + ix] + bN) + (tN[3 * nx + ix] + rN) * (tN[2 * nx + ix] + c2N));
-                const T vH = (tH[ix] * eH) * (p0H + (tH[nx + ix] + bH) + (tH[3 * nx + ix] + rH) * (tH[2 * nx + ix] + c2H));
+                // the correction records are conservation-corrected Maxwellians: their
+                // cubic (r.c) c^2 term is identically zero, so P = p0 + B
+                const T vN = (tN[ix] * eN) * (p0N + (tN[nx + ix] + bN));
+                const T vH = (tH[ix] * eH) * (p0H + (tH[nx + ix] + bH));
                 stT<T, S>(row + ix, fv + (vN - vH));
                 fv = ldT<T, S>(row + ix);   // moments of the stored value
             }
