@@ -178,6 +178,36 @@ __global__ void k_dvm_sides(int Nd, const int* __restrict__ dvm_cell, const int*
     }
 }
 
+// Packed per-cell data of the sweep (layout in sweep_device.cuh) from the
+// side lists: rows, second-neighbour rows (the neighbour's own row where a
+// DVM side has none), side kinds with the all-DVM bit over the nc flux
+// directions, and S/V component-major in the arithmetic type T.
+template <typename T>
+__global__ void k_sweep_desc(int Nd, int nc, const int* __restrict__ kind, const int* __restrict__ ref,
+                             const int* __restrict__ nb2, const double* __restrict__ SoV, int* __restrict__ sdi,
+                             T* __restrict__ sdv) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nd) return;
+    int w[SD_INTS];
+    for (int i = 0; i < SD_INTS; ++i) w[i] = 0;
+    unsigned kinds = 0;
+    bool interior = true;
+    for (int s = 0; s < 6; ++s) {
+        const int kd = kind[(long long)k * 6 + s], r = ref[(long long)k * 6 + s];
+        int r2 = nb2[(long long)k * 6 + s];
+        if (kd != SK_DVM || r2 < 0) r2 = r;
+        if (s < 2 * nc && kd != SK_DVM) interior = false;
+        kinds |= (unsigned)kd << (3 * s);
+        if (s < 4) { w[s] = r; w[4 + s] = r2; }
+        else { w[8 + (s - 4)] = r; w[10 + (s - 4)] = r2; }
+    }
+    w[12] = (int)(kinds | (interior ? 0x80000000u : 0u));
+    for (int i = 0; i < SD_INTS; ++i) sdi[(long long)k * SD_INTS + i] = w[i];
+    for (int q = 0; q < 3; ++q)
+        for (int s = 0; s < 8; ++s)
+            sdv[(long long)k * SD_VALS + 8 * q + s] = s < 6 ? (T)SoV[((long long)k * 6 + s) * 3 + q] : T(0);
+}
+
 __global__ void k_enter_mark(int Nd, const int* __restrict__ dvm_cell, const int* __restrict__ old_c2d,
                              int* __restrict__ enter_list, int* __restrict__ enter_of, int* __restrict__ counter) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,8 +252,10 @@ static bool ensure_dvm_capacity(gsis_ctx* c, long long Nd) {
     dev_free(c, c->recG.scal); dev_free(c, c->recG.tab); dev_free(c, c->recHalf.scal); dev_free(c, c->recHalf.tab);
     dev_free(c, c->recNew.scal); dev_free(c, c->recNew.tab); dev_free(c, c->enter_of);
     dev_free(c, c->SoVf); dev_free(c, c->itauf); dev_free(c, c->rho_wf);
-    dev_free(c, c->yzd); dev_free(c, c->yzf);
-    c->yzd = nullptr; c->yzf = nullptr;
+    dev_free(c, c->sd_int); dev_free(c, c->sd_val);
+    dev_free(c, c->gx4); dev_free(c, c->gx1); dev_free(c, c->gy4); dev_free(c, c->gy1);
+    c->sd_int = nullptr; c->sd_val = nullptr;
+    c->gx4 = c->gx1 = c->gy4 = c->gy1 = nullptr;
     dev_free(c, c->recG.tabf); dev_free(c, c->recG.scalf); dev_free(c, c->recHalf.tabf);
     dev_free(c, c->recHalf.scalf); dev_free(c, c->recNew.tabf); dev_free(c, c->recNew.scalf);
     c->SoVf = nullptr; c->itauf = nullptr; c->rho_wf = nullptr;
@@ -245,13 +277,16 @@ static bool ensure_dvm_capacity(gsis_ctx* c, long long Nd) {
     c->recNew.scal = (double*)dev_alloc(c, cap * RS * sizeof(double));
     c->recNew.tab = (double*)dev_alloc(c, cap * NTAB * NT * sizeof(double));
     c->enter_of = (int*)dev_alloc(c, cap * sizeof(int));
-    const long long nyz = (long long)c->vg.ny * c->vg.nz;
-    if (c->p.vdf_dtype == GSIS_F64) {
-        c->yzd = (double*)dev_alloc(c, cap * 5 * nyz * sizeof(double));
-        if (!c->yzd) return false;
-    } else {
-        c->yzf = (float*)dev_alloc(c, cap * 5 * nyz * sizeof(float));
-        if (!c->yzf) return false;
+    {   // sweep data in the sweep's arithmetic type
+        const long long nyz = (long long)c->vg.ny * c->vg.nz;
+        const size_t tb = c->p.vdf_dtype == GSIS_F64 ? sizeof(double) : sizeof(float);
+        c->sd_int = (int*)dev_alloc(c, cap * SD_INTS * sizeof(int));
+        c->sd_val = dev_alloc(c, cap * SD_VALS * tb);
+        c->gx4 = dev_alloc(c, cap * c->vg.nx * 4 * tb);
+        c->gx1 = dev_alloc(c, cap * c->vg.nx * tb);
+        c->gy4 = dev_alloc(c, cap * nyz * 4 * tb);
+        c->gy1 = dev_alloc(c, cap * nyz * tb);
+        if (!c->sd_int || !c->sd_val || !c->gx4 || !c->gx1 || !c->gy4 || !c->gy1) return false;
     }
     if (c->p.vdf_dtype != GSIS_F64) {
         c->SoVf = (float*)dev_alloc(c, cap * 18 * sizeof(float));
@@ -316,9 +351,17 @@ int build_region(gsis_ctx* c) {
         k_dvm_sides<<<kb, 128, 0, c->stream>>>((int)Nd_new, c->dvm_cell, c->cell2dvm, c->m.nbr, c->m.side_bc,
                                                c->m.Sout, c->m.vol, c->ghost_id, c->dside_kind, c->dside_ref,
                                                c->dside_nb2, c->SoV, c->SoVf);
+        if (c->p.vdf_dtype == GSIS_F64)
+            k_sweep_desc<double><<<kb, 128, 0, c->stream>>>((int)Nd_new, c->normal_components, c->dside_kind,
+                                                            c->dside_ref, c->dside_nb2, c->SoV, c->sd_int,
+                                                            (double*)c->sd_val);
+        else
+            k_sweep_desc<float><<<kb, 128, 0, c->stream>>>((int)Nd_new, c->normal_components, c->dside_kind,
+                                                           c->dside_ref, c->dside_nb2, c->SoV, c->sd_int,
+                                                           (float*)c->sd_val);
         k_enter_mark<<<kb, 128, 0, c->stream>>>((int)Nd_new, c->dvm_cell, c->old_cell2dvm, c->enter_list,
                                                 c->enter_of, c->d_count + 1);
-        c->launches += 2;
+        c->launches += 3;
     }
     cudaMemcpyAsync(c->h_count, c->d_count, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "region lists")) return -1;

@@ -247,12 +247,16 @@ __global__ void k_cell_eq(int Nd, const int* __restrict__ dvm_cell, const double
     }
 }
 
-// y-z factors of each DVM cell's reference distribution (see eval_g_yz):
-// yz[k][0..4][iy + ny iz] = E_y E_z / tau, p0 + B_y + B_z + 2 P2_yz C_y C_z,
-// R_y + R_z, C2_y + C2_z, 2 (P2_xy C_y + P2_xz C_z), from the FP64 record;
-// the first factor carries 1/tau, so eval_g_yz gives g~/tau directly.
+// Factor vectors of g~/tau for the sweep (eval_g in sweep_device.cuh), one
+// block per DVM cell, from the cell's record (Eq. updatef's corrected
+// Maxwellian tables) and 1/tau; formed in FP64 and stored in the sweep's
+// arithmetic type T:
+//   x(ix) = (E, E (B + R C2), E R, E C2 ; E C)             [gx4 ; gx1]
+//   y(q)  = E_yz/tau (D + R_yz C2_yz, 1, C2_yz, R_yz ; A)   [gy4 ; gy1]
+// so that g~/tau = sum of the five products x_i y_i.
 template <typename T>
-__global__ void k_build_yz(int Nd, Records rec, VGridDev vg, const double* __restrict__ itau, T* __restrict__ yz) {
+__global__ void k_build_gtab(int Nd, Records rec, VGridDev vg, const double* __restrict__ itau, T* __restrict__ gx4,
+                             T* __restrict__ gx1, T* __restrict__ gy4, T* __restrict__ gy1) {
     const int k = blockIdx.x;
     if (k >= Nd) return;
     const int NT = vg.NT, nx = vg.nx, ny = vg.ny, nyz = vg.ny * vg.nz;
@@ -260,15 +264,29 @@ __global__ void k_build_yz(int Nd, Records rec, VGridDev vg, const double* __res
     const double* sc = rec.scal + (long long)k * RS;
     const double p0 = sc[RS_P0], pxy = sc[RS_P2XY], pxz = sc[RS_P2XZ], pyz = sc[RS_P2YZ];
     const double it = itau[k];
-    T* out = yz + (long long)k * 5 * nyz;
+    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+        const double E = tab[ix], B = tab[NT + ix], C = tab[2 * NT + ix], C2 = tab[3 * NT + ix], R = tab[4 * NT + ix];
+        T* o = gx4 + ((long long)k * nx + ix) * 4;
+        o[0] = (T)E;
+        o[1] = (T)(E * (B + R * C2));
+        o[2] = (T)(E * R);
+        o[3] = (T)(E * C2);
+        gx1[(long long)k * nx + ix] = (T)(E * C);
+    }
     for (int q = threadIdx.x; q < nyz; q += blockDim.x) {
         const int jy = nx + q % ny, jz = nx + ny + q / ny;
         const double Cy = tab[2 * NT + jy], Cz = tab[2 * NT + jz];
-        out[q] = (T)(tab[jy] * tab[jz] * it);
-        out[nyz + q] = (T)(p0 + (tab[NT + jy] + tab[NT + jz]) + 2.0 * pyz * Cy * Cz);
-        out[2 * nyz + q] = (T)(tab[4 * NT + jy] + tab[4 * NT + jz]);
-        out[3 * nyz + q] = (T)(tab[3 * NT + jy] + tab[3 * NT + jz]);
-        out[4 * nyz + q] = (T)(2.0 * (pxy * Cy + pxz * Cz));
+        const double Eyz = tab[jy] * tab[jz] * it;
+        const double D = p0 + (tab[NT + jy] + tab[NT + jz]) + 2.0 * pyz * Cy * Cz;
+        const double Ryz = tab[4 * NT + jy] + tab[4 * NT + jz];
+        const double C2yz = tab[3 * NT + jy] + tab[3 * NT + jz];
+        const double A = 2.0 * (pxy * Cy + pxz * Cz);
+        T* o = gy4 + ((long long)k * nyz + q) * 4;
+        o[0] = (T)(Eyz * (D + Ryz * C2yz));
+        o[1] = (T)Eyz;
+        o[2] = (T)(Eyz * C2yz);
+        o[3] = (T)(Eyz * Ryz);
+        gy1[(long long)k * nyz + q] = (T)(Eyz * A);
     }
 }
 
@@ -281,9 +299,11 @@ void launch_cell_eq(gsis_ctx* c) {
     c->launches++;
     launch_build_records(c, c->recG, Nd, c->specs);
     if (c->p.vdf_dtype == GSIS_F64)
-        k_build_yz<double><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, c->yzd);
+        k_build_gtab<double><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, (double*)c->gx4,
+                                                        (double*)c->gx1, (double*)c->gy4, (double*)c->gy1);
     else
-        k_build_yz<float><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, c->yzf);
+        k_build_gtab<float><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, (float*)c->gx4,
+                                                       (float*)c->gx1, (float*)c->gy4, (float*)c->gy1);
     c->launches++;
 }
 

@@ -32,6 +32,9 @@ enum { RS_P0 = 0, RS_P2XY = 1, RS_P2XZ = 2, RS_P2YZ = 3, RS_OFFD = 4, RS_UX = 5,
 
 // DVM side kinds
 enum { SK_NONE = 0, SK_DVM = 1, SK_GHOST = 2, SK_FAR = 3, SK_WALL = 4 };
+// packed sweep data per DVM cell: integers and values (layout in sweep_device.cuh)
+constexpr int SD_INTS = 16;
+constexpr int SD_VALS = 24;
 
 struct VGridDev {
     int nx, ny, nz, NT;
@@ -142,8 +145,10 @@ struct gsis_ctx {
     int *dside_kind = nullptr, *dside_ref = nullptr, *dside_nb2 = nullptr;
     double* SoV = nullptr;
     float *SoVf = nullptr, *itauf = nullptr, *rho_wf = nullptr;   // FP32 mirrors for the FP32 sweep
-    double* yzd = nullptr;         // [Nd][5][ny*nz] y-z factors of g~ (FP64 sweep)
-    float* yzf = nullptr;          // the same for the FP32 sweep
+    int* sd_int = nullptr;         // [Nd][SD_INTS] packed sweep data per DVM cell (k_sweep_desc)
+    void* sd_val = nullptr;        // [Nd][SD_VALS] S/V of the sides, in the sweep's arithmetic type
+    void *gx4 = nullptr, *gx1 = nullptr;   // [Nd][nx] x factor vectors of g~/tau (k_build_gtab)
+    void *gy4 = nullptr, *gy1 = nullptr;   // [Nd][ny*nz] y-z factor vectors
     void* f = nullptr;
     double *itau = nullptr, *mom = nullptr, *rho_w = nullptr, *wall_den = nullptr;
     double *wall_in = nullptr;     // [N][6][5] incoming half-range moments of the wall Maxwellian

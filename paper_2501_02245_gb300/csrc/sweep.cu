@@ -144,20 +144,18 @@ SweepArgs sweep_args(gsis_ctx* c) {
     SweepArgs a;
     a.H = c->m.H;
     a.hp_off = c->hp_off;
-    a.kind = c->dside_kind;
-    a.ref = c->dside_ref;
-    a.nb2 = c->dside_nb2;
-    a.SoV = c->SoV;
-    a.SoVf = c->SoVf;
+    a.sdi = c->sd_int;
+    a.sdv = c->sd_val;
     a.itau = c->itau;
     a.itauf = c->itauf;
     a.rho_w = c->rho_w;
     a.rho_wf = c->rho_wf;
-    a.recG = c->recG;
     a.recGhost = c->recGhost;
     a.recBC = c->recBC;
-    a.yzd = c->yzd;
-    a.yzf = c->yzf;
+    a.gx4 = c->gx4;
+    a.gx1 = c->gx1;
+    a.gy4 = c->gy4;
+    a.gy1 = c->gy1;
     a.vg = c->vg;
     return a;
 }

@@ -7,21 +7,30 @@
 
 namespace gsis {
 
+// Packed per-cell data of the sweep (k_sweep_desc, rebuilt with the DVM
+// region).  Integers, SD_INTS per cell: [0..3] neighbour row (DVM side) or
+// record index (ghost / boundary side) of sides 0..3, [4..7] second-neighbour
+// rows of sides 0..3, [8..9] / [10..11] the same for sides 4..5, [12] the side
+// kinds (3 bits per side) with bit 31 set when every side that carries flux
+// is a DVM side.  Where a DVM side has no second neighbour its entry repeats
+// the neighbour's row: the slope test then sees a zero difference and gives a
+// zero slope, the value the scheme prescribes there, without a branch.
+// Values, SD_VALS per cell in the arithmetic type: S/V component-major,
+// [q * 8 + s] for component q < 3 of side s < 6.
+// (SD_INTS = 16, SD_VALS = 24: gsis_internal.h.)
 struct SweepArgs {
     int H;
     const int* hp_off;
-    const int* kind;      // [Nd][6]
-    const int* ref;       // [Nd][6]
-    const int* nb2;       // [Nd][6]
-    const double* SoV;    // [Nd][6][3]
-    const float* SoVf;
+    const int* sdi;       // [Nd][SD_INTS]
+    const void* sdv;      // [Nd][SD_VALS], double (FP64 sweep) or float
     const double* itau;   // [Nd] 1/tau
     const float* itauf;
     const double* rho_w;  // [Nd][6]
     const float* rho_wf;
-    Records recG, recGhost, recBC;
-    const double* yzd;    // [Nd][5][ny*nz] y-z factors of the reference distribution (FP64 sweep)
-    const float* yzf;     // the same in FP32 (FP32 sweep)
+    Records recGhost, recBC;
+    // factor vectors of the reference distribution (k_build_gtab), in the
+    // arithmetic type: gx4/gx1 [Nd][nx] (4-vector, scalar), gy4/gy1 [Nd][ny*nz]
+    const void *gx4, *gx1, *gy4, *gy1;
     VGridDev vg;
 };
 
@@ -67,28 +76,43 @@ __device__ __forceinline__ const T* pick(const double* d, const float* f);
 template <> __device__ __forceinline__ const double* pick<double>(const double* d, const float*) { return d; }
 template <> __device__ __forceinline__ const float* pick<float>(const double*, const float* f) { return f; }
 
-// Reference distribution of a cell at velocity (ix, q = iy + ny iz), divided
-// by tau, from the x-tables of its record and its y-z factors (k_build_yz,
-// whose E_yz carries 1/tau):
-//   g/tau = E_x E_yz (D_yz + B_x + (R_x + R_yz)(C2_x + C2_yz) + C_x A_yz),
-// the record's E_x E_y E_z (p0 + sum B + sum R sum C2 + 2 sum_{i<j} P2_ij C_i C_j)
-// with the y-z sums formed once per cell instead of once per velocity.
-template <typename T>
-__device__ __forceinline__ T eval_g_yz(const T* __restrict__ tab, const T* __restrict__ yz, int NT, int nyz, int ix,
-                                       int q) {
-    const T E = __ldg(tab + ix), B = __ldg(tab + NT + ix), C = __ldg(tab + 2 * NT + ix);
-    const T C2 = __ldg(tab + 3 * NT + ix), R = __ldg(tab + 4 * NT + ix);
-    const T Eyz = __ldg(yz + q), D = __ldg(yz + nyz + q), Ryz = __ldg(yz + 2 * nyz + q);
-    const T Cyz = __ldg(yz + 3 * nyz + q), A = __ldg(yz + 4 * nyz + q);
-    const T poly = (D + B) + (R + Ryz) * (C2 + Cyz) + C * A;
-    return (E * Eyz) * poly;
+template <typename T> struct V4 { T x, y, z, w; };
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(p)), v = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return {u.x, u.y, v.x, v.y};
 }
 
-// per-thread velocity data
+// Reference distribution of cell k at velocity (ix, q = iy + ny iz), divided
+// by tau.  The record's E_x E_y E_z (p0 + sum B + sum R sum C2
+// + 2 sum_{i<j} P2_ij C_i C_j), split into its x and y-z parts, is the sum of
+// five products x_i y_i (k_build_gtab):
+//   x = (E_x, E_x (B_x + R_x C2_x), E_x R_x, E_x C2_x, E_x C_x)
+//   y = E_yz/tau (D + R_yz C2_yz, 1, C2_yz, R_yz, A)
+// with E_yz = E_y E_z, D = p0 + B_y + B_z + 2 P2_yz C_y C_z, R_yz = R_y + R_z,
+// C2_yz = C2_y + C2_z and A = 2 (P2_xy C_y + P2_xz C_z).
+template <typename T>
+__device__ __forceinline__ T eval_g(const SweepArgs& a, int k, int ix, int q) {
+    const int kx = k * a.vg.nx + ix, ky = k * (a.vg.ny * a.vg.nz) + q;
+    const V4<T> x = ld4(static_cast<const T*>(a.gx4) + 4 * (long long)kx);
+    const V4<T> y = ld4(static_cast<const T*>(a.gy4) + 4 * (long long)ky);
+    T g = __ldg(static_cast<const T*>(a.gx1) + kx) * __ldg(static_cast<const T*>(a.gy1) + ky);
+    g = fma(x.x, y.x, g);
+    g = fma(x.y, y.y, g);
+    g = fma(x.z, y.z, g);
+    return fma(x.w, y.w, g);
+}
+
+// per-thread velocity data.  In the ragged last tile of the grid the
+// velocities past the end are clamped to the last one: their loads stay in
+// bounds and their results are not stored.
 template <typename T, int VPT>
 struct Vel {
-    long long v[VPT];
-    int ix[VPT], iy[VPT], iz[VPT], q[VPT];   // q = iy + ny iz
+    int v[VPT];             // flat velocity index (clamped)
+    int ix[VPT], q[VPT];    // q = iy + ny iz
     T x0[VPT], x1[VPT], x2[VPT];
     bool on[VPT];
 };
@@ -96,32 +120,51 @@ struct Vel {
 // metadata of one DVM cell
 template <typename T, int NC>
 struct CellMeta {
-    int kd[2 * NC], rf[2 * NC], n2[2 * NC];
-    T it;
+    int kinds;              // packed side kinds, bit 31: every flux side is a DVM side
+    int rf[2 * NC], n2[2 * NC];
     T S[2 * NC][NC];
-    T wall[2 * NC];
+    T it;
 };
+
+__device__ __forceinline__ int side_kind(int kinds, int s) { return (kinds >> (3 * s)) & 7; }
+
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T& a, T& b) {
+    a = __ldg(p);
+    b = __ldg(p + 1);
+}
 
 template <typename T, int NC>
 __device__ __forceinline__ void load_meta(const SweepArgs& a, int k, CellMeta<T, NC>& m) {
-    const T* So = pick<T>(a.SoV, a.SoVf) + (long long)k * 18;
-    const T* rw = pick<T>(a.rho_w, a.rho_wf) + (long long)k * 6;
+    const int* p = a.sdi + (long long)k * SD_INTS;
+    const int4 r = __ldg(reinterpret_cast<const int4*>(p)), r2 = __ldg(reinterpret_cast<const int4*>(p) + 1);
+    m.kinds = __ldg(p + 12);
+    m.rf[0] = r.x; m.rf[1] = r.y; m.n2[0] = r2.x; m.n2[1] = r2.y;
+    if constexpr (NC >= 2) { m.rf[2] = r.z; m.rf[3] = r.w; m.n2[2] = r2.z; m.n2[3] = r2.w; }
+    if constexpr (NC >= 3) {
+        const int4 r3 = __ldg(reinterpret_cast<const int4*>(p) + 2);
+        m.rf[4] = r3.x; m.rf[5] = r3.y; m.n2[4] = r3.z; m.n2[5] = r3.w;
+    }
+    const T* sv = static_cast<const T*>(a.sdv) + (long long)k * SD_VALS;
 #pragma unroll
-    for (int s = 0; s < 2 * NC; ++s) {
-        m.kd[s] = __ldg(a.kind + (long long)k * 6 + s);
-        m.rf[s] = __ldg(a.ref + (long long)k * 6 + s);
-        m.n2[s] = __ldg(a.nb2 + (long long)k * 6 + s);
-#pragma unroll
-        for (int q = 0; q < NC; ++q) m.S[s][q] = __ldg(So + 3 * s + q);
-        m.wall[s] = __ldg(rw + s);
+    for (int q = 0; q < NC; ++q) {
+        if constexpr (NC == 1) {
+            ld2<T>(sv, m.S[0][0], m.S[1][0]);
+        } else {
+            const V4<T> v = ld4(sv + 8 * q);
+            m.S[0][q] = v.x; m.S[1][q] = v.y; m.S[2][q] = v.z; m.S[3][q] = v.w;
+            if constexpr (NC >= 3) ld2<T>(sv + 8 * q + 4, m.S[4][q], m.S[5][q]);
+        }
     }
     m.it = __ldg(pick<T>(a.itau, a.itauf) + k);
 }
 
 // The implicit update of CB cells x VPT velocities from their gathered
 // stencils (own value fc, neighbours lo/hi and second neighbours lo2/hi2 per
-// direction; a missing neighbour repeats the nearer value): new values in fo.
-template <typename T, int NC, int VPT, int CB>
+// direction; a side that is not a DVM side repeats the own value, a missing
+// second neighbour the neighbour's): new values in fo.  INTERIOR: every flux
+// side of every cell is a DVM side (compiled without the side-kind branches).
+template <typename T, int NC, int VPT, int CB, bool INTERIOR>
 __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk, const bool* kon,
                                               const Vel<T, VPT>& V, const CellMeta<T, NC>* m, const T (*fc)[VPT],
                                               const T (*lo)[NC][VPT], const T (*hi)[NC][VPT],
@@ -131,67 +174,71 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
     for (int b = 0; b < CB; ++b) {
         if (!kon[b]) continue;
         const int k = kk[b];
-        const T* gt = RecT<T>::tab(a.recG, k, NT);
-        const int nyz = ny * a.vg.nz;
-        const T* yz = pick<T>(a.yzd, a.yzf) + (long long)k * 5 * nyz;
         T den[VPT], num[VPT];
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             den[u] = m[b].it;
-            num[u] = eval_g_yz<T>(gt, yz, NT, nyz, V.ix[u], V.q[u]);   // g~ / tau
+            num[u] = eval_g<T>(a, k, V.ix[u], V.q[u]);   // g~ / tau
         }
 #pragma unroll
         for (int d = 0; d < NC; ++d) {
-            const int kl = m[b].kd[2 * d], kh = m[b].kd[2 * d + 1];
+            const int kl = INTERIOR ? SK_DVM : side_kind(m[b].kinds, 2 * d);
+            const int kh = INTERIOR ? SK_DVM : side_kind(m[b].kinds, 2 * d + 1);
             if (kl == SK_NONE && kh == SK_NONE) continue;
-            const bool both = kl == SK_DVM && kh == SK_DVM;
-            const bool l2 = m[b].n2[2 * d] >= 0, h2 = m[b].n2[2 * d + 1] >= 0;
             // interface / boundary distributions of the non-DVM sides (the side
             // kinds are the same for every lane of the warp: uniform branches)
             const T *bsl = nullptr, *btl = nullptr, *bsh = nullptr, *bth = nullptr;
             T scl = T(1), sch = T(1);
-            if (kl == SK_GHOST || kl == SK_FAR || kl == SK_WALL) {
-                const Records& R = kl == SK_GHOST ? a.recGhost : a.recBC;
-                bsl = RecT<T>::scal(R, m[b].rf[2 * d]);
-                btl = RecT<T>::tab(R, m[b].rf[2 * d], NT);
-                if (kl == SK_WALL) scl = m[b].wall[2 * d];
-            }
-            if (kh == SK_GHOST || kh == SK_FAR || kh == SK_WALL) {
-                const Records& R = kh == SK_GHOST ? a.recGhost : a.recBC;
-                bsh = RecT<T>::scal(R, m[b].rf[2 * d + 1]);
-                bth = RecT<T>::tab(R, m[b].rf[2 * d + 1], NT);
-                if (kh == SK_WALL) sch = m[b].wall[2 * d + 1];
+            if (!INTERIOR) {
+                if (kl == SK_GHOST || kl == SK_FAR || kl == SK_WALL) {
+                    const Records& R = kl == SK_GHOST ? a.recGhost : a.recBC;
+                    bsl = RecT<T>::scal(R, m[b].rf[2 * d]);
+                    btl = RecT<T>::tab(R, m[b].rf[2 * d], NT);
+                    if (kl == SK_WALL) scl = __ldg(pick<T>(a.rho_w, a.rho_wf) + (long long)k * 6 + 2 * d);
+                }
+                if (kh == SK_GHOST || kh == SK_FAR || kh == SK_WALL) {
+                    const Records& R = kh == SK_GHOST ? a.recGhost : a.recBC;
+                    bsh = RecT<T>::scal(R, m[b].rf[2 * d + 1]);
+                    bth = RecT<T>::tab(R, m[b].rf[2 * d + 1], NT);
+                    if (kh == SK_WALL) sch = __ldg(pick<T>(a.rho_w, a.rho_wf) + (long long)k * 6 + 2 * d + 1);
+                }
             }
 #pragma unroll
             for (int u = 0; u < VPT; ++u) {
                 const T c0 = fc[b][u], vl = lo[b][d][u], vh = hi[b][d][u];
-                // half the cell's own limited slope (outgoing face values c0 -+ hown)
-                const T hown = both ? T(0.5) * mm_t<T>(c0 - vl, vh - c0) : T(0);
+                const T dl = c0 - vl, dh = vh - c0;
+                // half the cell's own limited slope (outgoing face values c0 -+ hown);
+                // zero next to a side that is not a DVM side (its value repeats c0)
+                const T hown = T(0.5) * mm_t<T>(dl, dh);
                 if (kl != SK_NONE) {
                     T xn = V.x0[u] * m[b].S[2 * d][0];
-                    if (NC >= 2) xn += V.x1[u] * m[b].S[2 * d][NC >= 2 ? 1 : 0];
-                    if (NC >= 3) xn += V.x2[u] * m[b].S[2 * d][NC >= 3 ? 2 : 0];
+                    if constexpr (NC >= 2) xn = fma(V.x1[u], m[b].S[2 * d][NC >= 2 ? 1 : 0], xn);
+                    if constexpr (NC >= 3) xn = fma(V.x2[u], m[b].S[2 * d][NC >= 3 ? 2 : 0], xn);
                     T fin;
-                    if (kl == SK_DVM)   // neighbour's face value: its value plus half its limited slope
-                        fin = fma(T(0.5), l2 ? mm_t<T>(vl - lo2[b][d][u], c0 - vl) : T(0), vl);
-                    else
-                        fin = scl * eval_recT<T>(bsl, btl, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
+                    if (kl == SK_DVM) {   // neighbour's face value: its value plus half its limited slope
+                        fin = fma(T(0.5), mm_t<T>(vl - lo2[b][d][u], dl), vl);
+                    } else {
+                        const int iz = V.q[u] / ny;
+                        fin = scl * eval_recT<T>(bsl, btl, NT, nx, ny, V.ix[u], V.q[u] - ny * iz, iz);
+                    }
                     const bool out = pos_t<T>(xn);
                     den[u] += out ? xn : T(0);
-                    num[u] -= xn * (out ? -hown : fin);
+                    num[u] = fma(-xn, out ? -hown : fin, num[u]);
                 }
                 if (kh != SK_NONE) {
                     T xn = V.x0[u] * m[b].S[2 * d + 1][0];
-                    if (NC >= 2) xn += V.x1[u] * m[b].S[2 * d + 1][NC >= 2 ? 1 : 0];
-                    if (NC >= 3) xn += V.x2[u] * m[b].S[2 * d + 1][NC >= 3 ? 2 : 0];
+                    if constexpr (NC >= 2) xn = fma(V.x1[u], m[b].S[2 * d + 1][NC >= 2 ? 1 : 0], xn);
+                    if constexpr (NC >= 3) xn = fma(V.x2[u], m[b].S[2 * d + 1][NC >= 3 ? 2 : 0], xn);
                     T fin;
-                    if (kh == SK_DVM)
-                        fin = fma(T(-0.5), h2 ? mm_t<T>(vh - c0, hi2[b][d][u] - vh) : T(0), vh);
-                    else
-                        fin = sch * eval_recT<T>(bsh, bth, NT, nx, ny, V.ix[u], V.iy[u], V.iz[u]);
+                    if (kh == SK_DVM) {
+                        fin = fma(T(-0.5), mm_t<T>(dh, hi2[b][d][u] - vh), vh);
+                    } else {
+                        const int iz = V.q[u] / ny;
+                        fin = sch * eval_recT<T>(bsh, bth, NT, nx, ny, V.ix[u], V.q[u] - ny * iz, iz);
+                    }
                     const bool out = pos_t<T>(xn);
                     den[u] += out ? xn : T(0);
-                    num[u] -= xn * (out ? hown : fin);
+                    num[u] = fma(-xn, out ? hown : fin, num[u]);
                 }
             }
         }
@@ -200,15 +247,12 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
     }
 }
 
-template <typename S, typename T, int NC, int VPT, int CB>
-__device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
-                                             const Vel<T, VPT>& V) {
-    const long long Nv = a.vg.Nv;
-    CellMeta<T, NC> m[CB];
-#pragma unroll
-    for (int b = 0; b < CB; ++b)
-        if (kon[b]) load_meta<T, NC>(a, kk[b], m[b]);
-    // ---- gather
+// Gather, update and store CB cells of one hyperplane (cells with kon false
+// are skipped).
+template <typename S, typename T, int NC, int VPT, int CB, bool INTERIOR>
+__device__ __forceinline__ void update_cells_k(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
+                                               const Vel<T, VPT>& V, const CellMeta<T, NC>* m) {
+    const int Nv = (int)a.vg.Nv;
     T fc[CB][VPT];
     T lo[CB][NC][VPT], hi[CB][NC][VPT], lo2[CB][NC][VPT], hi2[CB][NC][VPT];
 #pragma unroll
@@ -216,27 +260,26 @@ __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__
         if (!kon[b]) continue;
         const S* fk = f + (long long)kk[b] * Nv;
 #pragma unroll
-        for (int u = 0; u < VPT; ++u) fc[b][u] = V.on[u] ? ldT<T, S>(fk + V.v[u]) : T(0);
+        for (int u = 0; u < VPT; ++u) fc[b][u] = ldT<T, S>(fk + V.v[u]);
 #pragma unroll
         for (int d = 0; d < NC; ++d) {
-            const bool dl = m[b].kd[2 * d] == SK_DVM, dh = m[b].kd[2 * d + 1] == SK_DVM;
-            const bool dl2 = dl && m[b].n2[2 * d] >= 0, dh2 = dh && m[b].n2[2 * d + 1] >= 0;
+            const bool dl = INTERIOR || side_kind(m[b].kinds, 2 * d) == SK_DVM;
+            const bool dh = INTERIOR || side_kind(m[b].kinds, 2 * d + 1) == SK_DVM;
             const S* pl = f + (long long)m[b].rf[2 * d] * Nv;
             const S* ph = f + (long long)m[b].rf[2 * d + 1] * Nv;
             const S* pl2 = f + (long long)m[b].n2[2 * d] * Nv;
             const S* ph2 = f + (long long)m[b].n2[2 * d + 1] * Nv;
 #pragma unroll
             for (int u = 0; u < VPT; ++u) {
-                const bool on = V.on[u];
-                lo[b][d][u] = (dl && on) ? ldT<T, S>(pl + V.v[u]) : fc[b][u];
-                hi[b][d][u] = (dh && on) ? ldT<T, S>(ph + V.v[u]) : fc[b][u];
-                lo2[b][d][u] = (dl2 && on) ? ldT<T, S>(pl2 + V.v[u]) : lo[b][d][u];
-                hi2[b][d][u] = (dh2 && on) ? ldT<T, S>(ph2 + V.v[u]) : hi[b][d][u];
+                lo[b][d][u] = dl ? ldT<T, S>(pl + V.v[u]) : fc[b][u];
+                hi[b][d][u] = dh ? ldT<T, S>(ph + V.v[u]) : fc[b][u];
+                lo2[b][d][u] = dl ? ldT<T, S>(pl2 + V.v[u]) : lo[b][d][u];
+                hi2[b][d][u] = dh ? ldT<T, S>(ph2 + V.v[u]) : hi[b][d][u];
             }
         }
     }
     T fo[CB][VPT];
-    compute_cells<T, NC, VPT, CB>(a, kk, kon, V, m, fc, lo, hi, lo2, hi2, fo);
+    compute_cells<T, NC, VPT, CB, INTERIOR>(a, kk, kon, V, m, fc, lo, hi, lo2, hi2, fo);
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
         if (!kon[b]) continue;
@@ -247,17 +290,35 @@ __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__
     }
 }
 
+template <typename S, typename T, int NC, int VPT, int CB>
+__device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
+                                             const Vel<T, VPT>& V) {
+    CellMeta<T, NC> m[CB];
+    bool interior = true;
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+        if (kon[b]) {
+            load_meta<T, NC>(a, kk[b], m[b]);
+            interior = interior && m[b].kinds < 0;
+        }
+    if (interior)
+        update_cells_k<S, T, NC, VPT, CB, true>(a, f, kk, kon, V, m);
+    else
+        update_cells_k<S, T, NC, VPT, CB, false>(a, f, kk, kon, V, m);
+}
+
 // Velocities vbase + 32 u + lane (u < VPT) of the grid: flat index, axis
 // indices and node values.
 template <typename T, int VPT>
 __device__ __forceinline__ void make_vel(const VGridDev& vg, long long vbase, int lane, Vel<T, VPT>& V) {
 #pragma unroll
     for (int u = 0; u < VPT; ++u) {
-        V.v[u] = vbase + 32 * u + lane;
-        V.on[u] = V.v[u] < vg.Nv;
-        int ix = 0, iy = 0, iz = 0;
-        if (V.on[u]) vsplit(V.v[u], vg.nx, vg.ny, ix, iy, iz);
-        V.ix[u] = ix; V.iy[u] = iy; V.iz[u] = iz; V.q[u] = iy + vg.ny * iz;
+        const long long v = vbase + 32 * u + lane;
+        V.on[u] = v < vg.Nv;
+        V.v[u] = (int)(V.on[u] ? v : vg.Nv - 1);
+        int ix, iy, iz;
+        vsplit(V.v[u], vg.nx, vg.ny, ix, iy, iz);
+        V.ix[u] = ix; V.q[u] = iy + vg.ny * iz;
         V.x0[u] = (T)vg.xi[ix];
         V.x1[u] = (T)vg.xi[vg.nx + iy];
         V.x2[u] = (T)vg.xi[vg.nx + vg.ny + iz];

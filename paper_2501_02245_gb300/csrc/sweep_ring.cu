@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(32 * NW) k_sweep_ring(SweepArgs a, S* __restri
             };
 #pragma unroll
             for (int d = 0; d < NC; ++d) {
-                const bool dl = m[0].kd[2 * d] == SK_DVM, dh_ = m[0].kd[2 * d + 1] == SK_DVM;
-                const bool dl2 = dl && m[0].n2[2 * d] >= 0, dh2 = dh_ && m[0].n2[2 * d + 1] >= 0;
+                const bool dl = side_kind(m[0].kinds, 2 * d) == SK_DVM, dh_ = side_kind(m[0].kinds, 2 * d + 1) == SK_DVM;
+                const bool dl2 = dl, dh2 = dh_;   // (a missing second neighbour repeats the neighbour's row)
                 const S* sl = dl ? row_of(m[0].rf[2 * d], -1) : nullptr;
                 const S* sh = dh_ ? row_of(m[0].rf[2 * d + 1], 1) : nullptr;
                 const S* sl2 = dl2 ? row_of(m[0].n2[2 * d], -2) : nullptr;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(32 * NW) k_sweep_ring(SweepArgs a, S* __restri
             const int kk[1] = {k};
             const bool kon[1] = {true};
             T fo[1][VPT];
-            compute_cells<T, NC, VPT, 1>(a, kk, kon, V, m, fc, lo, hi, lo2, hi2, fo);
+            compute_cells<T, NC, VPT, 1, false>(a, kk, kon, V, m, fc, lo, hi, lo2, hi2, fo);
             S* orow = const_cast<S*>(own);
             S* grow = f + (long long)k * Nv + v0;
 #pragma unroll
