@@ -41,32 +41,49 @@ __device__ __forceinline__ T minmod_t(T a, T b) {
     return a * b > T(0) ? m : T(0);
 }
 
-// minmod(a, b) and x > 0 with the decisions taken on the bit patterns: for
-// FP64 this keeps the comparisons and the sign product off the FP64 pipe
-// (GB300 issues FP64 at 1/64 of the FP32 rate), with the same result as
-// minmod_t for finite values (magnitudes of IEEE doubles order like their
-// bit patterns with the sign bit cleared; +-0 never shares a sign).
-template <typename T> __device__ __forceinline__ T mm_t(T a, T b);
-template <> __device__ __forceinline__ float mm_t<float>(float a, float b) { return minmod_t<float>(a, b); }
-template <> __device__ __forceinline__ double mm_t<double>(double a, double b) {
+// Half the minmod, 0.5 minmod(a, b), and x > 0.  FP64: decisions on the bit
+// patterns and the halving as a decrement of the exponent field, all on the
+// integer pipe (GB300 issues FP64 at 1/64 of the FP32 rate).  Magnitudes of
+// IEEE doubles order like their bit patterns with the sign bit cleared, and
+// +-0 never shares a sign, so the result equals 0.5 minmod_t(a, b) for every
+// result of magnitude >= 2^-1021; a smaller one (300 orders of magnitude
+// below any value of the scheme) gives 0.
+template <typename T> __device__ __forceinline__ T hmm_t(T a, T b);
+template <> __device__ __forceinline__ float hmm_t<float>(float a, float b) { return 0.5f * minmod_t<float>(a, b); }
+template <> __device__ __forceinline__ double hmm_t<double>(double a, double b) {
     const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
     const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
-    const bool same = (ia ^ ib) >= 0 && ma != 0 && mb != 0;
-    return same ? (ma < mb ? a : b) : 0.0;
+    const bool a_smaller = ma < mb;
+    const long long m = a_smaller ? ia : ib, mm = a_smaller ? ma : mb;
+    const bool ok = (ia ^ ib) >= 0 && mm >= (2LL << 52);   // same sign, |result| >= 2^-1021 (so nonzero)
+    return ok ? __longlong_as_double(m - (1LL << 52)) : 0.0;
 }
 template <typename T> __device__ __forceinline__ bool pos_t(T x);
 template <> __device__ __forceinline__ bool pos_t<float>(float x) { return x > 0.0f; }
 template <> __device__ __forceinline__ bool pos_t<double>(double x) { return __double_as_longlong(x) > 0; }
 
-// n / d for d > 0 in the normal range.  FP64: one Newton-Raphson step
-// r <- r (2 - d r) on a single-precision reciprocal seed (relative error
-// ~2^-23 -> ~2^-46) and q = n r: relative error below 2e-14, far inside the
-// tolerance of the scheme's FP64 results, for three FP64 operations.  FP32:
-// IEEE division.
+// n / d for d > 0 with d and 1/d within the normal single-precision range
+// (the denominators of the sweep, 1/tau plus outflow terms, are).
+// FP64: a single-precision reciprocal seed, then one Newton-Raphson step
+// r <- r (2 - d r) and q = n r.  The seed moves d into single precision and
+// back on the integer pipe: the sign-less exponent and top 23 fraction bits
+// of d, shifted into place, with the exponent rebias 1023 - 127 = 896 folded
+// into one subtraction (d truncated: relative error < 2^-23), and the
+// approximate hardware reciprocal (rcp.approx.ftz.f32, within 1 ulp).  The
+// seed's relative error is below 2^-21.9, after the Newton step below
+// 2^-43.8 plus rounding: under 1e-13, far inside the tolerance of the
+// scheme's FP64 results, for three FP64 operations and none of the
+// double <-> float conversions (which occupy the FP64 pipe).
+// FP32: the fast single-precision quotient (__fdividef, within 2 ulp).
 template <typename T> __device__ __forceinline__ T div_t(T n, T d);
-template <> __device__ __forceinline__ float div_t<float>(float n, float d) { return n / d; }
+template <> __device__ __forceinline__ float div_t<float>(float n, float d) { return __fdividef(n, d); }
 template <> __device__ __forceinline__ double div_t<double>(double n, double d) {
-    double r = (double)__frcp_rn(__double2float_rn(d));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned fb = (unsigned)(b >> 29) - 0xC0000000u;   // (exponent - 896) << 23 | top 23 fraction bits
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+    const unsigned long long rb = ((unsigned long long)__float_as_uint(rf) << 29) + (896ULL << 52);
+    double r = __longlong_as_double((long long)rb);
     r = r * fma(-d, r, 2.0);
     return n * r;
 }
@@ -209,14 +226,14 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
                 const T dl = c0 - vl, dh = vh - c0;
                 // half the cell's own limited slope (outgoing face values c0 -+ hown);
                 // zero next to a side that is not a DVM side (its value repeats c0)
-                const T hown = T(0.5) * mm_t<T>(dl, dh);
+                const T hown = hmm_t<T>(dl, dh);
                 if (kl != SK_NONE) {
                     T xn = V.x0[u] * m[b].S[2 * d][0];
                     if constexpr (NC >= 2) xn = fma(V.x1[u], m[b].S[2 * d][NC >= 2 ? 1 : 0], xn);
                     if constexpr (NC >= 3) xn = fma(V.x2[u], m[b].S[2 * d][NC >= 3 ? 2 : 0], xn);
                     T fin;
                     if (kl == SK_DVM) {   // neighbour's face value: its value plus half its limited slope
-                        fin = fma(T(0.5), mm_t<T>(vl - lo2[b][d][u], dl), vl);
+                        fin = vl + hmm_t<T>(vl - lo2[b][d][u], dl);
                     } else {
                         const int iz = V.q[u] / ny;
                         fin = scl * eval_recT<T>(bsl, btl, NT, nx, ny, V.ix[u], V.q[u] - ny * iz, iz);
@@ -231,7 +248,7 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
                     if constexpr (NC >= 3) xn = fma(V.x2[u], m[b].S[2 * d + 1][NC >= 3 ? 2 : 0], xn);
                     T fin;
                     if (kh == SK_DVM) {
-                        fin = fma(T(-0.5), mm_t<T>(dh, hi2[b][d][u] - vh), vh);
+                        fin = vh - hmm_t<T>(dh, hi2[b][d][u] - vh);
                     } else {
                         const int iz = V.q[u] / ny;
                         fin = sch * eval_recT<T>(bsh, bth, NT, nx, ny, V.ix[u], V.q[u] - ny * iz, iz);
