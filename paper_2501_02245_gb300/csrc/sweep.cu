@@ -143,6 +143,7 @@ static void launch_sweep_shape(gsis_ctx* c, const SweepArgs& a, int pass, int sh
 SweepArgs sweep_args(gsis_ctx* c) {
     SweepArgs a;
     a.H = c->m.H;
+    a.nc = c->normal_components;
     a.hp_off = c->hp_off;
     a.sdi = c->sd_int;
     a.sdv = c->sd_val;

@@ -20,6 +20,7 @@ namespace gsis {
 // (SD_INTS = 16, SD_VALS = 24: gsis_internal.h.)
 struct SweepArgs {
     int H;
+    int nc;               // index directions of the mesh that carry flux (the all-DVM bit refers to these)
     const int* hp_off;
     const int* sdi;       // [Nd][SD_INTS]
     const void* sdv;      // [Nd][SD_VALS], double (FP64 sweep) or float
@@ -311,7 +312,10 @@ template <typename S, typename T, int NC, int VPT, int CB>
 __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
                                              const Vel<T, VPT>& V) {
     CellMeta<T, NC> m[CB];
-    bool interior = true;
+    // the branch-free update needs every one of the kernel's NC directions to
+    // be a flux direction of the mesh (a batch runs lower-dimensional solves
+    // in a 3-direction kernel: those take the general update)
+    bool interior = a.nc == NC;
 #pragma unroll
     for (int b = 0; b < CB; ++b)
         if (kon[b]) {

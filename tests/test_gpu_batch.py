@@ -79,3 +79,27 @@ def test_batch_rerecords_after_a_solo_iteration():
     assert w_rel_err(batch[0].W(), ref.W()) <= 4 * UNIT[cases[0][1]]
     for s in batch + [ref]:
         s.close()
+
+
+def test_batch_of_mixed_dimensions_matches_single_solves():
+    """A batch with a 2D member runs every member in the 3-direction sweep
+    kernel: the 1D shock and the 2D O-grid (walls, ghost sides, periodic seam)
+    must still match the same solves iterated alone."""
+    from paper_2501_02245_gb300 import Solver, iterate_batch
+    from workloads import cylinder_case
+    cyl = cylinder_case(Ma=2.0, Kn=0.1, n_r=8, n_theta=12, nv=(12, 10, 6), adaptive=False, macro_steps=10,
+                        cfl=5.0, k_sub=2, vbox=((-10, 10), (-9, 9), (-8, 8)), presolve_max_blocks=2)
+    cyl.dt = 0.5
+    shock = shock_1d_case(Ma=1.8, n_cells=21, half_width=5.0, nv=(16, 8, 8), vmax=9.0, macro_steps=20)
+    cases = [(shock, "f64"), (cyl, "f64"), (shock, "f32")]
+    n_iter = 2
+    batch = [Solver.from_case(c, vdf_dtype=dt) for c, dt in cases]
+    iterate_batch(batch, n_iter)
+    for (case, dt), sb in zip(cases, batch):
+        single = Solver.from_case(case, vdf_dtype=dt)
+        single.iterate(n_iter)
+        e = w_rel_err(sb.W(), single.W())
+        single.close()
+        assert e <= 4 * UNIT[dt], "%s %s batch vs single: %.3e" % (case.name, dt, e)
+    for s in batch:
+        s.close()
