@@ -3,6 +3,7 @@
 // block, per-thread velocity data, per-cell metadata and the update of CB
 // cells x VPT velocities of one hyperplane.
 #pragma once
+#include <type_traits>
 #include "gsis_device.cuh"
 
 namespace gsis {
@@ -58,6 +59,14 @@ template <> __device__ __forceinline__ double hmm_t<double>(double a, double b) 
     const long long m = a_smaller ? ia : ib, mm = a_smaller ? ma : mb;
     const bool ok = (ia ^ ib) >= 0 && mm >= (2LL << 52);   // same sign, |result| >= 2^-1021 (so nonzero)
     return ok ? __longlong_as_double(m - (1LL << 52)) : 0.0;
+}
+// -x if s else x (FP64: a flip of the sign bit on the integer pipe).
+template <typename T> __device__ __forceinline__ T neg_if(T x, bool s);
+template <> __device__ __forceinline__ float neg_if<float>(float x, bool s) {
+    return __uint_as_float(__float_as_uint(x) ^ ((unsigned)s << 31));
+}
+template <> __device__ __forceinline__ double neg_if<double>(double x, bool s) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
 }
 template <typename T> __device__ __forceinline__ bool pos_t(T x);
 template <> __device__ __forceinline__ bool pos_t<float>(float x) { return x > 0.0f; }
@@ -228,6 +237,44 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
                 // half the cell's own limited slope (outgoing face values c0 -+ hown);
                 // zero next to a side that is not a DVM side (its value repeats c0)
                 const T hown = hmm_t<T>(dl, dh);
+                if constexpr (INTERIOR && std::is_same<T, double>::value) {
+                    // (FP64 arithmetic, where the FP64 pipe bounds the sweep; in FP32
+                    // the votes and selects cost more issue slots than they save.)
+                    // Both sides are DVM sides.  Usually one face of the pair is an
+                    // inflow face and the other an outflow face (the radial faces of
+                    // an O-grid cell always are): then only the inflow side's MUSCL
+                    // face value is needed, formed once from operands selected by
+                    // the outflow test of the low side.  Lanes whose two faces are
+                    // both inflow (one more face value) or both outflow (one more
+                    // outflow term) are fixed up under warp-uniform branches.  Every
+                    // case takes the operations and summation order of the general
+                    // update below, so the results are the same.
+                    T xL = V.x0[u] * m[b].S[2 * d][0];
+                    if constexpr (NC >= 2) xL = fma(V.x1[u], m[b].S[2 * d][NC >= 2 ? 1 : 0], xL);
+                    if constexpr (NC >= 3) xL = fma(V.x2[u], m[b].S[2 * d][NC >= 3 ? 2 : 0], xL);
+                    T xH = V.x0[u] * m[b].S[2 * d + 1][0];
+                    if constexpr (NC >= 2) xH = fma(V.x1[u], m[b].S[2 * d + 1][NC >= 2 ? 1 : 0], xH);
+                    if constexpr (NC >= 3) xH = fma(V.x2[u], m[b].S[2 * d + 1][NC >= 3 ? 2 : 0], xH);
+                    const bool oL = pos_t<T>(xL), oH = pos_t<T>(xH);
+                    // face value of the low side (vl + h, low side inflow) or of the
+                    // high side (vh - h, low side outflow)
+                    const T e = oL ? hi2[b][d][u] - vh : vl - lo2[b][d][u];
+                    const T h = hmm_t<T>(e, oL ? dh : dl);
+                    const T fin = (oL ? vh : vl) + neg_if<T>(h, oL);
+                    T selH = oH ? hown : fin;
+                    const bool both_in = !oL && !oH, both_out = oL && oH;
+                    if (__any_sync(0xffffffffu, both_in)) {
+                        const T fH = vh - hmm_t<T>(dh, hi2[b][d][u] - vh);
+                        if (both_in) selH = fH;
+                    }
+                    den[u] += oL ? xL : (oH ? xH : T(0));
+                    num[u] = fma(-xL, oL ? -hown : fin, num[u]);
+                    if (__any_sync(0xffffffffu, both_out)) {
+                        if (both_out) den[u] += xH;
+                    }
+                    num[u] = fma(-xH, selH, num[u]);
+                    continue;
+                }
                 if (kl != SK_NONE) {
                     T xn = V.x0[u] * m[b].S[2 * d][0];
                     if constexpr (NC >= 2) xn = fma(V.x1[u], m[b].S[2 * d][NC >= 2 ? 1 : 0], xn);
