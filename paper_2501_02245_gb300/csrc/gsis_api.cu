@@ -188,7 +188,7 @@ gsis_status start(gsis_ctx* c) {
         cudaStreamSynchronize(c->stream);
     }
     if (build_region(c) < 0) return c->broken ? GSIS_ERR_CUDA : GSIS_ERR_OOM;
-    launch_moments(c, c->W, 0, c->mom);
+    launch_moments(c, c->W, c->mom);
     if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "start")) return GSIS_ERR_CUDA;
     c->started = true;
     return GSIS_OK;
@@ -210,7 +210,8 @@ void stage_cell_eq(gsis_ctx* c) {
 // 3. moments of f^{n+1/2} -> W^{n+1/2}, wall fluxes, HoT; set up the synthetic solve
 void stage_moments(gsis_ctx* c) {
     const int N = c->m.N;
-    launch_moments(c, c->W, 0, c->momh);
+    cudaMemcpyAsync(c->Wmom, c->W, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    launch_moments(c, c->Wmom, c->momh);
     launch_wall_flux(c);
     launch_half_state(c);
     launch_nsf(c, c->Wh, c->nsf);   // leaves the gradients of W^{n+1/2} in gu, gT
@@ -238,7 +239,7 @@ void stage_residual(gsis_ctx* c, bool fixed_buffers) {
 // 5. Eq. updatef in DVM cells, and moments of f^{n+1} about u^{n+1}
 void stage_correct(gsis_ctx* c) {
     launch_correction_records(c);
-    launch_moments(c, c->W, 1, c->mom);
+    launch_correct(c);
 }
 
 gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
@@ -247,7 +248,7 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
         phase_begin(c, GSIS_PH_ADAPT);
         launch_kn_gll(c, c->W);
         if (build_region(c) < 0) return c->broken ? GSIS_ERR_CUDA : GSIS_ERR_OOM;
-        launch_moments(c, c->W, 0, c->mom);
+        launch_moments(c, c->W, c->mom);
         phase_end(c, GSIS_PH_ADAPT);
     }
     used[GSIS_PH_CELLEQ] = true;
@@ -775,6 +776,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     const size_t N5 = (size_t)N * 5 * sizeof(double);
     c->W = (double*)dev_alloc(c, N5); c->Wh = (double*)dev_alloc(c, N5); c->Wp = (double*)dev_alloc(c, N5);
     c->Wm = (double*)dev_alloc(c, N5); c->U = (double*)dev_alloc(c, N5); c->Un = (double*)dev_alloc(c, N5);
+    c->Wmom = (double*)dev_alloc(c, N5);
     c->dU = (double*)dev_alloc(c, N5); c->dU2 = (double*)dev_alloc(c, N5); c->R = (double*)dev_alloc(c, N5);
     c->D = (double*)dev_alloc(c, N * sizeof(double));
     c->lamS = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
@@ -812,7 +814,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->specs = (RecSpec*)dev_alloc(c, (size_t)std::max(N, 6) * sizeof(RecSpec));
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
-    if (!c->d_job || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W ||
+    if (!c->d_job || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wmom ||
         !c->Wh || !c->fgeo || !c->bgeo || !c->acell || !c->wallq ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
         !c->lamf || !c->gu || !c->gT ||

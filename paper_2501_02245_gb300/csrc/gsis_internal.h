@@ -128,6 +128,7 @@ struct gsis_ctx {
 
     // macro state
     double *W = nullptr, *Wh = nullptr, *Wp = nullptr, *Wm = nullptr, *U = nullptr, *Un = nullptr;
+    double* Wmom = nullptr;        // [N][5] the state the moments of f^{n+1/2} (momh) were taken about
     double *dU = nullptr, *dU2 = nullptr, *R = nullptr, *D = nullptr, *lamS = nullptr;
     double *Ff = nullptr, *lamf = nullptr;   // interior face fluxes [N][3][5] and lambda|S| [N][3] (high faces)
     double *fgeo = nullptr, *bgeo = nullptr; // face geometry (see MacroArgs)
@@ -209,7 +210,8 @@ int batch_grid(int shape, int nc);
 void launch_sweep_batch(int shape, int nc, const BatchSolve* d_solves, const int2* d_items, int n_items,
                         int* d_ticket, int grid, cudaStream_t st, int pass0, int pass1);
 // moments.cu
-void launch_moments(gsis_ctx* c, const double* Wref, int correct_pass, double* out);
+void launch_moments(gsis_ctx* c, const double* Wref, double* out);
+void launch_correct(gsis_ctx* c);
 void launch_half_state(gsis_ctx* c);
 void launch_hot(gsis_ctx* c);
 void launch_wall_flux(gsis_ctx* c);

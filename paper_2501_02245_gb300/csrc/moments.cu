@@ -13,8 +13,8 @@
 // Row factoring: a thread owns whole x-rows (fixed iy, iz) of the cell's VDF.
 // Per point it accumulates only sum f c_x^k, k = 0..3 (c_x^k from shared
 // memory), and folds the row sums into the 13 moments with the row constants
-// c_y, c_z once per row.  In the correction pass the two corrected
-// Maxwellians are evaluated with their y/z factors hoisted out of the row.
+// c_y, c_z once per row.  The correction pass (k_correct) gets the moments of
+// the corrected VDF without a second reduction (see there).
 //
 // Arithmetic type T: FP64 for an FP64 VDF; for FP32/BF16/FP16 storage the
 // per-row work (row sums over at most nx <= 64 nodes, the correction) is
@@ -26,11 +26,11 @@
 
 namespace gsis {
 
-template <typename S, typename T, bool CORRECT>
+template <typename S, typename T>
 __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__ dvm_cell,
                                                  const double* __restrict__ Wref, const int* __restrict__ side_bc,
-                                                 const double* __restrict__ Sout, S* __restrict__ f, Records recNew,
-                                                 Records recHalf, VGridDev vg, double* __restrict__ mom) {
+                                                 const double* __restrict__ Sout, const S* __restrict__ f, VGridDev vg,
+                                                 double* __restrict__ mom) {
     const int k = blockIdx.x;
     if (k >= Nd) return;
     extern __shared__ double sh_raw[];
@@ -42,56 +42,30 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     T* scx = sh;                 // c_x, c_x^2, c_x^3
     T* scx2 = sh + nx;
     T* scx3 = sh + 2 * nx;
-    T* tN = sh + 3 * nx;         // x-tables E, B, C2, R of M~(W^{n+1})
-    T* tH = sh + 7 * nx;         // x-tables of M~(W^{n+1/2})
-    const T* TN = CORRECT ? RecT<T>::tab(recNew, k, NT) : nullptr;
-    const T* TH = CORRECT ? RecT<T>::tab(recHalf, k, NT) : nullptr;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const double cx = vg.xi[i] - ux;
         scx[i] = (T)cx;
         scx2[i] = (T)(cx * cx);
         scx3[i] = (T)(cx * cx * cx);
-        if (CORRECT) {
-            tN[i] = TN[i]; tN[nx + i] = TN[NT + i]; tN[2 * nx + i] = TN[3 * NT + i]; tN[3 * nx + i] = TN[4 * NT + i];
-            tH[i] = TH[i]; tH[nx + i] = TH[NT + i]; tH[2 * nx + i] = TH[3 * NT + i]; tH[3 * nx + i] = TH[4 * NT + i];
-        }
     }
     __syncthreads();
-    T p0N = T(0), p0H = T(0);
-    if (CORRECT) {
-        p0N = RecT<T>::scal(recNew, k)[RS_P0];
-        p0H = RecT<T>::scal(recHalf, k)[RS_P0];
-    }
     int wall_mask = 0;
     for (int s = 0; s < 6; ++s)
         if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
     double acc[MOMN];
 #pragma unroll
     for (int q = 0; q < MOMN; ++q) acc[q] = 0.0;
-    S* fk = f + (long long)k * vg.Nv;
+    const S* fk = f + (long long)k * vg.Nv;
     const int rows = ny * nz;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
         const int iy = r % ny, iz = r / ny;
         const int jy = nx + iy, jz = nx + ny + iz;
         const double xy = vg.xi[jy], xz = vg.xi[jz];
         const double cy = xy - uy, cz = xz - uz;
-        T eN = T(0), bN = T(0), eH = T(0), bH = T(0);
-        if (CORRECT) {
-            eN = TN[jy] * TN[jz]; bN = TN[NT + jy] + TN[NT + jz];
-            eH = TH[jy] * TH[jz]; bH = TH[NT + jy] + TH[NT + jz];
-        }
-        S* row = fk + (long long)r * nx;
+        const S* row = fk + (long long)r * nx;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         for (int ix = 0; ix < nx; ++ix) {
-            T fv = ldT<T, S>(row + ix);
-            if (CORRECT) {
-                // the correction records are conservation-corrected Maxwellians: their
-                // cubic (r.c) c^2 term is identically zero, so P = p0 + B
-                const T vN = (tN[ix] * eN) * (p0N + (tN[nx + ix] + bN));
-                const T vH = (tH[ix] * eH) * (p0H + (tH[nx + ix] + bH));
-                stT<T, S>(row + ix, fv + (vN - vH));
-                fv = ldT<T, S>(row + ix);   // moments of the stored value
-            }
+            const T fv = ldT<T, S>(row + ix);
             s0 += fv;
             s1 += fv * scx[ix];
             s2 += fv * scx2[ix];
@@ -127,6 +101,206 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     if (threadIdx.x == 0) {
         double* m = mom + (long long)k * MOMN;
         for (int q = 0; q < MOMN; ++q) m[q] = acc[q] * vg.w;
+    }
+}
+
+// 1D sums of one axis table of a record about velocity u, on the lanes of
+// one warp: s[a] = sum_j c^a E_j and s[4 + a] = sum_j c^a E_j B_j, a = 0..3,
+// c = xi_j - u (valid in lane 0).
+__device__ void axis_sums(const double* __restrict__ tab, int NT, const double* __restrict__ xi, int off, int n,
+                          double u, int lane, double* s) {
+    double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = lane; j < n; j += 32) {
+        const double c = xi[off + j] - u, E = tab[off + j], EB = E * tab[NT + off + j];
+        double ca = 1.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            p[a] += ca * E;
+            p[4 + a] += ca * EB;
+            ca *= c;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) p[a] = warp_sum(p[a]);
+    if (lane == 0)
+        for (int a = 0; a < 8; ++a) s[a] = p[a];
+}
+
+// Moment c_x^a c_y^b c_z^c of a record whose value at a node is
+// E_x E_y E_z (p0 + B_x + B_y + B_z), from its axis sums X, Y, Z (axis_sums).
+__device__ __forceinline__ double rec_moment(const double* X, const double* Y, const double* Z, double p0, int a,
+                                             int b, int c) {
+    return (p0 * X[a] + X[4 + a]) * Y[b] * Z[c] + X[a] * (Y[4 + b] * Z[c] + Y[b] * Z[4 + c]);
+}
+
+// The 13 moments (layout of k_moments) of a record about the velocity its
+// axis sums were taken about.
+__device__ void rec_moments13(const double* X, const double* Y, const double* Z, double p0, double* m) {
+    m[0] = rec_moment(X, Y, Z, p0, 0, 0, 0);
+    m[1] = rec_moment(X, Y, Z, p0, 1, 0, 0);
+    m[2] = rec_moment(X, Y, Z, p0, 0, 1, 0);
+    m[3] = rec_moment(X, Y, Z, p0, 0, 0, 1);
+    m[4] = rec_moment(X, Y, Z, p0, 2, 0, 0);
+    m[5] = rec_moment(X, Y, Z, p0, 0, 2, 0);
+    m[6] = rec_moment(X, Y, Z, p0, 0, 0, 2);
+    m[7] = rec_moment(X, Y, Z, p0, 1, 1, 0);
+    m[8] = rec_moment(X, Y, Z, p0, 1, 0, 1);
+    m[9] = rec_moment(X, Y, Z, p0, 0, 1, 1);
+    m[10] = rec_moment(X, Y, Z, p0, 3, 0, 0) + rec_moment(X, Y, Z, p0, 1, 2, 0) + rec_moment(X, Y, Z, p0, 1, 0, 2);
+    m[11] = rec_moment(X, Y, Z, p0, 2, 1, 0) + rec_moment(X, Y, Z, p0, 0, 3, 0) + rec_moment(X, Y, Z, p0, 0, 1, 2);
+    m[12] = rec_moment(X, Y, Z, p0, 2, 0, 1) + rec_moment(X, Y, Z, p0, 0, 2, 1) + rec_moment(X, Y, Z, p0, 0, 0, 3);
+}
+
+// The 13 moments (layout of k_moments) of a distribution taken about u,
+// re-expressed about u + d: with c' = c - d,
+//   m1' = m1 - d m0,  M' = M - d m1^T - m1 d^T + d d^T m0,
+//   Q'_i = Q_i - 2 (M d)_i + |d|^2 m1_i - d_i tr M + 2 d_i (d.m1) - |d|^2 d_i m0.
+__device__ void shift_moments13(const double* m, const double d[3], double* o) {
+    const double m0 = m[0], m1[3] = {m[1], m[2], m[3]};
+    const double M[3][3] = {{m[4], m[7], m[8]}, {m[7], m[5], m[9]}, {m[8], m[9], m[6]}};
+    const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double dm1 = d[0] * m1[0] + d[1] * m1[1] + d[2] * m1[2];
+    const double trM = M[0][0] + M[1][1] + M[2][2];
+    double Mp[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Mp[i][j] = M[i][j] - d[i] * m1[j] - m1[i] * d[j] + d[i] * d[j] * m0;
+    o[0] = m0;
+    for (int i = 0; i < 3; ++i) o[1 + i] = m1[i] - d[i] * m0;
+    o[4] = Mp[0][0]; o[5] = Mp[1][1]; o[6] = Mp[2][2];
+    o[7] = Mp[0][1]; o[8] = Mp[0][2]; o[9] = Mp[1][2];
+    for (int i = 0; i < 3; ++i) {
+        const double Md = M[i][0] * d[0] + M[i][1] * d[1] + M[i][2] * d[2];
+        o[10 + i] = m[10 + i] - 2.0 * Md + dd * m1[i] - d[i] * trM + 2.0 * d[i] * dm1 - dd * d[i] * m0;
+    }
+}
+
+// Eq. updatef in the DVM cells, f^{n+1} = f^{n+1/2} + M~(W^{n+1}) - M~(W^{n+1/2}),
+// and the moments of f^{n+1} about u^{n+1} that the next cell-equilibrium
+// step reads (its heat flux and wall densities), one block per DVM cell.
+//
+// The update is one coalesced pass over the cell's row.  Both records are
+// conservation-corrected Maxwellians, E_x E_y E_z (p0 + B_x + B_y + B_z), so
+// with per-x values (E, E B) and per-(y, z) values e = E_y E_z,
+// p = p0 + B_y + B_z held in shared memory each point costs
+//   a_N = E_x p_N + (E B)_x,  a_H likewise,  f += e_N a_N - e_H a_H
+// (five FP64 operations).  The moments need no second reduction over the
+// velocities: they are the moments of f^{n+1/2} (taken about u^n by the
+// moments pass, momh) moved to u^{n+1}, plus those of the two records, which
+// factor into 1D sums over each axis (six warps, after the pass).  The outgoing half-range wall
+// sums of a wall cell add the correction's, accumulated in the pass.
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__ dvm_cell,
+                                                 const double* __restrict__ Wnew, const double* __restrict__ Wmom,
+                                                 const int* __restrict__ side_bc, const double* __restrict__ Sout,
+                                                 S* __restrict__ f, Records recNew, Records recHalf, VGridDev vg,
+                                                 const double* __restrict__ momh, double* __restrict__ mom) {
+    const int k = blockIdx.x;
+    if (k >= Nd) return;
+    extern __shared__ double sh_raw[];
+    const int nx = vg.nx, ny = vg.ny, nz = vg.nz, NT = vg.NT, nyz = ny * nz;
+    T* xa = reinterpret_cast<T*>(sh_raw);   // [4][nx]: E_N, (E B)_N, E_H, (E B)_H
+    T* rv = xa + 4 * nx;                     // [4][nyz]: e_N, p_N, e_H, p_H
+    __shared__ double axs[2][3][8];
+    __shared__ double red[32 * 6];
+    const int c = dvm_cell[k];
+    const T* TN = RecT<T>::tab(recNew, k, NT);
+    const T* TH = RecT<T>::tab(recHalf, k, NT);
+    const T p0N = RecT<T>::scal(recNew, k)[RS_P0], p0H = RecT<T>::scal(recHalf, k)[RS_P0];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        xa[i] = TN[i];
+        xa[nx + i] = TN[i] * TN[NT + i];
+        xa[2 * nx + i] = TH[i];
+        xa[3 * nx + i] = TH[i] * TH[NT + i];
+    }
+    for (int q = threadIdx.x; q < nyz; q += blockDim.x) {
+        const int jy = nx + q % ny, jz = nx + ny + q / ny;
+        rv[q] = TN[jy] * TN[jz];
+        rv[nyz + q] = p0N + (TN[NT + jy] + TN[NT + jz]);
+        rv[2 * nyz + q] = TH[jy] * TH[jz];
+        rv[3 * nyz + q] = p0H + (TH[NT + jy] + TH[NT + jz]);
+    }
+    const double un[3] = {Wnew[c * 5 + 1], Wnew[c * 5 + 2], Wnew[c * 5 + 3]};
+    int wall_mask = 0;
+    for (int s = 0; s < 6; ++s)
+        if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    S* fk = f + (long long)k * vg.Nv;
+    const int Nv = (int)vg.Nv, step = blockDim.x, sx = step % nx, sq = step / nx;
+    int ix = threadIdx.x % nx, q = threadIdx.x / nx;
+    for (int v = threadIdx.x; v < Nv; v += step) {
+        const T aN = fma(xa[ix], rv[nyz + q], xa[nx + ix]);
+        const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
+        const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
+        stT<T, S>(fk + v, ldT<T, S>(fk + v) + dlt);
+        if (wall_mask) {
+            const int iz = q / ny, iy = q - iz * ny;
+            const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
+            for (int s = 0; s < 6; ++s) {
+                if (!((wall_mask >> s) & 1)) continue;
+                const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+                const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
+                if (xn > 0.0) acc[s] += xn * (double)dlt;
+            }
+        }
+        ix += sx;
+        q += sq;
+        if (ix >= nx) { ix -= nx; ++q; }
+    }
+    {   // axis sums of both FP64 records about u^{n+1}: warp 3 r + d takes record r, axis d
+        const int w = threadIdx.x >> 5;
+        if (w < 6) {
+            const int r = w / 3, d = w % 3;
+            const double* tab = (r == 0 ? recNew.tab : recHalf.tab) + (long long)k * NTAB * NT;
+            const int off = d == 0 ? 0 : (d == 1 ? nx : nx + ny), n = d == 0 ? nx : (d == 1 ? ny : nz);
+            axis_sums(tab, NT, vg.xi, off, n, un[d], threadIdx.x & 31, axs[r][d]);
+        }
+    }
+    if (wall_mask) block_sum<6>(acc, red);   // (its barriers also publish the axis sums)
+    else __syncthreads();
+    if (threadIdx.x == 0) {
+        const double* mh = momh + (long long)k * MOMN;
+        double* m = mom + (long long)k * MOMN;
+        const double d[3] = {un[0] - Wmom[c * 5 + 1], un[1] - Wmom[c * 5 + 2], un[2] - Wmom[c * 5 + 3]};
+        double sh[13], mN[13], mH[13];
+        shift_moments13(mh, d, sh);
+        rec_moments13(axs[0][0], axs[0][1], axs[0][2], recNew.scal[(long long)k * RS + RS_P0], mN);
+        rec_moments13(axs[1][0], axs[1][1], axs[1][2], recHalf.scal[(long long)k * RS + RS_P0], mH);
+        for (int i = 0; i < 13; ++i) m[i] = sh[i] + vg.w * (mN[i] - mH[i]);
+        for (int s = 0; s < 6; ++s) m[13 + s] = mh[13 + s] + (((wall_mask >> s) & 1) ? vg.w * acc[s] : 0.0);
+    }
+}
+
+template <typename S, typename T>
+static void correct_t(gsis_ctx* c) {
+    const int Nd = (int)c->Nd;
+    const long long nyz = (long long)c->vg.ny * c->vg.nz;
+    const size_t smem = (size_t)4 * (c->vg.nx + nyz) * sizeof(T);
+    static size_t configured = 0;   // per instantiation: the largest dynamic size set so far
+    if (smem > configured) {
+        if (cudaFuncSetAttribute(k_correct<S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            set_err(c, GSIS_ERR_UNSUPPORTED, "velocity grid too large for the correction pass's tables");
+            c->broken = true;
+            return;
+        }
+        configured = smem;
+    }
+    k_correct<S, T><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, c->W, c->Wmom, c->m.side_bc, c->m.Sout,
+                                                   (S*)c->f, c->recNew, c->recHalf, c->vg, c->momh, c->mom);
+    c->launches++;
+}
+
+// Eq. updatef on the DVM cells and the moments of f^{n+1} about u^{n+1}
+// (records recNew / recHalf; momh holds the moments of f^{n+1/2} about Wmom).
+void launch_correct(gsis_ctx* c) {
+    if (c->Nd == 0) return;
+    switch (c->p.vdf_dtype) {
+        case GSIS_F64: correct_t<double, double>(c); break;
+        case GSIS_F32: correct_t<float, float>(c); break;
+        case GSIS_BF16: correct_t<__nv_bfloat16, float>(c); break;
+        default: correct_t<__half, float>(c); break;
     }
 }
 
@@ -205,28 +379,22 @@ void launch_wall_rho(gsis_ctx* c) {
 }
 
 template <typename S, typename T>
-static void moments_t(gsis_ctx* c, const double* Wref, bool correct, double* out) {
+static void moments_t(gsis_ctx* c, const double* Wref, double* out) {
     const int Nd = (int)c->Nd;
-    const size_t smem = (size_t)(correct ? 11 : 3) * c->vg.nx * sizeof(T);
-    if (correct)
-        k_moments<S, T, true><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout,
-                                                             (S*)c->f, c->recNew, c->recHalf, c->vg, out);
-    else
-        k_moments<S, T, false><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout,
-                                                              (S*)c->f, c->recNew, c->recHalf, c->vg, out);
+    const size_t smem = (size_t)3 * c->vg.nx * sizeof(T);
+    k_moments<S, T><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (const S*)c->f,
+                                                  c->vg, out);
     c->launches++;
 }
 
-// correct_pass = 0: moments of f about Wref into `out`.
-// correct_pass = 1: f += M~(W^{n+1}) - M~(W^{n+1/2}) (records recNew/recHalf),
-//                   then moments of the corrected f about Wref into `out`.
-void launch_moments(gsis_ctx* c, const double* Wref, int correct_pass, double* out) {
+// Moments of f about Wref into `out` ([Nd][MOMN]).
+void launch_moments(gsis_ctx* c, const double* Wref, double* out) {
     if (c->Nd == 0) return;
     switch (c->p.vdf_dtype) {
-        case GSIS_F64: moments_t<double, double>(c, Wref, correct_pass != 0, out); break;
-        case GSIS_F32: moments_t<float, float>(c, Wref, correct_pass != 0, out); break;
-        case GSIS_BF16: moments_t<__nv_bfloat16, float>(c, Wref, correct_pass != 0, out); break;
-        default: moments_t<__half, float>(c, Wref, correct_pass != 0, out); break;
+        case GSIS_F64: moments_t<double, double>(c, Wref, out); break;
+        case GSIS_F32: moments_t<float, float>(c, Wref, out); break;
+        case GSIS_BF16: moments_t<__nv_bfloat16, float>(c, Wref, out); break;
+        default: moments_t<__half, float>(c, Wref, out); break;
     }
 }
 
