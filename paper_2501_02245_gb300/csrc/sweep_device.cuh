@@ -258,7 +258,8 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
                     const bool oL = pos_t<T>(xL), oH = pos_t<T>(xH);
                     // face value of the low side (vl + h, low side inflow) or of the
                     // high side (vh - h, low side outflow)
-                    const T e = oL ? hi2[b][d][u] - vh : vl - lo2[b][d][u];
+                    // (operands selected first: one subtraction, vh2 - vh or vl - vl2)
+                    const T e = (oL ? hi2[b][d][u] : vl) - (oL ? vh : lo2[b][d][u]);
                     const T h = hmm_t<T>(e, oL ? dh : dl);
                     const T fin = (oL ? vh : vl) + neg_if<T>(h, oL);
                     T selH = oH ? hown : fin;
