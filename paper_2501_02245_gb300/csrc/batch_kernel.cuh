@@ -22,11 +22,11 @@
 
 namespace gsis {
 
-template <typename S, typename T, int NC, int VPT, int CB>
-__device__ __forceinline__ void batch_item(const BatchSolve& B, int vtile, int lane, int pass0, int pass1) {
+template <typename S, typename T, int NC, int VPT, int CB, bool FULL>
+__device__ __forceinline__ void batch_item_t(const BatchSolve& B, int vtile, int lane, int pass0, int pass1) {
     const SweepArgs& a = B.a;
-    Vel<T, VPT> V;
-    make_vel<T, VPT>(a.vg, (long long)vtile * (32 * VPT), lane, V);
+    Vel<T, VPT, FULL> V;
+    make_vel(a.vg, (long long)vtile * (32 * VPT), lane, V);
     S* f = (S*)B.f;
     for (int step = pass0; step < pass1; ++step) {   // step 0: backward pass, step 1: forward pass
         const int pass = 1 - step;
@@ -47,6 +47,19 @@ __device__ __forceinline__ void batch_item(const BatchSolve& B, int vtile, int l
             }
         }
     }
+}
+
+template <typename S, typename T, int NC, int VPT, int CB>
+__device__ __forceinline__ void batch_item(const BatchSolve& B, int vtile, int lane, int pass0, int pass1) {
+    // tile inside the grid (warp-uniform); the 3-direction kernel (2D / 3D
+    // members, rare in batches) keeps one variant to bound its compile time
+    if constexpr (NC == 1) {
+        if ((long long)(vtile + 1) * (32 * VPT) <= B.a.vg.Nv) {
+            batch_item_t<S, T, NC, VPT, CB, true>(B, vtile, lane, pass0, pass1);
+            return;
+        }
+    }
+    batch_item_t<S, T, NC, VPT, CB, false>(B, vtile, lane, pass0, pass1);
 }
 
 template <int NC, int VPT, int CB, int WPB>

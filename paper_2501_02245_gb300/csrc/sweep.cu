@@ -36,11 +36,11 @@
 
 namespace gsis {
 
-template <typename S, typename T, int NC, int G, int VPT, int CB>
-__global__ void __launch_bounds__(32 * G) k_sweep(SweepArgs a, S* __restrict__ f, int pass) {
+template <typename S, typename T, int NC, int G, int VPT, int CB, bool FULL>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, S* __restrict__ f, int pass) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    Vel<T, VPT> V;
-    make_vel<T, VPT>(a.vg, (long long)blockIdx.x * (32 * VPT), lane, V);
+    Vel<T, VPT, FULL> V;
+    make_vel(a.vg, (long long)blockIdx.x * (32 * VPT), lane, V);
     for (int hh = 0; hh < a.H; ++hh) {
         const int h = pass ? (a.H - 1 - hh) : hh;
         const int kb = __ldg(a.hp_off + h), ke = __ldg(a.hp_off + h + 1);
@@ -59,6 +59,14 @@ __global__ void __launch_bounds__(32 * G) k_sweep(SweepArgs a, S* __restrict__ f
         }
         if (G > 1) __syncthreads();
     }
+}
+
+template <typename S, typename T, int NC, int G, int VPT, int CB>
+__global__ void __launch_bounds__(32 * G) k_sweep(SweepArgs a, S* __restrict__ f, int pass) {
+    if ((long long)(blockIdx.x + 1) * (32 * VPT) <= a.vg.Nv)   // tile inside the grid (uniform)
+        sweep_tile<S, T, NC, G, VPT, CB, true>(a, f, pass);
+    else
+        sweep_tile<S, T, NC, G, VPT, CB, false>(a, f, pass);
 }
 
 template <typename S, typename T, int G, int VPT, int CB>

@@ -135,13 +135,17 @@ __device__ __forceinline__ T eval_g(const SweepArgs& a, int k, int ix, int q) {
 
 // per-thread velocity data.  In the ragged last tile of the grid the
 // velocities past the end are clamped to the last one: their loads stay in
-// bounds and their results are not stored.
-template <typename T, int VPT>
+// bounds and their results are not stored.  FULL: the tile lies inside the
+// grid, so slot u is velocity v[0] + 32 u (the loads of a row then share one
+// address plus constant offsets) and every result is stored.
+template <typename T, int VPT, bool FULL = false>
 struct Vel {
     int v[VPT];             // flat velocity index (clamped)
     int ix[VPT], q[VPT];    // q = iy + ny iz
     T x0[VPT], x1[VPT], x2[VPT];
     bool on[VPT];
+    __device__ __forceinline__ int idx(int u) const { return FULL ? v[0] + 32 * u : v[u]; }
+    __device__ __forceinline__ bool active(int u) const { return FULL || on[u]; }
 };
 
 // metadata of one DVM cell
@@ -191,9 +195,9 @@ __device__ __forceinline__ void load_meta(const SweepArgs& a, int k, CellMeta<T,
 // direction; a side that is not a DVM side repeats the own value, a missing
 // second neighbour the neighbour's): new values in fo.  INTERIOR: every flux
 // side of every cell is a DVM side (compiled without the side-kind branches).
-template <typename T, int NC, int VPT, int CB, bool INTERIOR>
+template <typename T, int NC, int VPT, int CB, bool INTERIOR, typename VelT>
 __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk, const bool* kon,
-                                              const Vel<T, VPT>& V, const CellMeta<T, NC>* m, const T (*fc)[VPT],
+                                              const VelT& V, const CellMeta<T, NC>* m, const T (*fc)[VPT],
                                               const T (*lo)[NC][VPT], const T (*hi)[NC][VPT],
                                               const T (*lo2)[NC][VPT], const T (*hi2)[NC][VPT], T (*fo)[VPT]) {
     const int NT = a.vg.NT, nx = a.vg.nx, ny = a.vg.ny;
@@ -315,9 +319,9 @@ __device__ __forceinline__ void compute_cells(const SweepArgs& a, const int* kk,
 
 // Gather, update and store CB cells of one hyperplane (cells with kon false
 // are skipped).
-template <typename S, typename T, int NC, int VPT, int CB, bool INTERIOR>
+template <typename S, typename T, int NC, int VPT, int CB, bool INTERIOR, typename VelT>
 __device__ __forceinline__ void update_cells_k(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
-                                               const Vel<T, VPT>& V, const CellMeta<T, NC>* m) {
+                                               const VelT& V, const CellMeta<T, NC>* m) {
     const int Nv = (int)a.vg.Nv;
     T fc[CB][VPT];
     T lo[CB][NC][VPT], hi[CB][NC][VPT], lo2[CB][NC][VPT], hi2[CB][NC][VPT];
@@ -326,7 +330,7 @@ __device__ __forceinline__ void update_cells_k(const SweepArgs& a, S* __restrict
         if (!kon[b]) continue;
         const S* fk = f + (long long)kk[b] * Nv;
 #pragma unroll
-        for (int u = 0; u < VPT; ++u) fc[b][u] = ldT<T, S>(fk + V.v[u]);
+        for (int u = 0; u < VPT; ++u) fc[b][u] = ldT<T, S>(fk + V.idx(u));
 #pragma unroll
         for (int d = 0; d < NC; ++d) {
             const bool dl = INTERIOR || side_kind(m[b].kinds, 2 * d) == SK_DVM;
@@ -337,10 +341,10 @@ __device__ __forceinline__ void update_cells_k(const SweepArgs& a, S* __restrict
             const S* ph2 = f + (long long)m[b].n2[2 * d + 1] * Nv;
 #pragma unroll
             for (int u = 0; u < VPT; ++u) {
-                lo[b][d][u] = dl ? ldT<T, S>(pl + V.v[u]) : fc[b][u];
-                hi[b][d][u] = dh ? ldT<T, S>(ph + V.v[u]) : fc[b][u];
-                lo2[b][d][u] = dl ? ldT<T, S>(pl2 + V.v[u]) : lo[b][d][u];
-                hi2[b][d][u] = dh ? ldT<T, S>(ph2 + V.v[u]) : hi[b][d][u];
+                lo[b][d][u] = dl ? ldT<T, S>(pl + V.idx(u)) : fc[b][u];
+                hi[b][d][u] = dh ? ldT<T, S>(ph + V.idx(u)) : fc[b][u];
+                lo2[b][d][u] = dl ? ldT<T, S>(pl2 + V.idx(u)) : lo[b][d][u];
+                hi2[b][d][u] = dh ? ldT<T, S>(ph2 + V.idx(u)) : hi[b][d][u];
             }
         }
     }
@@ -352,13 +356,13 @@ __device__ __forceinline__ void update_cells_k(const SweepArgs& a, S* __restrict
         S* fk = f + (long long)kk[b] * Nv;
 #pragma unroll
         for (int u = 0; u < VPT; ++u)
-            if (V.on[u]) stT<T, S>(fk + V.v[u], fo[b][u]);
+            if (V.active(u)) stT<T, S>(fk + V.idx(u), fo[b][u]);
     }
 }
 
-template <typename S, typename T, int NC, int VPT, int CB>
+template <typename S, typename T, int NC, int VPT, int CB, typename VelT>
 __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__ f, const int* kk, const bool* kon,
-                                             const Vel<T, VPT>& V) {
+                                             const VelT& V) {
     CellMeta<T, NC> m[CB];
     // the branch-free update needs every one of the kernel's NC directions to
     // be a flux direction of the mesh (a batch runs lower-dimensional solves
@@ -378,12 +382,12 @@ __device__ __forceinline__ void update_cells(const SweepArgs& a, S* __restrict__
 
 // Velocities vbase + 32 u + lane (u < VPT) of the grid: flat index, axis
 // indices and node values.
-template <typename T, int VPT>
-__device__ __forceinline__ void make_vel(const VGridDev& vg, long long vbase, int lane, Vel<T, VPT>& V) {
+template <typename T, int VPT, bool FULL>
+__device__ __forceinline__ void make_vel(const VGridDev& vg, long long vbase, int lane, Vel<T, VPT, FULL>& V) {
 #pragma unroll
     for (int u = 0; u < VPT; ++u) {
         const long long v = vbase + 32 * u + lane;
-        V.on[u] = v < vg.Nv;
+        V.on[u] = FULL || v < vg.Nv;
         V.v[u] = (int)(V.on[u] ? v : vg.Nv - 1);
         int ix, iy, iz;
         vsplit(V.v[u], vg.nx, vg.ny, ix, iy, iz);

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(32 * NW) k_sweep_ring(SweepArgs a, S* __restri
     const int vcount = (int)min((long long)VT, Nv - v0);
     const int chunks = vcount * (int)sizeof(S) / 16;   // 16-byte copies per row
     Vel<T, VPT> V;
-    make_vel<T, VPT>(a.vg, v0, lane, V);
+    make_vel(a.vg, v0, lane, V);
     const int H = a.H;
 
     auto hyp = [&](int t) { return pass ? (H - 1 - t) : t; };
