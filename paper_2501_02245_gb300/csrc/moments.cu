@@ -175,32 +175,30 @@ __device__ void shift_moments13(const double* m, const double d[3], double* o) {
 }
 
 // Eq. updatef in the DVM cells, f^{n+1} = f^{n+1/2} + M~(W^{n+1}) - M~(W^{n+1/2}),
-// and the moments of f^{n+1} about u^{n+1} that the next cell-equilibrium
-// step reads (its heat flux and wall densities), one block per DVM cell.
+// one block per DVM cell, and the outgoing half-range wall sums of f^{n+1}.
 //
 // The update is one coalesced pass over the cell's row.  Both records are
 // conservation-corrected Maxwellians, E_x E_y E_z (p0 + B_x + B_y + B_z), so
 // with per-x values (E, E B) and per-(y, z) values e = E_y E_z,
 // p = p0 + B_y + B_z held in shared memory each point costs
 //   a_N = E_x p_N + (E B)_x,  a_H likewise,  f += e_N a_N - e_H a_H
-// (five FP64 operations).  The moments need no second reduction over the
-// velocities: they are the moments of f^{n+1/2} (taken about u^n by the
-// moments pass, momh) moved to u^{n+1}, plus those of the two records, which
-// factor into 1D sums over each axis (six warps, after the pass).  The outgoing half-range wall
-// sums of a wall cell add the correction's, accumulated in the pass.
+// (five operations).  Each thread loads four points before it stores any (the
+// loads and stores go through the same pointer, so the compiler would not
+// move a load above an earlier store), keeping four loads in flight.  A wall
+// cell adds the correction's outgoing wall sums to those of f^{n+1/2}.
+constexpr int CORR_UNROLL = 4;
+
 template <typename S, typename T>
 __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__ dvm_cell,
-                                                 const double* __restrict__ Wnew, const double* __restrict__ Wmom,
                                                  const int* __restrict__ side_bc, const double* __restrict__ Sout,
                                                  S* __restrict__ f, Records recNew, Records recHalf, VGridDev vg,
                                                  const double* __restrict__ momh, double* __restrict__ mom) {
     const int k = blockIdx.x;
     if (k >= Nd) return;
     extern __shared__ double sh_raw[];
-    const int nx = vg.nx, ny = vg.ny, nz = vg.nz, NT = vg.NT, nyz = ny * nz;
+    const int nx = vg.nx, ny = vg.ny, NT = vg.NT, nyz = ny * vg.nz;
     T* xa = reinterpret_cast<T*>(sh_raw);   // [4][nx]: E_N, (E B)_N, E_H, (E B)_H
     T* rv = xa + 4 * nx;                     // [4][nyz]: e_N, p_N, e_H, p_H
-    __shared__ double axs[2][3][8];
     __shared__ double red[32 * 6];
     const int c = dvm_cell[k];
     const T* TN = RecT<T>::tab(recNew, k, NT);
@@ -219,7 +217,6 @@ __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__
         rv[2 * nyz + q] = TH[jy] * TH[jz];
         rv[3 * nyz + q] = p0H + (TH[NT + jy] + TH[NT + jz]);
     }
-    const double un[3] = {Wnew[c * 5 + 1], Wnew[c * 5 + 2], Wnew[c * 5 + 3]};
     int wall_mask = 0;
     for (int s = 0; s < 6; ++s)
         if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
@@ -228,46 +225,79 @@ __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__
     S* fk = f + (long long)k * vg.Nv;
     const int Nv = (int)vg.Nv, step = blockDim.x, sx = step % nx, sq = step / nx;
     int ix = threadIdx.x % nx, q = threadIdx.x / nx;
-    for (int v = threadIdx.x; v < Nv; v += step) {
-        const T aN = fma(xa[ix], rv[nyz + q], xa[nx + ix]);
-        const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
-        const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
-        stT<T, S>(fk + v, ldT<T, S>(fk + v) + dlt);
-        if (wall_mask) {
-            const int iz = q / ny, iy = q - iz * ny;
-            const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
-            for (int s = 0; s < 6; ++s) {
-                if (!((wall_mask >> s) & 1)) continue;
-                const double* Sw = Sout + ((long long)c * 6 + s) * 3;
-                const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
-                if (xn > 0.0) acc[s] += xn * (double)dlt;
+    for (int v0 = threadIdx.x; v0 < Nv; v0 += CORR_UNROLL * step) {
+        T fv[CORR_UNROLL];
+#pragma unroll
+        for (int j = 0; j < CORR_UNROLL; ++j) {
+            const int v = v0 + j * step;
+            fv[j] = v < Nv ? ldT<T, S>(fk + v) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < CORR_UNROLL; ++j) {
+            const int v = v0 + j * step;
+            if (v < Nv) {
+                const T aN = fma(xa[ix], rv[nyz + q], xa[nx + ix]);
+                const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
+                const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
+                stT<T, S>(fk + v, fv[j] + dlt);
+                if (wall_mask) {
+                    const int iz = q / ny, iy = q - iz * ny;
+                    const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
+                    for (int s = 0; s < 6; ++s) {
+                        if (!((wall_mask >> s) & 1)) continue;
+                        const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+                        const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
+                        if (xn > 0.0) acc[s] += xn * (double)dlt;
+                    }
+                }
             }
-        }
-        ix += sx;
-        q += sq;
-        if (ix >= nx) { ix -= nx; ++q; }
-    }
-    {   // axis sums of both FP64 records about u^{n+1}: warp 3 r + d takes record r, axis d
-        const int w = threadIdx.x >> 5;
-        if (w < 6) {
-            const int r = w / 3, d = w % 3;
-            const double* tab = (r == 0 ? recNew.tab : recHalf.tab) + (long long)k * NTAB * NT;
-            const int off = d == 0 ? 0 : (d == 1 ? nx : nx + ny), n = d == 0 ? nx : (d == 1 ? ny : nz);
-            axis_sums(tab, NT, vg.xi, off, n, un[d], threadIdx.x & 31, axs[r][d]);
+            ix += sx;
+            q += sq;
+            if (ix >= nx) { ix -= nx; ++q; }
         }
     }
-    if (wall_mask) block_sum<6>(acc, red);   // (its barriers also publish the axis sums)
-    else __syncthreads();
+    if (wall_mask) block_sum<6>(acc, red);
     if (threadIdx.x == 0) {
         const double* mh = momh + (long long)k * MOMN;
         double* m = mom + (long long)k * MOMN;
-        const double d[3] = {un[0] - Wmom[c * 5 + 1], un[1] - Wmom[c * 5 + 2], un[2] - Wmom[c * 5 + 3]};
+        for (int s = 0; s < 6; ++s) m[13 + s] = mh[13 + s] + (((wall_mask >> s) & 1) ? vg.w * acc[s] : 0.0);
+    }
+}
+
+// The 13 velocity moments of f^{n+1} about u^{n+1} that the next
+// cell-equilibrium step reads (its heat flux), one block of six warps per
+// DVM cell, with no reduction over the velocities: the moments of f^{n+1/2}
+// (taken about u^n = Wmom by the moments pass, momh) moved to u^{n+1}, plus
+// those of the two corrected Maxwellians of Eq. updatef, which factor into 1D
+// sums over each axis (warp 3 r + d: record r, axis d).
+__global__ void __launch_bounds__(192) k_corr_moments(int Nd, const int* __restrict__ dvm_cell,
+                                                      const double* __restrict__ Wnew,
+                                                      const double* __restrict__ Wmom, Records recNew,
+                                                      Records recHalf, VGridDev vg, const double* __restrict__ momh,
+                                                      double* __restrict__ mom) {
+    const int k = blockIdx.x;
+    if (k >= Nd) return;
+    __shared__ double axs[2][3][8];
+    const int c = dvm_cell[k];
+    const int nx = vg.nx, ny = vg.ny, nz = vg.nz, NT = vg.NT;
+    const int w = threadIdx.x >> 5;
+    if (w < 6) {
+        const int r = w / 3, d = w % 3;
+        const double* tab = (r == 0 ? recNew.tab : recHalf.tab) + (long long)k * NTAB * NT;
+        const int off = d == 0 ? 0 : (d == 1 ? nx : nx + ny), n = d == 0 ? nx : (d == 1 ? ny : nz);
+        axis_sums(tab, NT, vg.xi, off, n, Wnew[c * 5 + 1 + d], threadIdx.x & 31, axs[r][d]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double* mh = momh + (long long)k * MOMN;
+        double* m = mom + (long long)k * MOMN;
+        const double d[3] = {Wnew[c * 5 + 1] - Wmom[c * 5 + 1], Wnew[c * 5 + 2] - Wmom[c * 5 + 2],
+                             Wnew[c * 5 + 3] - Wmom[c * 5 + 3]};
         double sh[13], mN[13], mH[13];
         shift_moments13(mh, d, sh);
         rec_moments13(axs[0][0], axs[0][1], axs[0][2], recNew.scal[(long long)k * RS + RS_P0], mN);
         rec_moments13(axs[1][0], axs[1][1], axs[1][2], recHalf.scal[(long long)k * RS + RS_P0], mH);
         for (int i = 0; i < 13; ++i) m[i] = sh[i] + vg.w * (mN[i] - mH[i]);
-        for (int s = 0; s < 6; ++s) m[13 + s] = mh[13 + s] + (((wall_mask >> s) & 1) ? vg.w * acc[s] : 0.0);
     }
 }
 
@@ -287,9 +317,11 @@ static void correct_t(gsis_ctx* c) {
         }
         configured = smem;
     }
-    k_correct<S, T><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, c->W, c->Wmom, c->m.side_bc, c->m.Sout,
-                                                   (S*)c->f, c->recNew, c->recHalf, c->vg, c->momh, c->mom);
-    c->launches++;
+    k_correct<S, T><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout, (S*)c->f, c->recNew,
+                                                   c->recHalf, c->vg, c->momh, c->mom);
+    k_corr_moments<<<Nd, 192, 0, c->stream>>>(Nd, c->dvm_cell, c->W, c->Wmom, c->recNew, c->recHalf, c->vg, c->momh,
+                                              c->mom);
+    c->launches += 2;
 }
 
 // Eq. updatef on the DVM cells and the moments of f^{n+1} about u^{n+1}
