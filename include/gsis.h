@@ -241,6 +241,23 @@ gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_repo
  * fits in shared memory).  The paper has no counterpart. */
 gsis_status gsis_debug_set_sweep_tile(gsis_ctx* ctx, const char* name);
 
+/* Test hook: velocity moments of the VDF of each DVM cell (Eq. getmoment,
+ * the quadrature of Sec. 3.1), dst [n_dvm][19] doubles in host memory, in
+ * the order of the cell list of gsis_get_vdf; capacity = entries of dst
+ * (>= 19 n_dvm, else GSIS_ERR_ARG).  Per cell, with c = xi - u the peculiar
+ * velocity about the cell's current macroscopic velocity u and w the
+ * quadrature weight: sum w f; sum w c f (3); sum w c_i c_j f for xx, yy, zz,
+ * xy, xz, yz; sum w c_i |c|^2 f (3); then for each of the six sides, on a
+ * diffuse-wall side, the outgoing half-range sum of w (xi.S) f (S the
+ * outward area vector), else 0.
+ * direct = 0: the moments the last GSIS iteration carried forward (taken
+ * without a pass over the velocities after the correction of Eq. updatef);
+ * direct = 1: a fresh reduction over the current VDF.  Both describe the same
+ * VDF, so they agree up to rounding (and, for reduced-precision storage, the
+ * storage rounding of the corrected values).  GSIS_ERR_STATE before the
+ * first iteration.  The paper has no counterpart. */
+gsis_status gsis_debug_vdf_moments(gsis_ctx* ctx, int direct, double* dst, long long capacity);
+
 /* Human-readable result of the sweep's tile-shape autotuning for this
  * context (chosen shape and the timing of every candidate), or "" before the
  * first iteration.  Each context times the candidate shapes of its kinetic

@@ -1130,6 +1130,23 @@ gsis_status gsis_debug_set_sweep_tile(gsis_ctx* c, const char* name) {
     return force_sweep_shape(c, name);
 }
 
+gsis_status gsis_debug_vdf_moments(gsis_ctx* c, int direct, double* dst, long long capacity) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!dst) return set_err(c, GSIS_ERR_ARG, "NULL destination");
+    if (!c->started || c->iteration == 0) return set_err(c, GSIS_ERR_STATE, "no GSIS iteration yet");
+    if (capacity < c->Nd * MOMN) return set_err(c, GSIS_ERR_ARG, "destination too small");
+    if (c->Nd == 0) return GSIS_OK;
+    // (momh is free between iterations: the next moments pass rewrites it before any use)
+    if (direct) launch_moments(c, c->W, c->momh);
+    if (!cuda_ok(c, cudaMemcpyAsync(dst, direct ? c->momh : c->mom, (size_t)c->Nd * MOMN * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream),
+                 "moment copy") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "moment copy"))
+        return GSIS_ERR_CUDA;
+    return GSIS_OK;
+}
+
 const char* gsis_tuning_info(gsis_ctx* c) {
     if (!c) return "";
     return c->sweep_info.c_str();

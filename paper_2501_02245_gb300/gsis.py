@@ -25,7 +25,7 @@ PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual"
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
             "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
-            "gsis_debug_set_sweep_tile"]
+            "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments"]
 
 
 class GsisError(RuntimeError):
@@ -101,6 +101,8 @@ def load():
     lib.gsis_batch_info.restype = ctypes.c_char_p
     lib.gsis_debug_set_sweep_tile.argtypes = [vp, ctypes.c_char_p]
     lib.gsis_debug_set_sweep_tile.restype = c_int
+    lib.gsis_debug_vdf_moments.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_longlong]
+    lib.gsis_debug_vdf_moments.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
     lib.gsis_tuning_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
@@ -256,6 +258,14 @@ class Solver:
     def set_sweep_tile(self, name):
         """Force the kinetic sweep's tile shape (test hook)."""
         self._check(self.lib.gsis_debug_set_sweep_tile(self.ctx, name.encode()))
+
+    def vdf_moments(self, n_dvm, direct):
+        """Per-DVM-cell velocity moments of the VDF, [n_dvm, 19] (test hook):
+        the ones the last iteration carried forward (direct=False) or a fresh
+        reduction over the current VDF (direct=True)."""
+        out = np.zeros((n_dvm, 19))
+        self._check(self.lib.gsis_debug_vdf_moments(self.ctx, int(bool(direct)), _dptr(out), out.size))
+        return out
 
     def tuning_info(self):
         """Result of the sweep tile-shape autotuning of this solve."""
