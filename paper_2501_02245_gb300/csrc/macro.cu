@@ -157,14 +157,16 @@ __global__ void k_prim_to_cons(int N, const double* __restrict__ Wp, double* __r
     U[c * 5 + 4] = r * (1.5 * T + 0.5 * (ux * ux + uy * uy + uz * uz));
 }
 
+// (One FP64 division per state, its reciprocal reused: on GB300 a division
+// costs about ten FP64-pipe operations.)
 __device__ __forceinline__ void cons_to_prim(const double* U, double* Wp) {
-    const double r = U[0];
-    const double ux = U[1] / r, uy = U[2] / r, uz = U[3] / r;
+    const double r = U[0], ir = 1.0 / r;
+    const double ux = U[1] * ir, uy = U[2] * ir, uz = U[3] * ir;
     Wp[0] = r;
     Wp[1] = ux;
     Wp[2] = uy;
     Wp[3] = uz;
-    Wp[4] = (2.0 * U[4] / r - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    Wp[4] = (2.0 * U[4] * ir - (ux * ux + uy * uy + uz * uz)) * (1.0 / 3.0);
 }
 
 __global__ void k_cons_to_prim(int N, const double* __restrict__ U, double* __restrict__ Wp) {
@@ -273,8 +275,8 @@ __device__ void kfvs(double rL, const double* uL, double pL, double rR, const do
 }
 
 __device__ __forceinline__ void euler_flux_dot(const double* U, const double* S, double* F) {
-    const double r = U[0];
-    const double ux = U[1] / r, uy = U[2] / r, uz = U[3] / r;
+    const double r = U[0], ir = 1.0 / r;
+    const double ux = U[1] * ir, uy = U[2] * ir, uz = U[3] * ir;
     const double p = (GAMMA - 1.0) * (U[4] - 0.5 * r * (ux * ux + uy * uy + uz * uz));
     const double uS = ux * S[0] + uy * S[1] + uz * S[2];
     F[0] = r * uS;
@@ -340,18 +342,18 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     const double Tf = 0.5 * (wL[4] + wR[4]);
     const double muf = viscosity(Tf, a.mu0, a.omega);
     const double e[3] = {G[4], G[5], G[6]};
-    const double dist = G[7];
+    const double dist = G[7], idist = 1.0 / dist;
     double guf[9], gTf[3];
     for (int j = 0; j < 3; ++j) {
         double gav[3];
         for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gu[(long long)L * 9 + j * 3 + i] + gu[(long long)Rr * 9 + j * 3 + i]);
-        const double corr = (wR[1 + j] - wL[1 + j]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
+        const double corr = (wR[1 + j] - wL[1 + j]) * idist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
         for (int i = 0; i < 3; ++i) guf[j * 3 + i] = gav[i] + corr * e[i];
     }
     {
         double gav[3];
         for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gT[(long long)L * 3 + i] + gT[(long long)Rr * 3 + i]);
-        const double corr = (wR[4] - wL[4]) / dist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
+        const double corr = (wR[4] - wL[4]) * idist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
         for (int i = 0; i < 3; ++i) gTf[i] = gav[i] + corr * e[i];
     }
     double sig[6], qf[3];
@@ -545,9 +547,10 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
         Dc += Vdt;
     }
     D[c] = Dc;
+    const double iD = 1.0 / Dc;
     for (int q = 0; q < 5; ++q) {
         R[c * 5 + q] = Rc[q];
-        dU[c * 5 + q] = Rc[q] / Dc;
+        dU[c * 5 + q] = Rc[q] * iD;
     }
 }
 
@@ -577,7 +580,8 @@ __device__ __forceinline__ void relax_one(const MacroArgs& a, const double* U, c
         const double ls = lamS[(long long)c * 6 + s];
         for (int q = 0; q < 5; ++q) off[q] += 0.5 * ((F1[q] - F0[q]) - ls * dUin[n * 5 + q]);
     }
-    for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) / D[c];
+    const double iD = 1.0 / D[c];
+    for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) * iD;
 }
 
 __global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double* __restrict__ R,
