@@ -251,9 +251,11 @@ void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim) {
 __device__ __forceinline__ void half_range_add(double r, const double* u, double T, const double* n, double sign,
                                                double* F) {
     const double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
-    const double st = sqrt(T);
-    const double P = 0.5 * (1.0 + sign * erf(un / (1.4142135623730951 * st)));
-    const double D = sign * st * exp(-0.5 * un * un / T) * 0.3989422804014327;   // 1/sqrt(2 pi)
+    // s = un / sqrt(T) and sqrt(T) = T / sqrt(T) from one reciprocal square root
+    // (instead of a square root and two FP64 divisions)
+    const double ist = rsqrt(T), st = T * ist, s = un * ist;
+    const double P = 0.5 * (1.0 + sign * erf(s * 0.7071067811865476));        // 1/sqrt(2)
+    const double D = sign * st * exp(-0.5 * s * s) * 0.3989422804014327;       // 1/sqrt(2 pi)
     const double M0 = un * P + D;
     const double M1 = (un * un + T) * P + un * D;
     const double M2 = (un * un * un + 3.0 * un * T) * P + (un * un + 2.0 * T) * D;
