@@ -325,8 +325,6 @@ int build_region(gsis_ctx* c) {
     const long long Nd_new = c->h_count[0];
     const long long Nd_old = c->Nd;
     void* f_old = c->f;
-    int* old_dvm_cell = nullptr;
-    (void)old_dvm_cell;
     // the old list is only needed through old_cell2dvm (cell -> old row)
     if (!ensure_dvm_capacity(c, Nd_new)) {
         set_err(c, GSIS_ERR_OOM, "allocation of the DVM lists failed");

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     extern __shared__ double sh_raw[];
     T* sh = reinterpret_cast<T*>(sh_raw);
     __shared__ double red[32 * MOMN];
-    const int nx = vg.nx, ny = vg.ny, nz = vg.nz, NT = vg.NT;
+    const int nx = vg.nx, ny = vg.ny, nz = vg.nz;
     const int c = dvm_cell[k];
     const double ux = Wref[c * 5 + 1], uy = Wref[c * 5 + 2], uz = Wref[c * 5 + 3];
     T* scx = sh;                 // c_x, c_x^2, c_x^3
