@@ -299,15 +299,20 @@ const char* gsis_version(void);
  *         momentum and energy equal those of W[k] exactly (the same rows the
  *         all-kinetic start of gsis_iterate stores as the initial VDF).
  * cuda_stream: cudaStream_t on which the work is queued (NULL = default).
- * Limits: n <= 256 and nx + ny + nz <= 384 per call, else GSIS_ERR_ARG;
- * process more states in several calls.  Other errors: GSIS_ERR_ARG for NULL
- * pointers or an invalid grid, GSIS_ERR_CUDA when a CUDA call fails.
+ * Limits: n <= 256 and nx + ny + nz <= 384 per call (each of nx, ny, nz
+ * checked before they are summed), else GSIS_ERR_ARG; process more states in
+ * several calls.  Other errors: GSIS_ERR_ARG for NULL pointers or an invalid
+ * grid; GSIS_ERR_CUDA when a CUDA call fails, or on entry when an error of
+ * earlier asynchronous work is already pending on the calling thread (that
+ * error is left pending for its owner and nothing is queued).
  * The first call on a device looks up the address of the device array
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents, so calls whose device work overlaps (other streams, other
- * host threads) race on it: order them on one stream.  Asynchronous: returns
- * after queueing the work. */
+ * before any stream capture.  The address is cached for the life of the
+ * process: after a cudaDeviceReset of that device the entry point must not be
+ * called again in the same process.  All calls share the array and it keeps
+ * the last call's contents, so calls whose device work overlaps (other
+ * streams, other host threads) race on it: order them on one stream.
+ * Asynchronous: returns after queueing the work. */
 gsis_status gsis_corrected_maxwellian_noalloc(const double* W, int n, const gsis_vgrid_desc* vgrid,
                                               double* f_out, void* cuda_stream);
 

@@ -8,6 +8,7 @@
 // distribution records live in one file-scope device array of fixed size,
 // sized here once for every GPU that loads the library.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include "gsis_device.cuh"
 
@@ -74,7 +75,10 @@ __global__ void k_noalloc_rows(int n, Records rec, VGridDev vg, double* __restri
     }
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device (looked up once
+// per device and cached for the life of the process; a cudaDeviceReset
+// reloads the module and may move the array, so the cached address is only
+// valid until the device is reset).
 gsis_status scratch_address(void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
@@ -101,14 +105,20 @@ extern "C" gsis_status gsis_corrected_maxwellian_noalloc(const double* W, int n,
                                                          double* f_out, void* cuda_stream) {
     if (!W || !f_out || !vgrid || n < 0) return GSIS_ERR_ARG;
     if (n > NOALLOC_MAX_STATES) return GSIS_ERR_ARG;
-    long long Nv = 1;
+    // each axis is bounded before the node count is summed, so the sum cannot overflow
+    long long Nv = 1, NTl = 0;
     for (int d = 0; d < 3; ++d) {
-        if (vgrid->n[d] < 1 || !(vgrid->hi[d] > vgrid->lo[d])) return GSIS_ERR_ARG;
+        if (vgrid->n[d] < 1 || vgrid->n[d] > NOALLOC_MAX_NODES) return GSIS_ERR_ARG;
+        if (!(vgrid->hi[d] > vgrid->lo[d]) || !std::isfinite(vgrid->lo[d]) || !std::isfinite(vgrid->hi[d]))
+            return GSIS_ERR_ARG;
         Nv *= vgrid->n[d];
+        NTl += vgrid->n[d];
     }
-    const int NT = vgrid->n[0] + vgrid->n[1] + vgrid->n[2];
-    if (NT > NOALLOC_MAX_NODES) return GSIS_ERR_ARG;
+    if (NTl > NOALLOC_MAX_NODES) return GSIS_ERR_ARG;
+    const int NT = (int)NTl;
     if (n == 0) return GSIS_OK;
+    // an error left by the caller's earlier asynchronous work is not this call's: leave it pending
+    if (cudaPeekAtLastError() != cudaSuccess) return GSIS_ERR_CUDA;
     void* base = nullptr;
     gsis_status st = scratch_address(&base);
     if (st != GSIS_OK) return st;
@@ -134,11 +144,15 @@ extern "C" gsis_status gsis_corrected_maxwellian_noalloc(const double* W, int n,
     vg.w = w;
     vg.xi = xi;
     // Every scratch entry read below is written first in this call (nodes,
-    // specs, record scalars and tables), so nothing needs clearing.
+    // specs, record scalars and tables), so nothing needs clearing.  Each
+    // launch is checked before the next one is queued.
     k_noalloc_nodes<<<(NT + 127) / 128, 128, 0, s>>>(vg.nx, vg.ny, vg.nz, vgrid->lo[0], vgrid->lo[1], vgrid->lo[2],
                                                      h[0], h[1], h[2], xi);
+    if (cudaGetLastError() != cudaSuccess) return GSIS_ERR_CUDA;
     k_noalloc_specs<<<(n + 127) / 128, 128, 0, s>>>(n, W, specs);
+    if (cudaGetLastError() != cudaSuccess) return GSIS_ERR_CUDA;
     build_records_raw(specs, n, rec, vg, s);
+    if (cudaGetLastError() != cudaSuccess) return GSIS_ERR_CUDA;
     dim3 grid((unsigned)std::min<long long>((Nv + 255) / 256, 64), (unsigned)n);
     k_noalloc_rows<<<grid, 256, 0, s>>>(n, rec, vg, f_out);
     if (cudaGetLastError() != cudaSuccess) return GSIS_ERR_CUDA;

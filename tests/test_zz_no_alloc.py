@@ -79,3 +79,23 @@ def test_noalloc_rejects_sizes_beyond_limits():
     vg.n[1] = 92
     assert lib.gsis_corrected_maxwellian_noalloc(p(W.data_ptr()), 1, ctypes.byref(vg), p(out.data_ptr()),
                                                  None) == gsis.GSIS_ERR_ARG
+    # an axis so large that nx + ny + nz would overflow a 32-bit sum is rejected per axis,
+    # at argument checking, before anything is queued
+    vg.n[0], vg.n[1], vg.n[2] = 2 ** 31 - 1, 1, 1
+    assert lib.gsis_corrected_maxwellian_noalloc(p(W.data_ptr()), 1, ctypes.byref(vg), p(out.data_ptr()),
+                                                 None) == gsis.GSIS_ERR_ARG
+    torch.cuda.synchronize()
+
+
+def test_noalloc_at_the_limits():
+    """256 states and nx + ny + nz = 384 velocity nodes, the largest call the
+    fixed device array is sized for (every record slot and every table entry
+    in use), against the existing entry point."""
+    import torch
+    stream = torch.cuda.current_stream()
+    case = shock_1d_case(Ma=2.5, n_cells=256, half_width=64.0, nv=(368, 8, 8), vmax=9.0)
+    ref = _existing_rows(case)
+    got = _noalloc_rows(case, stream)
+    assert np.all(np.isfinite(got))
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err < TOL, err
