@@ -17,6 +17,7 @@ Step 3 one re-identification after `adapt_every` GSIS iterations.
 import numpy as np
 
 from . import model as M
+from .reduced import ReducedGrid
 from .mesh import Topology, BC_NONE, BC_FARFIELD, BC_WALL
 from .kinetic import KineticInputs, sweep, wall_density, wall_kinetic_flux
 from .macro import (MacroGeometry, primitives, cell_gradients, nsf, macro_solve, boundary_values, lsq_grad,
@@ -54,7 +55,10 @@ class OracleSolver:
         self.case = case
         self.topo = Topology(case.mesh)
         self.geo = MacroGeometry(self.topo)
-        self.vg = M.VelocityGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
+        if getattr(case.vgrid, "reduced", False):   # 2D flow: xi_z integrated out (oracle.reduced)
+            self.vg = ReducedGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
+        else:
+            self.vg = M.VelocityGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
         self.mu0 = M.mu0_from_kn(case.Kn)
         self.omega = case.omega
         self.bc_state = np.array(case.mesh.bc_state, dtype=np.float64)
@@ -125,9 +129,9 @@ class OracleSolver:
         sig, q = self.nsf_field(W)
         for c in cells:
             rho, u, T = W[c, 0], W[c, 1:4], W[c, 4]
-            g13 = M.grad13(rho, u, T, sig[c], q[c], self.vg.xi)
-            Mx = M.maxwellian(rho, u, T, self.vg.xi)
-            self.f[c] = M.conservation_correct(g13, Mx, M.conserved_from_primitive(rho, u, T), self.vg)
+            g13 = self.vg.grad13(rho, u, T, sig[c], q[c])
+            Mx = self.vg.maxwellian(rho, u, T)
+            self.f[c] = self.vg.conservation_correct(g13, Mx, M.conserved_from_primitive(rho, u, T))
 
     def set_region(self, new_flags, W):
         entering = [c for c in range(self.N) if new_flags[c] and not self.dvm[c]]
@@ -164,7 +168,7 @@ class OracleSolver:
             self.dvm[:] = True
             for c in range(self.N):
                 rho, u, T = self.W[c, 0], self.W[c, 1:4], self.W[c, 4]
-                self.f[c] = M.corrected_maxwellian(rho, u, T, self.vg)
+                self.f[c] = self.vg.corrected_maxwellian(rho, u, T)
 
     def kinetic_inputs(self):
         W = self.W
@@ -174,8 +178,8 @@ class OracleSolver:
             if not self.dvm[c]:
                 continue
             rho, u, T = W[c, 0], W[c, 1:4], W[c, 4]
-            q = M.heat_flux_about(self.f[c], u, vg)
-            gt[c] = M.corrected_shakhov(rho, u, T, q, vg)
+            q = vg.heat_flux_about(self.f[c], u)
+            gt[c] = vg.corrected_shakhov(rho, u, T, q)
             tau[c] = M.viscosity(T, self.mu0, self.omega) / (rho * T)
         need = set()
         for c in range(self.N):
@@ -187,15 +191,15 @@ class OracleSolver:
             sig, qn = self.nsf_field(W)
             for c in need:
                 rho, u, T = W[c, 0], W[c, 1:4], W[c, 4]
-                g13 = M.grad13(rho, u, T, sig[c], qn[c], vg.xi)
-                Mx = M.maxwellian(rho, u, T, vg.xi)
-                ghost[c] = M.conservation_correct(g13, Mx, M.conserved_from_primitive(rho, u, T), vg)
+                g13 = vg.grad13(rho, u, T, sig[c], qn[c])
+                Mx = vg.maxwellian(rho, u, T)
+                ghost[c] = vg.conservation_correct(g13, Mx, M.conserved_from_primitive(rho, u, T))
         for s in range(6):
             st = self.bc_state[s]
             if self.case.mesh.bc_type[s] == BC_FARFIELD:
-                ff[s] = M.corrected_maxwellian(st[0], st[1:4], st[4], vg)
+                ff[s] = vg.corrected_maxwellian(st[0], st[1:4], st[4])
             elif self.case.mesh.bc_type[s] == BC_WALL:
-                mw[s] = M.maxwellian(1.0, np.zeros(3), st[4], vg.xi)
+                mw[s] = vg.maxwellian(1.0, np.zeros(3), st[4])
         return KineticInputs(gt, tau, ghost, ff, mw)
 
     def wall_correction(self, W_half, mw):
@@ -235,7 +239,7 @@ class OracleSolver:
         for r, f_i in enumerate(idx):
             c = geo.bC[f_i]
             if self.dvm[c]:
-                Mw = M.maxwellian(1.0, np.zeros(3), self.bc_state[geo.bSide[f_i], 4], self.vg.xi)
+                Mw = self.vg.maxwellian(1.0, np.zeros(3), self.bc_state[geo.bSide[f_i], 4])
                 e = wall_kinetic_flux(self.f[c], geo.bS[f_i], Mw, self.vg)[4]
             else:
                 e = F_nsf[r, 4]
@@ -256,7 +260,7 @@ class OracleSolver:
         sig_k = np.zeros((self.N, 3, 3)); q_k = np.zeros((self.N, 3))
         for c in range(self.N):
             if self.dvm[c]:
-                rho, u, T, sig, q = M.moments(self.f[c], vg)
+                rho, u, T, sig, q = vg.moments(self.f[c])
                 W_half[c] = [rho, u[0], u[1], u[2], T]
                 sig_k[c] = sig; q_k[c] = q
         sig_n, q_n = self.nsf_field(W_half)
@@ -273,8 +277,8 @@ class OracleSolver:
             W_new = W_half + case.relax * (W_new - W_half)
         for c in range(self.N):
             if self.dvm[c]:
-                a = M.corrected_maxwellian(W_new[c, 0], W_new[c, 1:4], W_new[c, 4], vg)
-                b = M.corrected_maxwellian(W_half[c, 0], W_half[c, 1:4], W_half[c, 4], vg)
+                a = vg.corrected_maxwellian(W_new[c, 0], W_new[c, 1:4], W_new[c, 4])
+                b = vg.corrected_maxwellian(W_half[c, 0], W_half[c, 1:4], W_half[c, 4])
                 self.f[c] = self.f[c] + a - b
         eps = residual_eps(W_new, self.W, self.topo.vol)
         self.W = W_new

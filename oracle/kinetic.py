@@ -51,9 +51,13 @@ class KineticInputs:
 
 def wall_density(f_cell, S_out, Mw, vg):
     """Diffuse-wall density: the emitted half-range rho_w M_w carries the mass
-    that the outgoing half of f brings to the face (zero net mass flux)."""
+    that the outgoing half of f brings to the face (zero net mass flux).  On
+    the reduced grid only the G plane carries mass."""
     xn = vg.xi @ S_out
     out = xn > 0
+    if vg.reduced:
+        m = vg.psi[:, 0]
+        return np.sum(np.where(out, xn * f_cell * m, 0.0)) / np.sum(np.where(~out, -xn * Mw * m, 0.0))
     num = np.sum(np.where(out, xn * f_cell, 0.0))
     den = np.sum(np.where(~out, -xn * Mw, 0.0))
     return num / den
@@ -69,6 +73,8 @@ def wall_kinetic_flux(f_cell, S_out, Mw, vg):
     rho_w = wall_density(f_cell, S_out, Mw, vg)
     face = np.where(xn > 0, f_cell, rho_w * Mw)
     g = vg.w * xn * face
+    if vg.reduced:   # per-plane weights of mass, momentum and energy
+        return g @ vg.psi
     return np.array([np.sum(g), g @ xi[:, 0], g @ xi[:, 1], g @ xi[:, 2],
                      np.sum(g * 0.5 * np.sum(xi * xi, axis=1))])
 

@@ -32,6 +32,38 @@ class VelocityGrid:
         self.xi = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)   # [Nv, 3]
         self.nv = self.xi.shape[0]
 
+    # The distributions and moments on this grid, as methods so that the GSIS
+    # driver works unchanged on the reduced (xi_z-integrated) grid of
+    # oracle.reduced, which has the same methods.
+    reduced = False
+
+    def maxwellian(self, rho, u, T):
+        return maxwellian(rho, u, T, self.xi)
+
+    def shakhov(self, rho, u, T, q):
+        return reference_g0t(rho, u, T, q, self.xi)
+
+    def grad13(self, rho, u, T, sigma, q):
+        return grad13(rho, u, T, sigma, q, self.xi)
+
+    def conserved(self, f):
+        return conserved(f, self)
+
+    def moments(self, f):
+        return moments(f, self)
+
+    def heat_flux_about(self, f, u):
+        return heat_flux_about(f, u, self)
+
+    def conservation_correct(self, base, M, U):
+        return conservation_correct(base, M, U, self)
+
+    def corrected_maxwellian(self, rho, u, T):
+        return corrected_maxwellian(rho, u, T, self)
+
+    def corrected_shakhov(self, rho, u, T, q):
+        return corrected_shakhov(rho, u, T, q, self)
+
 
 # --------------------------------------------------------------------------- transport coefficients
 def mu0_from_kn(Kn, L=1.0, p0=1.0, T0=1.0):

@@ -19,13 +19,18 @@ OMEGA = 0.81           # viscosity index of the monatomic workloads
 
 @dataclass
 class VGrid:
-    """Uniform midpoint velocity grid: n[d] nodes on [lo[d], hi[d]] per axis."""
+    """Uniform midpoint velocity grid: n[d] nodes on [lo[d], hi[d]] per axis.
+    reduced: the xi_z axis is integrated out (2D flows): two reduced
+    distributions on the n[0] x n[1] grid, n[2] / lo[2] / hi[2] unused."""
     n: tuple
     lo: tuple
     hi: tuple
+    reduced: bool = False
 
     @property
     def nv(self):
+        if self.reduced:
+            return int(2 * self.n[0] * self.n[1])
         return int(self.n[0] * self.n[1] * self.n[2])
 
 
