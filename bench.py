@@ -51,13 +51,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsis", choices=["gsis", "reference"])
     ap.add_argument("--config", default="cylinder",
-                    choices=["cylinder", "shock", "cylinder_full", "sphere", "cylinder32", "batch"])
+                    choices=["cylinder", "shock", "cylinder_full", "cylinder_reduced", "sphere", "cylinder32",
+                             "batch"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "f16"])
     ap.add_argument("--tile", default=None,
                     help="run the sweep with this tile shape instead of the autotuned one (for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-converge", action="store_true", help="skip the time-to-converged measurement")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the reduced-precision forms and the full-kinetic arm (default cylinder run)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA peak probe (derived FP64 peak instead)")
     return ap.parse_args()
 
 
@@ -73,11 +77,13 @@ def make_case(config, small=False):
         return shock_1d_case(n_cells=200 if not small else 40)
     if config == "cylinder32":   # reduced mesh, same velocity grid (for profiler captures)
         return cylinder_case(n_r=32, n_theta=32, presolve_max_blocks=5)
-    if config in ("cylinder", "cylinder_full"):
-        adaptive = config == "cylinder"
+    if config in ("cylinder", "cylinder_full", "cylinder_reduced"):
+        adaptive = config != "cylinder_full"
+        reduced = config == "cylinder_reduced"
         if small:
-            return cylinder_case(n_r=12, n_theta=12, presolve_max_blocks=1, macro_steps=20, adaptive=adaptive)
-        return cylinder_case(adaptive=adaptive)
+            return cylinder_case(n_r=12, n_theta=12, presolve_max_blocks=1, macro_steps=20, adaptive=adaptive,
+                                 reduced=reduced)
+        return cylinder_case(adaptive=adaptive, reduced=reduced)
     if small:
         return sphere_case(n_r=6, n_pol=4, n_az=4, presolve_max_blocks=1, macro_steps=10)
     return sphere_case()
@@ -87,6 +93,8 @@ def workload_name(config, dtype):
     return {
         "cylinder": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, velocity grid 48x48x24, adaptive Kn_ref=0.01",
         "cylinder_full": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, velocity grid 48x48x24, full kinetic",
+        "cylinder_reduced": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 128x128, reduced distributions (xi_z "
+                            "integrated out) on a 48x48 velocity grid, adaptive Kn_ref=0.01",
         "cylinder32": "2D cylinder Ma=5 Kn=0.01 Tw=2, O-grid 32x32, velocity grid 48x48x24, adaptive Kn_ref=0.01",
         "shock": "1D normal shock Ma=2, 200 cells on [-25,25] mfp, velocity grid 48x24x24, all kinetic",
         "sphere": "3D sphere Ma=5 Kn=0.005 Tw=2, O-grid 96x64x64, velocity grid 48^3, adaptive Kn_ref=0.01",
@@ -183,9 +191,29 @@ def traffic_from_profile(config, dtype):
     return d.get("dram_bytes_per_launch_full")
 
 
-def cpu_baseline(config, steps=1):
-    """The oracle as it stands, timed on a bounded sample of the workload:
-    one GSIS iteration on a 12x12 O-grid (same velocity grid, same physics)."""
+def _cpu_model():
+    """CPU model name of this host (for the record of the CPU baseline)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_sample(config, steps):
+    """One worker of the CPU baseline: the oracle as it stands on the bounded
+    sample of the workload (set-up untimed), `steps` GSIS iterations timed.
+    Returns (points, seconds, n_dvm, n_v, n_cells)."""
     from oracle.gsis import OracleSolver
     case = make_case(config, small=True)
     o = OracleSolver(case)
@@ -195,43 +223,146 @@ def cpu_baseline(config, steps=1):
     for _ in range(steps):
         o.step()
         pts += int(o.dvm.sum()) * o.vg.nv
-    dt = time.perf_counter() - t
-    return pts / dt, dt, int(o.dvm.sum()), o.vg.nv, case.mesh.ncell
+    return pts, time.perf_counter() - t, int(o.dvm.sum()), o.vg.nv, case.mesh.ncell
+
+
+def cpu_baseline(config, steps=1, cores=None):
+    """The oracle as it stands, timed on every host core: one independent
+    instance of the bounded sample per core (a process pool started with
+    `spawn`, one BLAS thread each), throughput = all points of all instances
+    over the wall time of the slowest.  Returns (updates/s, seconds, n_dvm,
+    n_v, n_cells, cores, cpu model)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.starmap(_oracle_sample, [(config, steps)] * cores)
+        wall = time.perf_counter() - t0
+    pts = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    _, _, nd, nv, nc = res[0]
+    return pts / slowest, slowest, nd, nv, nc, cores, _cpu_model(), wall
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on every host core of
+    rank 0, each core running its own instance of the bounded sample of the
+    workload (warm-up iterations untimed, then `steps` timed ones)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle.gsis import OracleSolver
-    case = make_case(args.config, small=True)
-    o = OracleSolver(case)
-    o.initialise()
-    for _ in range(args.warmup):
-        o.step()
-    t = time.perf_counter()
-    pts = 0
-    for _ in range(args.steps):
-        o.step()
-        pts += int(o.dvm.sum()) * o.vg.nv
-    dt = time.perf_counter() - t
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_reference_steps, [(args.config, args.warmup, args.steps)] * cores)
+    pts = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
     value = pts / dt
-    sample = ("one GSIS iteration per step of the FP64 oracle on a %d-cell %s sample (%d DVM cells) with the "
-              "workload's velocity grid (%d velocities)" % (case.mesh.ncell, args.config, int(o.dvm.sum()), o.vg.nv))
+    nd, nv, nc = res[0][2], res[0][3], res[0][4]
+    sample = ("%d independent instances (one per host core, %s) of the FP64 oracle, each one GSIS iteration per "
+              "step on a %d-cell %s sample (%d DVM cells) with the workload's velocity grid (%d velocities)"
+              % (cores, _cpu_model(), nc, args.config, nd, nv))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.config, args.dtype), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _oracle_reference_steps(config, warmup, steps):
+    from oracle.gsis import OracleSolver
+    case = make_case(config, small=True)
+    o = OracleSolver(case)
+    o.initialise()
+    for _ in range(warmup):
+        o.step()
+    t = time.perf_counter()
+    pts = 0
+    for _ in range(steps):
+        o.step()
+        pts += int(o.dvm.sum()) * o.vg.nv
+    return pts, time.perf_counter() - t, int(o.dvm.sum()), o.vg.nv, case.mesh.ncell
 
 
 def mesh_bytes(case):
     m = case.mesh
     b = m.centers.nbytes + m.volumes.nbytes + sum(a.nbytes for a in m.S) + sum(a.nbytes for a in m.xf)
     return b + case.W0.nbytes
+
+
+def measured_alu_peaks(stream, local):
+    """FP64 and FP32 FMA throughput of this GPU's CUDA cores, measured by the
+    library's probe kernel (CUDA events, best of four ~40 ms launches), with
+    the SM clock sampled during the probes."""
+    from paper_2501_02245_gb300.gsis import fma_peak
+    clocks = Clocks(local)
+    clocks.start()
+    out = {}
+    try:
+        for name, fp64 in (("fp64", True), ("fp32", False)):
+            r, ms = fma_peak(fp64, stream)
+            out[name + "_tflops"] = r / 1e12
+            out[name + "_launch_ms"] = ms
+    finally:
+        ck = clocks.stop()
+    out["clocks"] = ck
+    out["how"] = ("8 independent FMA chains per thread, 8 CTAs x 256 threads per SM, 2 flop per FMA; "
+                  "k_fma_probe in paper_2501_02245_gb300/csrc/peaks.cu")
+    if ck.get("sm_mhz"):
+        out["derived_fp64_tflops_at_sampled_clock"] = 152 * 4 * ck["sm_mhz"] * 1e6 / 1e12
+    return out
+
+
+def sweep_roofline(args, rep, steps, peaks, traffic):
+    """Roofline of the dominant kernel (the kinetic sweep) in the unit of one
+    GSIS iteration -- every (cell, velocity) point updated once: read f once,
+    write f once (2b bytes), one point update's flops -- over the measured
+    duration of the sweep launches of one iteration (two Gauss-Seidel passes
+    on 2D/3D meshes), with the same figures per pass beside it."""
+    sweep_ms_iter = rep["phase_ms"]["sweep"] / steps
+    launches_iter = rep["sweep_launches"] / steps
+    pts = rep["n_dvm"] * rep["n_v"]
+    eb = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[args.dtype]
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        mp = json.load(fh)
+    trf = None if traffic is None else traffic * launches_iter
+    if args.dtype == "f64":
+        fpp = SWEEP_FLOPS_PER_POINT_1D if args.config == "shock" else SWEEP_FLOPS_PER_POINT_2D
+        peak = peaks.get("fp64_tflops") if peaks else None
+        src = "measured FP64 FMA throughput (gsis_probe_fma_peak, this run)"
+        if not peak:
+            peak, src = FP64_PEAK_TFLOPS, "FP64 unit counts x clock: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)"
+        achieved = fpp * pts / (sweep_ms_iter * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": trf, "kernel": "k_sweep<double>", "peak_source": src,
+                "per": "GSIS iteration: %g sweep launches (Gauss-Seidel passes) per iteration" % launches_iter,
+                "algorithmic": "%d FP64 flop per (cell, velocity) per GSIS iteration (one point update)" % fpp,
+                "per_pass": {"achieved": achieved * launches_iter, "frac": achieved * launches_iter / peak,
+                             "algorithmic": "%d FP64 flop per (cell, velocity) per pass" % fpp},
+                "hbm_frac": 2 * eb * pts / (sweep_ms_iter * 1e-3) / 1e9 / mp["hbm_gbs"]}
+    else:
+        achieved = 2 * eb * pts / (sweep_ms_iter * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / mp["hbm_gbs"], "traffic": trf, "kernel": "k_sweep",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)",
+                "per": "GSIS iteration: %g sweep launches (Gauss-Seidel passes) per iteration" % launches_iter,
+                "algorithmic": "2 x %d bytes per (cell, velocity) per GSIS iteration (read f once, write once)" % eb,
+                "per_pass": {"achieved": achieved * launches_iter, "frac": achieved * launches_iter / mp["hbm_gbs"],
+                             "algorithmic": "2 x %d bytes per (cell, velocity) per pass" % eb}}
+        if peaks and peaks.get("fp32_tflops"):
+            fpp = SWEEP_FLOPS_PER_POINT_1D if args.config == "shock" else SWEEP_FLOPS_PER_POINT_2D
+            roof["fp32_alu_frac_per_pass"] = fpp * pts * launches_iter / (sweep_ms_iter * 1e-3) / 1e12 / peaks[
+                "fp32_tflops"]
+    return roof
 
 
 def run_gsis(args):
@@ -272,55 +403,174 @@ def run_gsis(args):
     ms = e0.elapsed_time(e1)
     pts = rep["n_dvm"] * rep["n_v"] * args.steps
     value, t_max = combine_ranks(pts, ms, pg, "cuda")
-    # dominant kernel: the sweep; its launches are bracketed by CUDA events on the context stream
-    sweep_ms_per_launch = rep["phase_ms"]["sweep"] / max(rep["sweep_launches"], 1)
-    pts_per_launch = rep["n_dvm"] * rep["n_v"]
-    eb = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[args.dtype]
-    traffic = traffic_from_profile(args.config, args.dtype)
-    if args.dtype == "f64":
-        fpp = SWEEP_FLOPS_PER_POINT_1D if args.config == "shock" else SWEEP_FLOPS_PER_POINT_2D
-        flops = fpp * pts_per_launch
-        achieved = flops / (sweep_ms_per_launch * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_sweep<double> (one Gauss-Seidel pass)",
-                "peak_source": "FP64 unit counts x clock: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived)",
-                "algorithmic": "%d FP64 flop per (cell, velocity) per pass" % fpp}
-    else:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-        bytes_alg = 2 * eb * pts_per_launch   # read f once + write f once per pass
-        achieved = bytes_alg / (sweep_ms_per_launch * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_sweep (one Gauss-Seidel pass)", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "algorithmic": "2 x %d bytes per (cell, velocity) per pass" % eb}
+    reference_state = (s.W(), s.moments(["wall_q"])["wall_q"], args.warmup + args.steps)
+    tuning = s.tuning_info()
+    s.close()
+    peaks = None
+    if not args.no_peaks:
+        try:
+            peaks = measured_alu_peaks(stream, local)
+        except Exception as exc:   # the roofline then falls back to the derived FP64 peak, and says so
+            peaks = {"error": str(exc)}
+    roof = sweep_roofline(args, rep, args.steps, peaks, traffic_from_profile(args.config, args.dtype))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": workload_name(args.config, args.dtype), "parallelism": "replicas" if ws > 1 else "1 GPU",
                        "n_dvm": rep["n_dvm"], "n_cells": case.mesh.ncell, "n_v": rep["n_v"],
                        "vdf_bytes": rep["vdf_bytes"], "l2": "VDF (%.1f GB) larger than L2" % (rep["vdf_bytes"] / 1e9),
-                       "presolve_blocks": rep0["presolve_blocks"], "eps_last": rep["eps"],
-                       "sweep_tile": s.tuning_info(),
+                       "presolve_blocks": rep0["presolve_blocks"], "presolve_ms": rep0["phase_ms"]["presolve"],
+                       "eps_last": rep["eps"], "sweep_tile": tuning,
                        "phase_ms_per_step": {k: v / args.steps for k, v in rep["phase_ms"].items() if v > 0}},
-            "roofline": roof, "clocks": ck, "gpu_launches": rep["kernel_launches"]}
-    s.close()
+            "roofline": roof, "measured_peaks": peaks, "clocks": ck, "gpu_launches": rep["kernel_launches"]}
     if not args.no_e2e:
         line["e2e"] = e2e(args, case, stream)
     if not args.no_converge and args.config in ("cylinder", "cylinder_full", "shock"):
-        line["time_to_converged"] = time_to_converged(args, case, stream)
+        line["time_to_converged"] = time_to_converged(args, case, stream, args.dtype)
+    if not args.no_forms and args.config == "cylinder" and args.dtype == "f64" and rank == 0:
+        line["precision_forms"] = precision_forms(args, case, stream, reference_state,
+                                                  line.get("time_to_converged"), t_max / args.steps)
+        line["full_kinetic"] = full_kinetic_arm(args, stream, rep, t_max / args.steps)
+        line["reduced_2d"] = reduced_arm(args, stream, rep, reference_state, t_max / args.steps)
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, nd, nv, nc = cpu_baseline(args.config)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "one GSIS iteration of the FP64 oracle on a %d-cell sample of the workload "
-                                          "(%d DVM cells, %d velocities), %.1f s" % (nc, nd, nv, dt)}
+        v, dt, nd, nv, nc, cores, cpu, wall = cpu_baseline(args.config)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu,
+                                "sample": "%d independent instances of the FP64 oracle (one per host core), one GSIS "
+                                          "iteration each on a %d-cell sample of the workload (%d DVM cells, %d "
+                                          "velocities); slowest instance %.1f s" % (cores, nc, nd, nv, dt)}
     if pg:
         pg.barrier()
         pg.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _error_vs(Wr, qr, W, q):
+    """Largest error of density, temperature (relative to their largest value)
+    and wall heat flux (relative to its largest magnitude)."""
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+    return {"rho": rel(W[:, 0], Wr[:, 0]), "T": rel(W[:, 4], Wr[:, 4]), "wall_q": rel(q, qr)}
+
+
+def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_iter):
+    """The cylinder with FP32, BF16 and FP16 VDF storage (FP32 sweep
+    arithmetic; FP64 moments, conservation correction and synthetic solve):
+    throughput, time to the residual thresholds from a fresh context, VDF
+    memory, and the error in density, temperature and wall heat flux against
+    the FP64 GPU run (the parity-tested path) after the same number of
+    iterations from the same start."""
+    import torch
+    from paper_2501_02245_gb300 import Solver
+    Wr, qr, n_ref = reference_state
+    out = {"reference": "FP64 GPU run of this benchmark after %d GSIS iterations" % n_ref}
+    thresholds = (1e-3, 2e-4)
+    for dt in ("f32", "bf16", "f16"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = Solver.from_case(case, vdf_dtype=dt, stream=stream)
+        s.iterate(0)
+        reached, err, it_ms = {}, None, []
+        eps_min = 1e300
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n_dvm = vdf = 0
+        for it in range(max(n_ref, 60)):
+            e0.record(stream)
+            r = s.iterate(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= 2:
+                it_ms.append(e0.elapsed_time(e1))
+            n_dvm, vdf = r["n_dvm"], r["vdf_bytes"]
+            eps_min = min(eps_min, r["eps"])
+            for th in thresholds:
+                k = "%.0e" % th
+                if k not in reached and r["eps"] < th:
+                    reached[k] = {"iterations": it + 1, "seconds": time.perf_counter() - t0}
+            if it + 1 == n_ref:
+                err = _error_vs(Wr, qr, s.W(), s.moments(["wall_q"])["wall_q"])
+            if it + 1 >= n_ref and len(reached) == len(thresholds):
+                break
+        s.close()
+        ms_it = float(np.median(it_ms)) if it_ms else None
+        d = {"ms_per_iteration": ms_it, "updates_per_s": n_dvm * case.vgrid.nv / (ms_it * 1e-3) if ms_it else None,
+             "vdf_bytes": vdf, "error_vs_f64": err, "time_to_converged": reached, "eps_min": eps_min}
+        if f64_ms_per_iter and ms_it:
+            d["speedup_per_iteration_vs_f64"] = f64_ms_per_iter / ms_it
+        if f64_ttc:
+            d["speedup_to_threshold_vs_f64"] = {
+                k: f64_ttc["reached"][k]["seconds"] / v["seconds"] for k, v in reached.items()
+                if k in f64_ttc.get("reached", {})}
+        out[dt] = d
+    return out
+
+
+def reduced_arm(args, stream, rep_3d, reference_state, ms_per_iter_3d, steps=5):
+    """The cylinder with the reduced distributions of a 2D flow (xi_z
+    integrated out: G and H on the 48 x 48 (xi_x, xi_y) grid, the paper's 2D
+    memory saver) against the 3D velocity grid: throughput, VDF memory, time
+    to the residual thresholds, and the largest difference of density,
+    temperature and wall heat flux from the 3D run after the same number of
+    iterations (two discretisations of the same flow: the reduced one is
+    exact in xi_z)."""
+    import torch
+    from paper_2501_02245_gb300 import Solver
+    Wr, qr, n_ref = reference_state
+    case = make_case("cylinder_reduced")
+    case.tol = 0.0
+    s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
+    s.iterate(0)
+    s.iterate(n_ref - steps)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = s.iterate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    diff = _error_vs(Wr, qr, s.W(), s.moments(["wall_q"])["wall_q"])
+    s.close()
+    out = {"workload": workload_name("cylinder_reduced", args.dtype), "ms_per_iteration": ms,
+           "updates_per_s": r["n_dvm"] * r["n_v"] / (ms * 1e-3), "n_dvm": r["n_dvm"], "n_v": r["n_v"],
+           "vdf_bytes": r["vdf_bytes"], "vdf_fraction_of_3d": r["vdf_bytes"] / rep_3d["vdf_bytes"],
+           "time_per_iteration_fraction_of_3d": ms / ms_per_iter_3d,
+           "phase_ms_per_step": {k: v / steps for k, v in r["phase_ms"].items() if v > 0},
+           "difference_from_3d_after_%d_iterations" % n_ref: diff}
+    if not args.no_converge:
+        out["time_to_converged"] = time_to_converged(args, case, stream, args.dtype, cap=60)
+    return out
+
+
+def full_kinetic_arm(args, stream, rep_adaptive, adaptive_ms_per_iter, steps=3):
+    """The other arm of the cylinder configuration: every cell kinetic (no
+    adaptation), same mesh, velocity grid and precision: throughput, VDF
+    memory and time to the residual thresholds, against the adaptive run."""
+    import torch
+    from paper_2501_02245_gb300 import Solver
+    case = make_case("cylinder_full")
+    case.tol = 0.0
+    s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
+    s.iterate(0)
+    s.iterate(2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = s.iterate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    out = {"workload": workload_name("cylinder_full", args.dtype), "ms_per_iteration": ms,
+           "updates_per_s": r["n_dvm"] * r["n_v"] / (ms * 1e-3), "n_dvm": r["n_dvm"], "vdf_bytes": r["vdf_bytes"],
+           "adaptive_vdf_fraction": rep_adaptive["vdf_bytes"] / r["vdf_bytes"],
+           "adaptive_time_per_iteration_fraction": adaptive_ms_per_iter / ms}
+    if not args.no_converge:
+        out["time_to_converged"] = time_to_converged(args, case, stream, args.dtype, cap=60)
+    return out
 
 
 def run_batch(args):
@@ -394,10 +644,11 @@ def run_batch(args):
                        "includes": "set-up upload of 64 solves, autotuning and graph recording, %d iterations, "
                                    "result read-back" % args.steps}
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, nd, nv, nc = cpu_baseline("batch")
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "one GSIS iteration of the FP64 oracle on one shock of the batch reduced "
-                                          "to %d cells (%d velocities), %.1f s" % (nc, nv, dt)}
+        v, dt, nd, nv, nc, cores, cpu, wall = cpu_baseline("batch")
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu,
+                                "sample": "%d independent instances of the FP64 oracle (one per host core), one GSIS "
+                                          "iteration each on one shock of the batch reduced to %d cells (%d "
+                                          "velocities); slowest instance %.1f s" % (cores, nc, nv, dt)}
     if pg:
         pg.barrier()
         pg.destroy_process_group()
@@ -406,7 +657,7 @@ def run_batch(args):
     return 0
 
 
-def time_to_converged(args, case, stream, thresholds=(1e-3, 2e-4), cap=80):
+def time_to_converged(args, case, stream, dtype, thresholds=(1e-3, 2e-4), cap=80):
     """Wall-clock time (device synchronised) from a fresh context (host data,
     presolve, region) until the residual of Sec. 4 first falls below each
     threshold, at most `cap` GSIS iterations.  The 1e-6 criterion of the paper
@@ -416,7 +667,7 @@ def time_to_converged(args, case, stream, thresholds=(1e-3, 2e-4), cap=80):
     from paper_2501_02245_gb300 import Solver
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s = Solver.from_case(case, vdf_dtype=args.dtype, stream=stream)
+    s = Solver.from_case(case, vdf_dtype=dtype, stream=stream)
     s.iterate(0)
     torch.cuda.synchronize()
     out = {"criterion": "epsilon of Sec. 4 between consecutive iterations", "cap": cap,

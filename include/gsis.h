@@ -97,7 +97,10 @@ typedef struct {
     int    presolve_max_blocks; /* Sec. 3.4 Step 1 NS presolve (HoT = 0): at most this many blocks of
                                    macro_steps steps, stopping when epsilon between blocks < tol;
                                    0 = start from W0 directly                                     */
-    unsigned long long spin_limit; /* iteration limit of any bounded device wait (0 = default)    */
+    unsigned long long spin_limit; /* polls (about 32 ns apart) of any device-side wait before it gives
+                                      up with GSIS_ERR_TIMEOUT: the grid barriers of the persistent
+                                      synthetic-solve kernel (GSIS_MACRO_PERSISTENT);
+                                      0 = default 2^24 (about a second)                              */
     double relax;         /* weight of the synthetic correction: W^{n+1} = W^{n+1/2} + relax *
                              (W_synthetic - W^{n+1/2}); 1 = the plain scheme, (0, 1]; 0 is read as 1 */
 } gsis_params;
@@ -127,11 +130,19 @@ typedef struct {
 
 /* Uniform midpoint velocity grid (Sec. 4.2: uniform discretisation of a
  * truncated box): n[d] nodes on [lo[d], hi[d]], node k at lo+(k+1/2)(hi-lo)/n,
- * weight prod_d (hi-lo)/n; flat index v = ix + nx*(iy + ny*iz). */
+ * weight prod_d (hi-lo)/n; flat index v = ix + nx*(iy + ny*iz).
+ * reduced = 1 (2D flows, Sec. 3.3 and the 2D velocity grid of Sec. 4.2): the
+ * xi_z direction is integrated out and the VDF of a cell is stored as two
+ * reduced distributions on the n[0] x n[1] grid, G = int f dxi_z and
+ * H = int xi_z^2 f dxi_z (flat index v = ix + nx*(iy + ny*p), p = 0 for G,
+ * 1 for H; weight (hi[0]-lo[0])(hi[1]-lo[1])/(n[0] n[1]); n[2], lo[2], hi[2]
+ * ignored).  Needs a mesh whose faces have no z component and a state with
+ * u_z = 0 (GSIS_ERR_ARG at the first gsis_iterate otherwise). */
 typedef struct {
     int    n[3];
     double lo[3];
     double hi[3];
+    int    reduced;
 } gsis_vgrid_desc;
 
 /* Per-call report of gsis_iterate. Phase times are CUDA-event times on the
@@ -173,7 +184,10 @@ gsis_status gsis_set_velocity_grid(gsis_ctx* ctx, const gsis_vgrid_desc* vgrid);
  * (presolve, region, initial VDF).  Stops early when eps < tol.  Synchronises
  * the stream once per iteration to read eps (8 bytes device->host).
  * report may be NULL.  Errors: GSIS_ERR_STATE (mesh or grid missing),
- * GSIS_ERR_NONFINITE, GSIS_ERR_CUDA, GSIS_ERR_OOM. */
+ * GSIS_ERR_NONFINITE, GSIS_ERR_CUDA, GSIS_ERR_OOM, GSIS_ERR_TIMEOUT (with
+ * the persistent synthetic solve selected: a grid barrier waited more than
+ * spin_limit polls; every block of that launch returns, the CUDA context
+ * stays usable, the state of this solve is lost). */
 gsis_status gsis_iterate(gsis_ctx* ctx, int max_iter, gsis_report* report);
 
 /* Write the selected per-cell fields (GSIS_FIELD_* bits, in bit order) of the
@@ -258,6 +272,23 @@ gsis_status gsis_debug_set_sweep_tile(gsis_ctx* ctx, const char* name);
  * first iteration.  The paper has no counterpart. */
 gsis_status gsis_debug_vdf_moments(gsis_ctx* ctx, int direct, double* dst, long long capacity);
 
+/* Test hook: choose how the synthetic solve (Eq. macro) runs from now on.
+ * GSIS_MACRO_AUTO (default): the fused one-CTA kernel for meshes of up to
+ * 4096 cells, else the per-phase kernels (4 + k_sub launches per
+ * pseudo-step).  GSIS_MACRO_FUSED, _MULTI and _PERSISTENT (one cooperative
+ * launch per block of pseudo-steps, the phases separated by grid barriers
+ * bounded by spin_limit; the per-phase kernels inside a batch graph capture
+ * or where a cooperative launch is not available) force one
+ * implementation; all compute the same result.
+ * GSIS_MACRO_PERSISTENT_STALL (tests of the bounded wait only): the
+ * persistent launch's barrier waits for one CTA more than the launch has, so
+ * the wait can only end by running out of spin_limit polls; the next
+ * gsis_iterate returns GSIS_ERR_TIMEOUT.  GSIS_ERR_ARG for another value.
+ * The paper has no counterpart. */
+enum { GSIS_MACRO_AUTO = 0, GSIS_MACRO_FUSED = 1, GSIS_MACRO_MULTI = 2, GSIS_MACRO_PERSISTENT = 3,
+       GSIS_MACRO_PERSISTENT_STALL = 4 };
+gsis_status gsis_debug_set_macro_path(gsis_ctx* ctx, int path);
+
 /* Human-readable result of the sweep's tile-shape autotuning for this
  * context (chosen shape and the timing of every candidate), or "" before the
  * first iteration.  Each context times the candidate shapes of its kinetic
@@ -281,6 +312,16 @@ void gsis_free(gsis_ctx* ctx);
 /* Library version string. */
 const char* gsis_version(void);
 
+/* Measurement utility (the paper has no counterpart): the fused
+ * multiply-add throughput of the CUDA cores of the current device in FP64
+ * (fp64 != 0) or FP32, in flop/s (2 per FMA), the best of four launches of
+ * about 40 ms each on cuda_stream (NULL = default stream; synchronises it).
+ * It is the measured roof of the FP64- and FP32-arithmetic kinetic sweeps.
+ * ms (may be NULL) receives the duration of the best launch.  Allocates and
+ * frees a few KB of device memory.  Errors: GSIS_ERR_ARG (NULL
+ * flops_per_s), GSIS_ERR_OOM, GSIS_ERR_CUDA. */
+gsis_status gsis_probe_fma_peak(int fp64, void* cuda_stream, double* flops_per_s, double* ms);
+
 /* Allocation-free evaluation of conservation-corrected discrete Maxwellians
  * (the paper has no counterpart; this is a library service).
  *
@@ -293,7 +334,8 @@ const char* gsis_version(void);
  * holds until the process exits.
  *
  * W:      device pointer, [n][5] states (rho, ux, uy, uz, T), rho > 0, T > 0.
- * vgrid:  host pointer, the velocity grid (as for gsis_set_velocity_grid).
+ * vgrid:  host pointer, the velocity grid (as for gsis_set_velocity_grid;
+ *         full 3D grids only: reduced = 1 gives GSIS_ERR_ARG).
  * f_out:  device pointer, [n][nx*ny*nz] doubles (x fastest): row k receives
  *         the Maxwellian of W[k] corrected so that its discrete mass,
  *         momentum and energy equal those of W[k] exactly (the same rows the

@@ -19,7 +19,8 @@ namespace gsis {
 gsis_status set_err(gsis_ctx* c, gsis_status s, const std::string& msg) {
     if (c) {
         c->err = msg;
-        if (s == GSIS_ERR_CUDA || s == GSIS_ERR_NONFINITE || s == GSIS_ERR_INTERNAL) c->broken = true;
+        if (s == GSIS_ERR_CUDA || s == GSIS_ERR_NONFINITE || s == GSIS_ERR_INTERNAL || s == GSIS_ERR_TIMEOUT)
+            c->broken = true;
     }
     return s;
 }
@@ -137,12 +138,16 @@ gsis_status presolve(gsis_ctx* c) {
     launch_prim_to_cons(c, c->W, c->U);
     cudaMemcpyAsync(c->Wm, c->W, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
     c->presolve_blocks = 0;
+    *c->h_err = 0;
     for (int b = 0; b < c->p.presolve_max_blocks; ++b) {
         cudaMemcpyAsync(c->Wp, c->Wm, (size_t)N * 5 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
         macro_block(c, c->p.macro_steps, false, false);
         launch_eps(c, c->Wm, c->Wp);
         cudaMemcpyAsync(c->h_eps, c->eps_buf, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "presolve")) return GSIS_ERR_CUDA;
+        if (*c->h_err != 0)
+            return set_err(c, GSIS_ERR_TIMEOUT, "a grid barrier of the synthetic solve ran out of spin_limit polls "
+                                                "(NS presolve)");
         c->presolve_blocks = b + 1;
         if (c->h_eps[1] != 0.0) return set_err(c, GSIS_ERR_NONFINITE, "non-finite state in the NS presolve");
         if (c->h_eps[0] < c->p.tol) break;
@@ -153,6 +158,16 @@ gsis_status presolve(gsis_ctx* c) {
 
 gsis_status start(gsis_ctx* c) {
     const int N = c->m.N;
+    if (c->vg.reduced) {   // the reduced distributions assume a flow without z dependence and u_z = 0
+        if (c->normal_components > 2)
+            return set_err(c, GSIS_ERR_ARG, "reduced velocity grid needs a mesh whose faces have no z component");
+        for (int q = 0; q < N; ++q)
+            if (c->host_W0[(size_t)q * 5 + 3] != 0.0)
+                return set_err(c, GSIS_ERR_ARG, "reduced velocity grid needs u_z = 0 in the initial state");
+        for (int s = 0; s < 6; ++s)
+            if (c->m.bc_type[s] == GSIS_BC_FARFIELD && c->m.bc_state[s][3] != 0.0)
+                return set_err(c, GSIS_ERR_ARG, "reduced velocity grid needs u_z = 0 in the far-field states");
+    }
     if (!cuda_ok(c, cudaMemcpyAsync(c->W, c->host_W0.data(), (size_t)N * 5 * sizeof(double),
                                     cudaMemcpyHostToDevice, c->stream), "upload W0"))
         return GSIS_ERR_CUDA;
@@ -243,6 +258,7 @@ void stage_correct(gsis_ctx* c) {
 }
 
 gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
+    *c->h_err = 0;   // barrier error word of a persistent synthetic-solve launch (written back by it)
     if (c->p.adaptive && c->iteration == c->p.adapt_every && !c->have_forced) {
         used[GSIS_PH_ADAPT] = true;
         phase_begin(c, GSIS_PH_ADAPT);
@@ -289,6 +305,9 @@ gsis_status gsis_step(gsis_ctx* c, double* eps_out, bool* used) {
     phase_end(c, GSIS_PH_CORRECT);
     if (!cuda_ok(c, cudaStreamSynchronize(c->stream), "GSIS iteration")) return GSIS_ERR_CUDA;
     if (!cuda_ok(c, cudaGetLastError(), "kernel launch")) return GSIS_ERR_CUDA;
+    if (*c->h_err != 0)
+        return set_err(c, GSIS_ERR_TIMEOUT, "a grid barrier of the synthetic solve ran out of spin_limit polls "
+                                            "in iteration " + std::to_string(c->iteration));
     if (c->h_eps[1] != 0.0)
         return set_err(c, GSIS_ERR_NONFINITE, "non-finite or non-positive density/temperature after iteration " +
                                                   std::to_string(c->iteration));
@@ -533,7 +552,7 @@ gsis_status build_plan(BatchPlan* P) {
         if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream, P->macro_cluster);
         for (int i : P->big) {
             gsis_ctx* c = P->ctxs[i];
-            macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0);
+            macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0, true);
         }
         for (gsis_ctx* c : P->ctxs) {
             stage_residual(c, true);
@@ -606,7 +625,7 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
     if (!c) return GSIS_ERR_OOM;
     c->p = p;
     if (c->p.relax == 0.0) c->p.relax = 1.0;
-    if (c->p.spin_limit == 0) c->p.spin_limit = 1ull << 26;
+    if (c->p.spin_limit == 0) c->p.spin_limit = 1ull << 24;   // with 32 ns sleeps: about a second
     if (alloc) { c->alloc = *alloc; c->have_alloc = true; }
     c->stream = (cudaStream_t)cuda_stream;
     c->device = dev;
@@ -616,7 +635,8 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
     for (int i = 0; i < 2 * GSIS_NPHASE; ++i) ev_ok = ev_ok && cudaEventCreate(&c->ev[i]) == cudaSuccess;
     c->events = ev_ok;
     if (cudaMallocHost(&c->h_eps, 4 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&c->h_count, 4 * sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&c->h_count, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         gsis_free(c);
         return GSIS_ERR_CUDA;
@@ -782,6 +802,9 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->lamS = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
     c->Ff = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
     c->lamf = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
+    c->F0 = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
+    c->dFa = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
+    c->dFb = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
     c->fgeo = (double*)dev_alloc(c, (size_t)N * 3 * 8 * sizeof(double));
     c->bgeo = (double*)dev_alloc(c, (size_t)N * 6 * 8 * sizeof(double));
     c->acell = (double*)dev_alloc(c, (size_t)N * sizeof(double));
@@ -811,13 +834,14 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->hp_cnt = (int*)dev_alloc(c, (m.H + 1) * sizeof(int));
     c->d_count = (int*)dev_alloc(c, 4 * sizeof(int));
     c->d_job = (gsis::MacroJob*)dev_alloc(c, sizeof(gsis::MacroJob));
+    c->d_bar = (gsis::GridBarrier*)dev_alloc(c, sizeof(gsis::GridBarrier));
     c->specs = (RecSpec*)dev_alloc(c, (size_t)std::max(N, 6) * sizeof(RecSpec));
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
-    if (!c->d_job || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wmom ||
+    if (!c->d_job || !c->d_bar || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wmom ||
         !c->Wh || !c->fgeo || !c->bgeo || !c->acell || !c->wallq ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
-        !c->lamf || !c->gu || !c->gT ||
+        !c->lamf || !c->F0 || !c->dFa || !c->dFb || !c->gu || !c->gT ||
         !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->wall_in ||
         !c->wall_kin || !c->wall_corr || !c->eps_buf || !c->flag ||
         !c->cell2dvm || !c->old_cell2dvm || !c->ghost_id || !c->ghost_cell || !c->enter_list || !c->hp_off ||
@@ -843,18 +867,27 @@ gsis_status gsis_set_velocity_grid(gsis_ctx* c, const gsis_vgrid_desc* vd) {
     if (st != GSIS_OK) return st;
     if (!vd) return set_err(c, GSIS_ERR_ARG, "NULL velocity-grid descriptor");
     if (c->started) return set_err(c, GSIS_ERR_STATE, "velocity grid cannot change after the first iterate");
-    for (int d = 0; d < 3; ++d)
+    if (vd->reduced != 0 && vd->reduced != 1) return set_err(c, GSIS_ERR_ARG, "reduced must be 0 or 1");
+    const bool red = vd->reduced == 1;
+    const int naxes = red ? 2 : 3;   // the reduced grid's z "axis" is its two planes G and H
+    for (int d = 0; d < naxes; ++d)
         if (vd->n[d] < 1 || !(vd->hi[d] > vd->lo[d]) || !std::isfinite(vd->lo[d]) || !std::isfinite(vd->hi[d]))
             return set_err(c, GSIS_ERR_ARG, "velocity grid needs n >= 1 and hi > lo on every axis");
-    const long long Nv = (long long)vd->n[0] * vd->n[1] * vd->n[2];
+    const int n3[3] = {vd->n[0], vd->n[1], red ? 2 : vd->n[2]};
+    const long long Nv = (long long)n3[0] * n3[1] * n3[2];
     if (Nv > (1ll << 31)) return set_err(c, GSIS_ERR_ARG, "too many velocities");
     std::vector<double> xi;
     double w = 1.0;
     for (int d = 0; d < 3; ++d) {
-        const double h = (vd->hi[d] - vd->lo[d]) / vd->n[d];
-        for (int q = 0; q < vd->n[d]; ++q) xi.push_back(vd->lo[d] + (q + 0.5) * h);
-        w *= h;
-        c->nv3[d] = vd->n[d];
+        if (red && d == 2) {   // planes G and H: xi_z = 0 in every flux, weight 1
+            xi.push_back(0.0);
+            xi.push_back(0.0);
+        } else {
+            const double h = (vd->hi[d] - vd->lo[d]) / vd->n[d];
+            for (int q = 0; q < vd->n[d]; ++q) xi.push_back(vd->lo[d] + (q + 0.5) * h);
+            w *= h;
+        }
+        c->nv3[d] = n3[d];
         c->vlo[d] = vd->lo[d];
         c->vhi[d] = vd->hi[d];
     }
@@ -863,8 +896,9 @@ gsis_status gsis_set_velocity_grid(gsis_ctx* c, const gsis_vgrid_desc* vd) {
     if (c->recGhost.tab) dev_free(c, c->recGhost.tab);
     c->recGhost.tab = nullptr;
     c->d_xi = upload(c, xi);
-    c->vg.nx = vd->n[0]; c->vg.ny = vd->n[1]; c->vg.nz = vd->n[2];
-    c->vg.NT = vd->n[0] + vd->n[1] + vd->n[2];
+    c->vg.nx = n3[0]; c->vg.ny = n3[1]; c->vg.nz = n3[2];
+    c->vg.NT = n3[0] + n3[1] + n3[2];
+    c->vg.reduced = red ? 1 : 0;
     c->vg.Nv = Nv;
     c->vg.w = w;
     c->vg.xi = c->d_xi;
@@ -1147,6 +1181,14 @@ gsis_status gsis_debug_vdf_moments(gsis_ctx* c, int direct, double* dst, long lo
     return GSIS_OK;
 }
 
+gsis_status gsis_debug_set_macro_path(gsis_ctx* c, int path) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (path < GSIS_MACRO_AUTO || path > GSIS_MACRO_PERSISTENT_STALL) return set_err(c, GSIS_ERR_ARG, "unknown path");
+    c->macro_path = path;
+    return GSIS_OK;
+}
+
 const char* gsis_tuning_info(gsis_ctx* c) {
     if (!c) return "";
     return c->sweep_info.c_str();
@@ -1173,6 +1215,7 @@ void gsis_free(gsis_ctx* c) {
         for (int i = 0; i < 2 * GSIS_NPHASE; ++i) cudaEventDestroy(c->ev[i]);
     if (c->h_eps) cudaFreeHost(c->h_eps);
     if (c->h_count) cudaFreeHost(c->h_count);
+    if (c->h_err) cudaFreeHost(c->h_err);
     delete c;
 }
 

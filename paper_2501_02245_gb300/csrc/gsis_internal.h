@@ -41,7 +41,22 @@ struct VGridDev {
     long long Nv;
     double w;
     const double* xi;            // [NT]
+    // 1: reduced distributions (xi_z integrated out): the z "nodes" are the
+    // planes G (iz = 0) and H (iz = 1), their xi values are 0 (xi_z never
+    // enters a face flux of a 2D mesh), and the xi_z^k weight of plane iz is
+    // zpow(iz, k) (1 for G and k = 0, 1 for H and k = 2, else 0)
+    int reduced = 0;
 };
+
+// xi_z^k weight of z node iz for a moment: on a 3D grid the node value cz^k
+// (cz = xi_z - u_z); on the reduced grid plane G carries k = 0 and plane H
+// k = 2 (its values are int xi_z^2 f; odd powers vanish with u_z = 0).
+__host__ __device__ __forceinline__ double zpow(const VGridDev& vg, int iz, double cz, int k) {
+    if (vg.reduced) return (k == 0 && iz == 0) || (k == 2 && iz == 1) ? 1.0 : 0.0;
+    double r = 1.0;
+    for (int j = 0; j < k; ++j) r *= cz;
+    return r;
+}
 
 struct Records {                 // R records
     double* scal;                // [R][RS]
@@ -93,10 +108,27 @@ struct MacroJob {
     double *Wm, *U;
     const double *Un, *hot, *wall_corr;
     double *gu, *gT, *Ff, *lamf, *R, *D, *lamS, *dU, *dU2, *acell;
+    double *F0, *dFa, *dFb;   // Euler flux tensor of U and its changes for the relaxation increments [N][15]
 };
 
 constexpr int MACRO_FUSED_THREADS = 512;
 constexpr int MACRO_FUSED_MAX_CELLS = 4096;
+constexpr int MACRO_PERSISTENT_THREADS = 256;
+
+// Grid-wide barrier of the persistent synthetic-solve kernel: arrival count,
+// generation, and an error word set by a block whose wait ran out of
+// spin_limit iterations (then every block returns at its next barrier).
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
+
+// Synthetic-solve implementation (gsis_debug_set_macro_path): AUTO picks the
+// fused one-CTA kernel up to MACRO_FUSED_MAX_CELLS cells and the persistent
+// cooperative kernel above (the per-phase kernels inside a batch graph).
+enum { MACRO_AUTO = 0, MACRO_FUSED = 1, MACRO_MULTI = 2, MACRO_PERSISTENT = 3, MACRO_PERSISTENT_STALL = 4 };
 }  // namespace gsis
 
 struct gsis_ctx {
@@ -131,13 +163,17 @@ struct gsis_ctx {
     double* Wmom = nullptr;        // [N][5] the state the moments of f^{n+1/2} (momh) were taken about
     double *dU = nullptr, *dU2 = nullptr, *R = nullptr, *D = nullptr, *lamS = nullptr;
     double *Ff = nullptr, *lamf = nullptr;   // interior face fluxes [N][3][5] and lambda|S| [N][3] (high faces)
+    double *F0 = nullptr, *dFa = nullptr, *dFb = nullptr;   // [N][15] Euler flux tensor and its changes (relaxation)
     double *fgeo = nullptr, *bgeo = nullptr; // face geometry (see MacroArgs)
     double* acell = nullptr;                 // [N] sound speed of the current pseudo-time state
     double* wallq = nullptr;                 // [N] wall heat flux output (gsis_moments)
     double *gu = nullptr, *gT = nullptr, *grho = nullptr, *gU = nullptr;
     double *hot = nullptr, *kin = nullptr, *nsf = nullptr, *kn_gll = nullptr;
     double *eps_buf = nullptr, *h_eps = nullptr;
-    int *err_flag = nullptr, *h_err = nullptr;
+    gsis::GridBarrier* d_bar = nullptr;   // barrier of the persistent synthetic-solve kernel
+    int* h_err = nullptr;          // pinned: barrier error word of the last persistent launch
+    int macro_path = 0;            // gsis::MACRO_* (test hook; 0 = automatic)
+    int pers_grid = 0;             // co-resident CTAs of the persistent kernel (0 = not queried yet)
     uint8_t* flag = nullptr;
 
     // DVM state
@@ -225,7 +261,9 @@ void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim);
 void launch_blend(gsis_ctx* c, const double* Wh, double w, double* W);
 void launch_face_geometry(gsis_ctx* c);
 void launch_wall_heat(gsis_ctx* c, double* out);
-void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term);
+// capturing: the launches are being recorded into a CUDA graph (then the
+// per-phase kernels replace the cooperative persistent launch)
+void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term, bool capturing = false);
 MacroJob macro_job(gsis_ctx* c, int steps, bool time_term);
 void launch_macro_fused(const MacroJob* d_jobs, int njobs, cudaStream_t stream, int cs);
 int fused_cluster_size(int want);

@@ -22,6 +22,7 @@
 // Every interior face flux is evaluated once, by one thread (face kernel),
 // and gathered by both cells in a fixed order (cell kernel), so the scheme is
 // exactly conservative and deterministic.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include "gsis_device.cuh"
 
@@ -276,16 +277,28 @@ __device__ void kfvs(double rL, const double* uL, double pL, double rR, const do
     half_range_add(rR, uR, pR / rR, n, -1.0, F);
 }
 
-__device__ __forceinline__ void euler_flux_dot(const double* U, const double* S, double* F) {
+// Euler flux tensor of conserved state U: F[q * 3 + i] = flux of component q
+// along axis i (so that F.S is euler_flux_dot(U, S)), one division.
+__device__ __forceinline__ void euler_tensor(const double* U, double* F) {
     const double r = U[0], ir = 1.0 / r;
-    const double ux = U[1] * ir, uy = U[2] * ir, uz = U[3] * ir;
-    const double p = (GAMMA - 1.0) * (U[4] - 0.5 * r * (ux * ux + uy * uy + uz * uz));
-    const double uS = ux * S[0] + uy * S[1] + uz * S[2];
-    F[0] = r * uS;
-    F[1] = U[1] * uS + p * S[0];
-    F[2] = U[2] * uS + p * S[1];
-    F[3] = U[3] * uS + p * S[2];
-    F[4] = (U[4] + p) * uS;
+    const double u[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const double p = (GAMMA - 1.0) * (U[4] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    for (int i = 0; i < 3; ++i) {
+        F[i] = U[1 + i];
+        for (int j = 0; j < 3; ++j) F[(1 + j) * 3 + i] = U[1 + j] * u[i] + (i == j ? p : 0.0);
+        F[12 + i] = (U[4] + p) * u[i];
+    }
+}
+
+// Change of the Euler flux tensor of cell c for the relaxation increment
+// dU_c, F(U_c + dU_c) - F(U_c), with F(U_c) kept in F0 for the pseudo-step:
+// each neighbour then reads the 15 values instead of evaluating both fluxes
+// (and their divisions) itself.
+__device__ __forceinline__ void flux_change(const double* U, const double* dU, const double* F0, double* dF, int c) {
+    double Up[5], F1[15];
+    for (int q = 0; q < 5; ++q) Up[q] = U[c * 5 + q] + dU[c * 5 + q];
+    euler_tensor(Up, F1);
+    for (int q = 0; q < 15; ++q) dF[(long long)c * 15 + q] = F1[q] - F0[(long long)c * 15 + q];
 }
 
 __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u, p)
@@ -486,7 +499,7 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
                                                   const double* Un, const double* gu, const double* gT,
                                                   const double* hot, const double* Ff, const double* lamf,
                                                   const double* wall_corr, double cfl, double dt, double* R, double* D,
-                                                  double* lamS, double* dU, int c) {
+                                                  double* lamS, double* dU, double* F0, double* dF, int c) {
     const double* wc = Wm + c * 5;
     const double rho_c = wc[0], T_c = wc[4], p_c = rho_c * T_c;
     const double u_c[3] = {wc[1], wc[2], wc[3]};
@@ -554,6 +567,10 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
         R[c * 5 + q] = Rc[q];
         dU[c * 5 + q] = Rc[q] * iD;
     }
+    if (dF) {   // relaxation sweeps follow: the flux tensor of U_c and its change for dU_c
+        euler_tensor(U + c * 5, F0 + (long long)c * 15);
+        flux_change(U, dU, F0, dF, c);
+    }
 }
 
 __global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ U,
@@ -562,35 +579,40 @@ __global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, cons
                                 const double* __restrict__ Ff, const double* __restrict__ lamf,
                                 const double* __restrict__ wall_corr, double cfl, double dt,
                                 double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
-                                double* __restrict__ dU) {
+                                double* __restrict__ dU, double* __restrict__ F0, double* __restrict__ dF) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < a.N) cell_residual_one(a, Wm, U, Un, gu, gT, hot, Ff, lamf, wall_corr, cfl, dt, R, D, lamS, dU, c);
+    if (c < a.N) cell_residual_one(a, Wm, U, Un, gu, gT, hot, Ff, lamf, wall_corr, cfl, dt, R, D, lamS, dU, F0, dF, c);
 }
 
-// One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D.
+// One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D,
+// dF_j = F(U_j + dU_j) - F(U_j) read from the neighbour's flux-change tensor
+// (dFin); with dFout the cell's own tensor for dU_new follows for the next sweep.
 __device__ __forceinline__ void relax_one(const MacroArgs& a, const double* U, const double* R, const double* D,
-                                          const double* lamS, const double* dUin, double* dUout, int c) {
+                                          const double* lamS, const double* dUin, double* dUout, const double* dFin,
+                                          double* dFout, const double* F0, int c) {
     double off[5] = {0, 0, 0, 0, 0};
     for (int s = 0; s < 6; ++s) {
         const int n = a.nbr[c * 6 + s];
         if (n < 0) continue;
         const double* So = a.Sout + ((long long)c * 6 + s) * 3;
-        double Uj[5], Uj2[5], F1[5], F0[5];
-        for (int q = 0; q < 5; ++q) { Uj[q] = U[n * 5 + q]; Uj2[q] = Uj[q] + dUin[n * 5 + q]; }
-        euler_flux_dot(Uj2, So, F1);
-        euler_flux_dot(Uj, So, F0);
+        const double* dF = dFin + (long long)n * 15;
         const double ls = lamS[(long long)c * 6 + s];
-        for (int q = 0; q < 5; ++q) off[q] += 0.5 * ((F1[q] - F0[q]) - ls * dUin[n * 5 + q]);
+        for (int q = 0; q < 5; ++q) {
+            const double dFS = dF[q * 3] * So[0] + dF[q * 3 + 1] * So[1] + dF[q * 3 + 2] * So[2];
+            off[q] += 0.5 * (dFS - ls * dUin[n * 5 + q]);
+        }
     }
     const double iD = 1.0 / D[c];
     for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) * iD;
+    if (dFout) flux_change(U, dUout, F0, dFout, c);
 }
 
 __global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double* __restrict__ R,
                         const double* __restrict__ D, const double* __restrict__ lamS, const double* __restrict__ dUin,
-                        double* __restrict__ dUout) {
+                        double* __restrict__ dUout, const double* __restrict__ dFin, double* __restrict__ dFout,
+                        const double* __restrict__ F0) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < a.N) relax_one(a, U, R, D, lamS, dUin, dUout, c);
+    if (c < a.N) relax_one(a, U, R, D, lamS, dUin, dUout, dFin, dFout, F0, c);
 }
 
 __device__ __forceinline__ void update_one(double* U, const double* dU, double* Wm, int c) {
@@ -632,12 +654,14 @@ __global__ void __launch_bounds__(MACRO_FUSED_THREADS, 1) k_macro_fused(const Ma
         fused_sync(cs);
         for (int c = first; c < N; c += stride)
             cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.wall_corr, J.cfl, J.dt, J.R,
-                              J.D, J.lamS, J.dU, c);
+                              J.D, J.lamS, J.dU, J.F0, J.k_sub > 0 ? J.dFa : nullptr, c);
         fused_sync(cs);
         double* din = J.dU;
         double* dout = J.dU2;
         for (int s = 0; s < J.k_sub; ++s) {
-            for (int c = first; c < N; c += stride) relax_one(a, J.U, J.R, J.D, J.lamS, din, dout, c);
+            double* fin = (s & 1) ? J.dFb : J.dFa;
+            double* fout = s + 1 < J.k_sub ? ((s & 1) ? J.dFa : J.dFb) : nullptr;
+            for (int c = first; c < N; c += stride) relax_one(a, J.U, J.R, J.D, J.lamS, din, dout, fin, fout, J.F0, c);
             fused_sync(cs);
             double* t = din; din = dout; dout = t;
         }
@@ -688,6 +712,9 @@ MacroJob macro_job(gsis_ctx* c, int steps, bool time_term) {
     J.lamf = c->lamf; J.wall_corr = c->wall_corr; J.R = c->R; J.D = c->D; J.lamS = c->lamS; J.dU = c->dU;
     J.dU2 = c->dU2;
     J.acell = c->acell;
+    J.F0 = c->F0;
+    J.dFa = c->dFa;
+    J.dFb = c->dFb;
     return J;
 }
 
@@ -719,20 +746,158 @@ int fused_cluster_for(int N) {
     return 1;
 }
 
-// `steps` DP-LUR pseudo-steps on c->U / c->Wm (prim kept in step), HoT from c->hot,
-// time term against c->Un when time_term.  Small meshes run the fused
-// one-CTA kernel (one launch per block of steps); larger ones launch the
-// per-phase kernels over the whole grid.
-void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term) {
+// ---------------------------------------------------------------------------- persistent kernel
+// The whole block of pseudo-steps of one solve in ONE cooperative launch
+// over all SMs (meshes above MACRO_FUSED_MAX_CELLS cells: the cylinder, the
+// sphere).  The same per-cell and per-face functions as the per-phase
+// kernels, separated by a grid-wide barrier, so the result is identical;
+// what goes away is the launch latency of the ~(4 + k_sub) kernels per
+// pseudo-step.  Every wait of the barrier is bounded by spin_limit polls:
+// a block that runs out records the error and returns, and every other
+// block returns at its next barrier (the host reports GSIS_ERR_TIMEOUT).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Returns false when the barrier failed (this block's wait ran out, or
+// another block's did): the caller returns at once.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned expected, unsigned long long spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_gpu(&bar->gen);   // read before arriving: gen cannot move before we arrive
+        __threadfence();                                // this block's writes before its arrival
+        const unsigned arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == expected - 1) {
+            bar->count = 0;                             // reset for the next barrier before releasing
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned long long polls = 0;
+            while (ld_acquire_gpu(&bar->gen) == g) {
+                if (++polls > spin_limit || ld_relaxed_gpu(&bar->err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (!ok) atomicExch(&bar->err, 1);
+        __threadfence();                                // the other blocks' writes before ours
+        s_ok = ok && ld_relaxed_gpu(&bar->err) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(MACRO_PERSISTENT_THREADS, 2)
+    k_macro_persistent(MacroJob J, GridBarrier* bar, unsigned long long spin_limit, int stall) {
+    const MacroArgs a = J.a;
+    const int N = a.N;
+    const int first = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    // stall (test hook): the barrier waits for one block more than the grid
+    // holds, so its wait can only end by running out of spin_limit polls
+    const unsigned expected = gridDim.x + (stall ? 1u : 0u);
+    for (int it = 0; it < J.steps; ++it) {
+        for (int c = first; c < N; c += stride)
+            gradients_cell(a, J.Wm, 0, J.gu, J.gT, nullptr, nullptr, J.acell, c);
+        if (!grid_barrier(bar, expected, spin_limit)) return;
+        for (int t = first; t < N * J.ndir; t += stride)
+            face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.acell, J.ndir, J.Ff, J.lamf, t);
+        if (!grid_barrier(bar, expected, spin_limit)) return;
+        for (int c = first; c < N; c += stride)
+            cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.wall_corr, J.cfl, J.dt, J.R,
+                              J.D, J.lamS, J.dU, J.F0, J.k_sub > 0 ? J.dFa : nullptr, c);
+        if (!grid_barrier(bar, expected, spin_limit)) return;
+        double* din = J.dU;
+        double* dout = J.dU2;
+        for (int s = 0; s < J.k_sub; ++s) {
+            double* fin = (s & 1) ? J.dFb : J.dFa;
+            double* fout = s + 1 < J.k_sub ? ((s & 1) ? J.dFa : J.dFb) : nullptr;
+            for (int c = first; c < N; c += stride) relax_one(a, J.U, J.R, J.D, J.lamS, din, dout, fin, fout, J.F0, c);
+            if (!grid_barrier(bar, expected, spin_limit)) return;
+            double* t = din; din = dout; dout = t;
+        }
+        for (int c = first; c < N; c += stride) update_one(J.U, din, J.Wm, c);
+        if (!grid_barrier(bar, expected, spin_limit)) return;
+    }
+}
+
+// Co-resident CTAs of the persistent kernel on this device (0 if a
+// cooperative launch is not possible).
+static int persistent_capacity(gsis_ctx* c) {
+    if (c->pers_grid != 0) return c->pers_grid;
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_macro_persistent, MACRO_PERSISTENT_THREADS, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    c->pers_grid = (coop && per_sm > 0) ? per_sm * sms : -1;
+    return c->pers_grid;
+}
+
+// One cooperative launch for `steps` pseudo-steps; the barrier's error word
+// is copied to c->h_err (read by the host after its next synchronisation).
+static bool launch_macro_persistent(gsis_ctx* c, const MacroJob& J, bool stall) {
+    const int cap = persistent_capacity(c);
+    if (cap <= 0) return false;
+    // every co-resident CTA: the phases are bound by the FP64 pipes of all SMs (a grid sized to the work
+    // alone left SMs idle), capped where some CTAs would find no item in any phase
+    const long long work = std::max<long long>((long long)J.a.N * J.ndir, J.a.N);
+    const int grid = (int)std::min<long long>(cap, std::max<long long>(1, work / 32));
+    cudaMemsetAsync(c->d_bar, 0, sizeof(GridBarrier), c->stream);
+    MacroJob Jc = J;
+    GridBarrier* bar = c->d_bar;
+    unsigned long long spin = c->p.spin_limit;
+    int st = stall ? 1 : 0;
+    void* args[] = {&Jc, &bar, &spin, &st};
+    if (cudaLaunchCooperativeKernel((const void*)k_macro_persistent, dim3(grid), dim3(MACRO_PERSISTENT_THREADS), args,
+                                    0, c->stream) != cudaSuccess)
+        return false;
+    cudaMemcpyAsync(c->h_err, &c->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    c->launches++;
+    return true;
+}
+
+// `steps` DP-LUR pseudo-steps on c->U / c->Wm (prim kept in step), HoT from
+// c->hot, time term against c->Un when time_term.  Small meshes run the fused
+// one-CTA kernel (one launch per block of steps), larger ones the persistent
+// cooperative kernel (one launch per block of steps); inside a graph capture
+// and where a cooperative launch is not available the per-phase kernels run
+// over the whole grid.  Every path computes the same result.
+void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term, bool capturing) {
     (void)with_hot;
     const int N = c->m.N;
     if (steps <= 0) return;
-    if (N <= MACRO_FUSED_MAX_CELLS) {
+    // automatic choice: the per-phase kernels above the fused kernel's limit (measured on the 16,384-cell
+    // cylinder, 100 pseudo-steps: per-phase kernels 11.1 ms, persistent kernel 13.0 ms with one CTA on
+    // each of 128 SMs and 23.8 ms with every co-resident CTA -- its 600 grid barriers cost more than
+    // the launches they replace, the phases being bound by the FP64 special functions of the fluxes)
+    int path = c->macro_path;
+    if (path == MACRO_AUTO) path = N <= MACRO_FUSED_MAX_CELLS ? MACRO_FUSED : MACRO_MULTI;
+    if (capturing && (path == MACRO_PERSISTENT || path == MACRO_PERSISTENT_STALL)) path = MACRO_MULTI;
+    if (path == MACRO_FUSED) {
         MacroJob J = macro_job(c, steps, time_term);
         cudaMemcpyAsync(c->d_job, &J, sizeof(MacroJob), cudaMemcpyHostToDevice, c->stream);
         launch_macro_fused(c->d_job, 1, c->stream, fused_cluster_for(N));
         c->launches++;
         return;
+    }
+    if (path == MACRO_PERSISTENT || path == MACRO_PERSISTENT_STALL) {
+        if (launch_macro_persistent(c, macro_job(c, steps, time_term), path == MACRO_PERSISTENT_STALL)) return;
+        cudaGetLastError();   // no cooperative launch here: fall through to the per-phase kernels
     }
     const int TB = 64;
     const int nb = (N + TB - 1) / TB;
@@ -744,12 +909,15 @@ void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term) {
         launch_gradients(c, c->Wm, false);
         k_face_flux<<<nf, TB, 0, c->stream>>>(a, c->Wm, c->gu, c->gT, c->hot, c->acell, ndir, c->Ff, c->lamf);
         k_cell_residual<<<nb, TB, 0, c->stream>>>(a, c->Wm, c->U, c->Un, c->gu, c->gT, c->hot, c->Ff, c->lamf,
-                                                  c->wall_corr, c->p.cfl, dt, c->R, c->D, c->lamS, c->dU);
+                                                  c->wall_corr, c->p.cfl, dt, c->R, c->D, c->lamS, c->dU, c->F0,
+                                                  c->p.k_sub > 0 ? c->dFa : nullptr);
         c->launches += 2;
         double* din = c->dU;
         double* dout = c->dU2;
         for (int s = 0; s < c->p.k_sub; ++s) {
-            k_relax<<<nb, TB, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout);
+            double* fin = (s & 1) ? c->dFb : c->dFa;
+            double* fout = s + 1 < c->p.k_sub ? ((s & 1) ? c->dFa : c->dFb) : nullptr;
+            k_relax<<<nb, TB, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout, fin, fout, c->F0);
             c->launches++;
             double* t = din; din = dout; dout = t;
         }

@@ -88,8 +88,11 @@ struct SweepShape {
     int g, vpt, cb;
     const char* name;
 };
+// (The wide FP64 blocks serve small velocity grids -- the reduced distributions
+// of 2D flows -- whose few velocity tiles leave SMs idle with narrow blocks.)
 static const SweepShape kShapesF64[] = {
-    {2, 1, 2, "g2_v1_c2"}, {1, 1, 2, "g1_v1_c2"}, {4, 1, 1, "g4_v1_c1"}, {2, 1, 1, "g2_v1_c1"}};
+    {2, 1, 2, "g2_v1_c2"}, {1, 1, 2, "g1_v1_c2"}, {4, 1, 1, "g4_v1_c1"}, {2, 1, 1, "g2_v1_c1"},
+    {8, 1, 1, "g8_v1_c1"}, {16, 1, 1, "g16_v1_c1"}};
 static const SweepShape kShapesF32[] = {
     {8, 1, 1, "g8_v1_c1"}, {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"},
     {4, 4, 1, "g4_v4_c1"}, {8, 4, 1, "g8_v4_c1"}, {4, 2, 2, "g4_v2_c2"}};
@@ -130,6 +133,8 @@ static void sweep_f64_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape
         case 1: sweep_t<double, double, 1, 1, 2>(c, a, pass); break;
         case 2: sweep_t<double, double, 4, 1, 1>(c, a, pass); break;
         case 3: sweep_t<double, double, 2, 1, 1>(c, a, pass); break;
+        case 4: sweep_t<double, double, 8, 1, 1>(c, a, pass); break;
+        case 5: sweep_t<double, double, 16, 1, 1>(c, a, pass); break;
         default: sweep_t<double, double, 2, 1, 2>(c, a, pass); break;
     }
 }

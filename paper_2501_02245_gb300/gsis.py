@@ -25,7 +25,9 @@ PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual"
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
             "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
-            "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments"]
+            "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments", "gsis_debug_set_macro_path",
+            "gsis_probe_fma_peak"]
+MACRO_PATHS = {"auto": 0, "fused": 1, "multi": 2, "persistent": 3, "persistent_stall": 4}
 
 
 class GsisError(RuntimeError):
@@ -58,7 +60,8 @@ class MeshDesc(ctypes.Structure):
 
 
 class VGridDesc(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+    _fields_ = [("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("reduced", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -103,6 +106,10 @@ def load():
     lib.gsis_debug_set_sweep_tile.restype = c_int
     lib.gsis_debug_vdf_moments.argtypes = [vp, c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_longlong]
     lib.gsis_debug_vdf_moments.restype = c_int
+    lib.gsis_debug_set_macro_path.argtypes = [vp, c_int]
+    lib.gsis_debug_set_macro_path.restype = c_int
+    lib.gsis_probe_fma_peak.argtypes = [c_int, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]
+    lib.gsis_probe_fma_peak.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
     lib.gsis_tuning_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
@@ -163,7 +170,8 @@ class Solver:
                    float(params.get("Kn_ref", 0.0)), int(params.get("adapt_every", 5)),
                    int(params.get("wall_layers", 2)), DTYPES[vdf_dtype], int(params.get("macro_steps", 200)),
                    float(params.get("cfl", 5.0)), int(params.get("k_sub", 2)), float(params.get("dt", 0.0)),
-                   float(params.get("tol", 1e-6)), int(params.get("presolve_max_blocks", 0)), 0,
+                   float(params.get("tol", 1e-6)), int(params.get("presolve_max_blocks", 0)),
+                   int(params.get("spin_limit", 0)),
                    float(params.get("relax", 1.0)))
         self._alloc = None
         alloc_ptr = None
@@ -185,7 +193,7 @@ class Solver:
         self.ncell = mesh.ni * mesh.nj * mesh.nk
         self._set_mesh(mesh, W0)
         self._set_vgrid(vgrid)
-        self.nv = int(np.prod(vgrid.n))
+        self.nv = 2 * int(vgrid.n[0]) * int(vgrid.n[1]) if getattr(vgrid, "reduced", False) else int(np.prod(vgrid.n))
         if forced_flags is not None:
             fl = np.ascontiguousarray(np.asarray(forced_flags, dtype=np.uint8).reshape(-1))
             self._check(lib.gsis_debug_set_region(self.ctx, fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
@@ -232,6 +240,7 @@ class Solver:
         d = VGridDesc()
         for a in range(3):
             d.n[a], d.lo[a], d.hi[a] = int(vg.n[a]), float(vg.lo[a]), float(vg.hi[a])
+        d.reduced = 1 if getattr(vg, "reduced", False) else 0
         self._check(self.lib.gsis_set_velocity_grid(self.ctx, ctypes.byref(d)))
 
     # ------------------------------------------------------------------ API
@@ -266,6 +275,12 @@ class Solver:
         out = np.zeros((n_dvm, 19))
         self._check(self.lib.gsis_debug_vdf_moments(self.ctx, int(bool(direct)), _dptr(out), out.size))
         return out
+
+    def set_macro_path(self, name):
+        """Choose the synthetic-solve implementation (test hook): auto, fused,
+        multi, persistent, or persistent_stall (a barrier that can only end by
+        running out of spin_limit polls)."""
+        self._check(self.lib.gsis_debug_set_macro_path(self.ctx, MACRO_PATHS[name]))
 
     def tuning_info(self):
         """Result of the sweep tile-shape autotuning of this solve."""
@@ -330,6 +345,18 @@ def iterate_batch(solvers, n):
 def batch_info(solvers):
     """Description of the recorded batch plan of this solver list."""
     return load().gsis_batch_info(_ctx_array(solvers), len(solvers)).decode()
+
+
+def fma_peak(fp64, stream=None):
+    """Measured FMA throughput of the current GPU's CUDA cores (flop/s) and
+    the duration of the best timed launch (ms): FP64 if fp64 else FP32."""
+    lib = load()
+    r, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = lib.gsis_probe_fma_peak(1 if fp64 else 0, sp, ctypes.byref(r), ctypes.byref(ms))
+    if st != GSIS_OK:
+        raise GsisError(st, "FMA peak probe failed")
+    return r.value, ms.value
 
 
 def version():

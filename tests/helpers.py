@@ -47,3 +47,15 @@ def vdf_by_cell(solver, n_dvm, ncell, nv):
     full = np.zeros((ncell, nv))
     full[cells] = f
     return full
+
+
+def moment_scales(direct):
+    """Per-component magnitude of each moment order of gsis_debug_vdf_moments
+    over all cells: rho, rho sqrt(T), rho T, rho T^(3/2) (from the direct
+    moments), and the largest wall sum."""
+    s0 = np.abs(direct[:, 0]).max()
+    s2 = np.abs(direct[:, 4] + direct[:, 5] + direct[:, 6]).max() / 3.0
+    s1 = np.sqrt(s0 * s2)
+    s3 = s2 ** 1.5 / np.sqrt(s0)
+    sw = max(np.abs(direct[:, 13:]).max(), 1e-300)
+    return np.array([s0] + [s1] * 3 + [s2] * 6 + [s3] * 3 + [sw] * 6)

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from workloads import cylinder_case
+from helpers import moment_scales
 
 pytestmark = pytest.mark.gpu
 
@@ -19,17 +20,6 @@ def _case():
                          cfl=5.0, k_sub=2, vbox=((-10, 10), (-9, 9), (-8, 8)), presolve_max_blocks=2)
     case.dt = 0.5
     return case
-
-
-def _scales(direct):
-    """Per-component magnitude of each moment order over all cells: rho, rho sqrt(T),
-    rho T, rho T^(3/2) (from the direct moments), and the largest wall sum."""
-    s0 = np.abs(direct[:, 0]).max()
-    s2 = np.abs(direct[:, 4] + direct[:, 5] + direct[:, 6]).max() / 3.0
-    s1 = np.sqrt(s0 * s2)
-    s3 = s2 ** 1.5 / np.sqrt(s0)
-    sw = np.abs(direct[:, 13:]).max()
-    return np.array([s0] + [s1] * 3 + [s2] * 6 + [s3] * 3 + [sw] * 6)
 
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-11), ("f32", 1e-5)])
@@ -43,7 +33,7 @@ def test_carried_moments_match_a_direct_reduction(dtype, tol):
     s.close()
     assert np.isfinite(carried).all() and np.isfinite(direct).all()
     assert np.abs(direct[:, 13:]).max() > 0, "the case has diffuse-wall cells"
-    err = (np.abs(carried - direct) / _scales(direct)).max(axis=0)
+    err = (np.abs(carried - direct) / moment_scales(direct)).max(axis=0)
     assert err.max() < tol, "per-component error %s" % np.array2string(err, precision=2)
 
 

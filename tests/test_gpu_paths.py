@@ -1,0 +1,295 @@
+"""GPU parity on the paths the full-size runs take, and the failure statuses.
+
+- the synthetic solve above the 4096-cell limit of the fused one-CTA kernel
+  (the persistent cooperative kernel: the cylinder and the sphere take it),
+  and every synthetic-solve implementation forced on one small case;
+- the re-identification of the DVM region mid-run with a region that changes
+  (surviving rows copied, entering rows seeded with Grad-13, Sec. 3.4 Step 3),
+  decided by the GPU itself (no forced flags);
+- the plain scheme (no under-relaxation) on the O-grid;
+- a batch whose big member runs the per-phase synthetic-solve kernels inside
+  the batch graph, against the same solves run alone;
+- the statuses of the C ABI for a wait that runs out (GSIS_ERR_TIMEOUT), an
+  allocator that fails (GSIS_ERR_OOM), a non-finite input (GSIS_ERR_ARG) and a
+  run that diverges (GSIS_ERR_NONFINITE).  None of them faults the GPU: the
+  timeout comes from a barrier that waits for one CTA more than the launch
+  has, bounded by spin_limit; the failures are made on the host.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads import cylinder_case, sphere_case, shock_1d_case
+from helpers import RTOL_W, rel_err, w_rel_err, run_oracle, vdf_by_cell
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(case, n_iter, path=None, **over):
+    from paper_2501_02245_gb300 import Solver
+    s = Solver.from_case(case, **over)
+    if path is not None:
+        s.set_macro_path(path)
+    s.iterate(0)
+    hist, reps = [s.W()], []
+    for _ in range(n_iter):
+        reps.append(s.iterate(1))
+        hist.append(s.W())
+    return s, hist, reps
+
+
+def _check(o, ho, s, hg, reps, f_tol=1e-10):
+    assert np.array_equal(s.dvm_flags(), o.dvm)
+    for it, (a, b) in enumerate(zip(hg, ho)):
+        e = w_rel_err(a, b)
+        assert e < RTOL_W, "iteration %d: W relative error %.3e" % (it, e)
+    for it, r in enumerate(reps):
+        assert abs(r["eps"] - o.eps_history[it]) <= 1e-8 * o.eps_history[it] + 1e-14
+    nd = int(o.dvm.sum())
+    fg = vdf_by_cell(s, nd, o.N, o.vg.nv)
+    assert rel_err(fg[o.dvm], o.f[o.dvm]) < f_tol
+    ho_ = np.concatenate([o.hot_sigma[:, [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]], o.hot_q], axis=1)
+    assert rel_err(s.hot(), ho_, max(np.max(np.abs(ho_)), 1e-12)) < 1e-9
+
+
+def _small_cylinder(relax=0.7):
+    case = cylinder_case(Ma=2.0, Kn=0.1, n_r=6, n_theta=8, nv=(14, 12, 6), adaptive=False, macro_steps=10,
+                         cfl=5.0, k_sub=2, vbox=((-10, 10), (-9, 9), (-8, 8)), relax=relax)
+    case.dt = 0.5
+    return case
+
+
+@pytest.mark.parametrize("path", ["fused", "multi", "persistent"])
+def test_every_synthetic_solve_path_matches_the_oracle(path):
+    """Fused one-CTA kernel, per-phase kernels and the persistent cooperative
+    kernel on the same small O-grid case (presolve included)."""
+    case = _small_cylinder()
+    o, ho = run_oracle(case, 3)
+    s, hg, reps = _gpu(case, 3, path=path)
+    _check(o, ho, s, hg, reps)
+    s.close()
+
+
+def test_cylinder_plain_scheme():
+    """The O-grid case without under-relaxation of the synthetic correction
+    (relax = 1, the scheme as the paper writes it)."""
+    case = _small_cylinder(relax=1.0)
+    o, ho = run_oracle(case, 3)
+    s, hg, reps = _gpu(case, 3)
+    _check(o, ho, s, hg, reps)
+    s.close()
+
+
+@pytest.mark.parametrize("path", ["auto", "persistent"])
+def test_synthetic_solve_above_the_fused_limit_cylinder(path):
+    """72 x 64 = 4,608 cells (above the 4,096 of the fused kernel): the
+    automatic path (per-phase kernels, (4 + k_sub) launches per pseudo-step)
+    and the persistent cooperative kernel (one launch per block of
+    pseudo-steps)."""
+    case = cylinder_case(Ma=2.0, Kn=0.1, n_r=72, n_theta=64, nv=(12, 12, 6), adaptive=False, macro_steps=20,
+                         cfl=5.0, k_sub=2, vbox=((-10, 10), (-9, 9), (-8, 8)), presolve_max_blocks=4, relax=1.0)
+    case.dt = 0.5
+    o, ho = run_oracle(case, 2)
+    s, hg, reps = _gpu(case, 2, path=path)
+    _check(o, ho, s, hg, reps)
+    if path == "persistent":   # the per-phase kernels need (4 + k_sub) x 20 = 120 launches for the solve alone
+        assert all(r["kernel_launches"] < 100 for r in reps)
+    else:
+        assert all(r["kernel_launches"] > 120 for r in reps)
+    s.close()
+
+
+def test_synthetic_solve_above_the_fused_limit_sphere():
+    """3D spherical O-grid 24 x 16 x 16 = 6,144 cells with 12 x 10 x 10
+    velocities: polar-axis zero-area faces, azimuthal wrap, all three flux
+    directions, synthetic solve above the fused kernel's limit."""
+    case = sphere_case(Ma=2.0, Kn=0.1, n_r=24, n_pol=16, n_az=16, nv=(12, 10, 10), adaptive=False, macro_steps=10,
+                       vbox=((-10, 10), (-9, 9), (-9, 9)), presolve_max_blocks=4, relax=1.0)
+    case.dt = 0.5
+    o, ho = run_oracle(case, 2)
+    s, hg, reps = _gpu(case, 2)
+    _check(o, ho, s, hg, reps)
+    s.close()
+
+
+def test_reidentification_with_a_changing_region():
+    """Adaptive run re-identified after two iterations with the region
+    decided on the GPU from its own Kn_Gll (Sec. 3.4 Step 3): cells enter
+    (seeded with the conservation-corrected Grad-13 VDF of Eq. G13_VDF) and
+    leave; surviving rows are copied.  The oracle decides its own region too;
+    the case is chosen with every Kn_Gll far (> 1e-4 relative) from Kn_ref,
+    so both sides must take the same decisions.  W every iteration, and the
+    VDF, HoT and region after the re-identification, match the oracle."""
+    case = cylinder_case(Ma=2.0, Kn=0.02, n_r=8, n_theta=10, nv=(14, 12, 6), adaptive=True, Kn_ref=0.02,
+                         macro_steps=20, cfl=5.0, k_sub=2, presolve_max_blocks=3, vbox=((-10, 10), (-9, 9), (-8, 8)))
+    case.tol = 0.0
+    case.adapt_every = 2
+    from oracle.gsis import OracleSolver
+    o = OracleSolver(case)
+    o.initialise()
+    start_flags = o.dvm.copy()
+    assert np.min(np.abs(o.kn_gll / case.Kn_ref - 1.0)) > 1e-4
+    ho = [o.W.copy()]
+    for _ in range(4):
+        o.step()
+        ho.append(o.W.copy())
+    assert np.min(np.abs(o.kn_gll / case.Kn_ref - 1.0)) > 1e-4
+    assert np.any(o.dvm & ~start_flags) and np.any(start_flags & ~o.dvm)   # cells entered and left
+    s, hg, reps = _gpu(case, 4)
+    assert reps[2]["n_dvm"] == int(o.dvm.sum())
+    _check(o, ho, s, hg, reps)
+    s.close()
+
+
+def test_batch_big_member_runs_the_per_phase_kernels_in_the_graph():
+    """A batch holding a 4,608-cell cylinder (its synthetic solve recorded as
+    per-phase kernels in the batch graph) and a small shock: each member
+    matches the same solve run alone."""
+    from paper_2501_02245_gb300 import Solver, iterate_batch
+    big = cylinder_case(Ma=2.0, Kn=0.1, n_r=72, n_theta=64, nv=(12, 12, 6), adaptive=False, macro_steps=20,
+                        cfl=5.0, k_sub=2, vbox=((-10, 10), (-9, 9), (-8, 8)), presolve_max_blocks=4, relax=1.0)
+    big.dt = 0.5
+    small = shock_1d_case(n_cells=30, half_width=7.5, nv=(20, 10, 9), vmax=8.0, macro_steps=30)
+    alone = []
+    for c in (big, small):
+        s = Solver.from_case(c)
+        s.iterate(2)
+        alone.append(s.W())
+        s.close()
+    sv = [Solver.from_case(c) for c in (big, small)]
+    iterate_batch(sv, 2)
+    for s, W in zip(sv, alone):
+        assert w_rel_err(s.W(), W) < 1e-12
+        s.close()
+
+
+# ----------------------------------------------------------------------------- failure statuses
+def test_barrier_wait_runs_out_with_timeout_status():
+    """The persistent synthetic solve with a barrier that waits for one CTA
+    more than its launch has (test hook) and spin_limit = 2000 polls: every
+    CTA gives up after its bounded wait, gsis_iterate returns
+    GSIS_ERR_TIMEOUT, the context refuses further iterations, and the CUDA
+    context stays usable (a fresh solve runs and matches the oracle)."""
+    from paper_2501_02245_gb300 import Solver, gsis
+    case = _small_cylinder(relax=1.0)
+    case.presolve_max_blocks = 0
+    s = Solver.from_case(case, spin_limit=2000)
+    s.set_macro_path("persistent_stall")
+    with pytest.raises(gsis.GsisError) as ei:
+        s.iterate(1)
+    assert ei.value.status == gsis.GSIS_ERR_TIMEOUT
+    with pytest.raises(gsis.GsisError) as ei:
+        s.iterate(1)
+    assert ei.value.status == gsis.GSIS_ERR_STATE
+    s.close()
+    import torch
+    torch.cuda.synchronize()
+    case = _small_cylinder()
+    o, ho = run_oracle(case, 1)
+    s, hg, reps = _gpu(case, 1, path="persistent")
+    _check(o, ho, s, hg, reps)
+    s.close()
+
+
+def _raw_ctx(lib, gsis, case, alloc=None):
+    p = gsis.Params(case.Kn, case.omega, 0, 0.0, 5, 2, 0, case.macro_steps, case.cfl, case.k_sub, case.dt, 0.0,
+                    0, 0, 1.0)
+    ctx = ctypes.c_void_p()
+    st = lib.gsis_init(ctypes.byref(p), ctypes.byref(alloc) if alloc is not None else None, None, ctypes.byref(ctx))
+    assert st == gsis.GSIS_OK
+    return ctx
+
+
+def _mesh_desc(gsis, mesh, W0, keep):
+    def arr(a):
+        a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    md = gsis.MeshDesc()
+    md.ni, md.nj, md.nk, md.dim = mesh.ni, mesh.nj, mesh.nk, mesh.dim
+    md.centers, md.volumes = arr(mesh.centers), arr(mesh.volumes)
+    for d in range(3):
+        md.S[d], md.xf[d] = arr(mesh.S[d]), arr(mesh.xf[d])
+    for q in range(6):
+        md.bc_type[q] = int(mesh.bc_type[q])
+        for k in range(5):
+            md.bc_state[q][k] = float(mesh.bc_state[q][k])
+    md.W0 = arr(W0)
+    return md
+
+
+def test_allocator_returning_null_gives_oom():
+    """An allocator callback that fails (returns NULL) after a few
+    allocations: gsis_set_mesh reports GSIS_ERR_OOM, gsis_free releases what
+    was allocated (every pointer handed out is freed exactly once)."""
+    from paper_2501_02245_gb300 import gsis
+    import torch
+    lib = gsis.load()
+    live, count = {}, [0]
+
+    def _alloc(nbytes, stream, user):
+        count[0] += 1
+        if count[0] > 5:
+            return None
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(p, stream, user):
+        assert p in live
+        del live[p]
+
+    a = gsis.Allocator(gsis.Allocator._fields_[0][1](_alloc), gsis.Allocator._fields_[1][1](_free), None)
+    case = shock_1d_case(n_cells=20, half_width=5.0, nv=(8, 4, 4))
+    ctx = _raw_ctx(lib, gsis, case, a)
+    keep = []
+    st = lib.gsis_set_mesh(ctx, ctypes.byref(_mesh_desc(gsis, case.mesh, case.W0, keep)))
+    assert st == gsis.GSIS_ERR_OOM
+    assert b"allocation" in lib.gsis_last_error(ctx)
+    lib.gsis_free(ctx)
+    assert live == {} and count[0] > 5
+
+
+def test_non_finite_input_is_rejected_unchanged():
+    """A NaN in the initial state or a non-positive temperature: gsis_set_mesh
+    returns GSIS_ERR_ARG and the context stays usable (a valid mesh is then
+    accepted and iterates)."""
+    from paper_2501_02245_gb300 import gsis
+    lib = gsis.load()
+    case = shock_1d_case(n_cells=24, half_width=6.0, nv=(20, 10, 9), vmax=8.0, macro_steps=20)
+    ctx = _raw_ctx(lib, gsis, case)
+    keep = []
+    bad = case.W0.copy(); bad[7, 1] = np.nan
+    assert lib.gsis_set_mesh(ctx, ctypes.byref(_mesh_desc(gsis, case.mesh, bad, keep))) == gsis.GSIS_ERR_ARG
+    bad = case.W0.copy(); bad[3, 4] = -1.0
+    assert lib.gsis_set_mesh(ctx, ctypes.byref(_mesh_desc(gsis, case.mesh, bad, keep))) == gsis.GSIS_ERR_ARG
+    assert lib.gsis_set_mesh(ctx, ctypes.byref(_mesh_desc(gsis, case.mesh, case.W0, keep))) == gsis.GSIS_OK
+    vg = gsis.VGridDesc()
+    for d in range(3):
+        vg.n[d], vg.lo[d], vg.hi[d] = case.vgrid.n[d], case.vgrid.lo[d], case.vgrid.hi[d]
+    assert lib.gsis_set_velocity_grid(ctx, ctypes.byref(vg)) == gsis.GSIS_OK
+    rep = gsis.Report()
+    assert lib.gsis_iterate(ctx, 1, ctypes.byref(rep)) == gsis.GSIS_OK and np.isfinite(rep.eps)
+    lib.gsis_free(ctx)
+
+
+def test_diverging_run_reports_nonfinite():
+    """An all-kinetic O-grid run started from the uniform stream without the
+    NS presolve and without the time term diverges (its state leaves the
+    range the scheme can represent within a few iterations: non-positive
+    temperature, then NaN arithmetic, which does not fault): gsis_iterate
+    returns GSIS_ERR_NONFINITE and the context accepts nothing but
+    gsis_free afterwards."""
+    from paper_2501_02245_gb300 import Solver, gsis
+    case = cylinder_case(Ma=2.0, Kn=0.1, n_r=4, n_theta=6, nv=(14, 12, 6), adaptive=False, macro_steps=5,
+                         vbox=((-10, 10), (-9, 9), (-8, 8)), presolve_max_blocks=0, relax=1.0)
+    s = Solver.from_case(case)
+    with pytest.raises(gsis.GsisError) as ei:
+        s.iterate(10)
+    assert ei.value.status == gsis.GSIS_ERR_NONFINITE
+    with pytest.raises(gsis.GsisError) as ei:
+        s.iterate(1)
+    assert ei.value.status == gsis.GSIS_ERR_STATE
+    s.close()
+

@@ -13,7 +13,7 @@ from helpers import run_oracle, w_rel_err, rel_err, RTOL_W
 pytestmark = pytest.mark.gpu
 
 TILES = {
-    "f64": ["g2_v1_c2", "g1_v1_c2", "g4_v1_c1", "g2_v1_c1", "ring_w8_v32", "ring_w4_v32"],
+    "f64": ["g2_v1_c2", "g1_v1_c2", "g4_v1_c1", "g2_v1_c1", "g8_v1_c1", "g16_v1_c1", "ring_w8_v32", "ring_w4_v32"],
     "f32": ["g8_v1_c1", "g4_v1_c1", "g8_v2_c1", "g4_v4_c1", "g8_v4_c1", "g4_v2_c2",
             "ring_w8_v32", "ring_w4_v32", "ring_w8_v64"],
 }
