@@ -96,8 +96,20 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
     double part[3][6];
     for (int d = 0; d < 3; ++d)
         for (int k = 0; k < 6; ++k) part[d][k] = 0.0;
+    // reduced grid: the z "nodes" are the planes G (p = 0) and H (p = 1); integrating the separable form
+    // over xi_z (u_z = r_z = 0 and no xz / yz stress in a flow without z dependence) leaves the same form
+    // with the plane values E_z = int xi_z^{2p} e_z dxi_z = sqrt(2 pi T) (1, T), C_z = 0 and
+    // C2_z = (2p + 1) T, the ratio of the Gaussian moments 3T^2 / T and T / 1
+    const double sq2piT = sqrt(2.0 * PI * T);
     for (int idx = lane; idx < NT; idx += 32) {
         const int d = idx < nx ? 0 : (idx < nx + ny ? 1 : 2);
+        if (vg.reduced && d == 2) {
+            const int p = idx - nx - ny;
+            tab[idx] = p ? sq2piT * T : sq2piT;
+            tab[2 * NT + idx] = 0.0;
+            tab[3 * NT + idx] = p ? 3.0 * T : T;
+            continue;
+        }
         const double c = vg.xi[idx] - s.u[d];
         const double e = exp(-(c * c) / (2.0 * T));
         tab[idx] = e;
@@ -113,6 +125,10 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
     double Cs[3][6];
     for (int d = 0; d < 3; ++d)
         for (int k = 0; k < 6; ++k) Cs[d][k] = warp_sum(part[d][k]);
+    if (vg.reduced) {   // exact xi_z integrals int c_z^k e_z dxi_z of the Gaussian (k = 0..5)
+        const double zk[6] = {1.0, 0.0, T, 0.0, 3.0 * T * T, 0.0};
+        for (int k = 0; k < 6; ++k) Cs[2][k] = sq2piT * zk[k];
+    }
 
     double coef[12];   // p0', p'(3), P2'(diag 3), alpha(5)
     // the 5 right-hand sides and 25 matrix entries of the correction system,
@@ -171,7 +187,7 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
     for (int idx = lane; idx < NT; idx += 32) {
         const int d = idx < nx ? 0 : (idx < nx + ny ? 1 : 2);
         const double c = tab[2 * NT + idx];
-        tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * (c * c);
+        tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * tab[3 * NT + idx];   // C2 = c^2 (plane value if reduced)
         tab[4 * NT + idx] = s.r[d] * c;
         if (d == 0) tab[idx] *= A;
         if (out.tabf) {
@@ -356,12 +372,14 @@ __global__ void k_wall_den(int N, const int* __restrict__ side_bc, const double*
             if (!(xn > 0.0)) {
                 const double m = eval_rec(sc, tb, vg.NT, vg.nx, vg.ny, ix, iy, iz);
                 const double g = xn * m;
-                acc[0] += -g;
-                acc[1] += g;
-                acc[2] += g * x0;
-                acc[3] += g * x1;
-                acc[4] += g * x2;
-                acc[5] += g * 0.5 * (x0 * x0 + x1 * x1 + x2 * x2);
+                double psi[5];
+                psi_node(vg, x0, x1, x2, iz, psi);
+                acc[0] += -g * psi[0];
+                acc[1] += g * psi[0];
+                acc[2] += g * psi[1];
+                acc[3] += g * psi[2];
+                acc[4] += g * psi[3];
+                acc[5] += g * psi[4];
             }
         }
         block_sum<6>(acc, sm);

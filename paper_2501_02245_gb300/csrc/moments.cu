@@ -62,6 +62,13 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
         const int jy = nx + iy, jz = nx + ny + iz;
         const double xy = vg.xi[jy], xz = vg.xi[jz];
         const double cy = xy - uy, cz = xz - uz;
+        // plane weights of c_z^k on the reduced grid; the wall-flux sums below carry mass, which
+        // only the G plane holds there
+        double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+        if (vg.reduced) {
+            z0 = zpow(vg, iz, cz, 0); z1 = zpow(vg, iz, cz, 1); z2 = zpow(vg, iz, cz, 2); z3 = zpow(vg, iz, cz, 3);
+        }
+        const bool mass_row = !vg.reduced || iz == 0;
         const S* row = fk + (long long)r * nx;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         for (int ix = 0; ix < nx; ++ix) {
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
             s1 += fv * scx[ix];
             s2 += fv * scx2[ix];
             s3 += fv * scx3[ix];
-            if (wall_mask) {
+            if (wall_mask && mass_row) {
 #pragma unroll
                 for (int s = 0; s < 6; ++s) {
                     if ((wall_mask >> s) & 1) {
@@ -82,20 +89,37 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
             }
         }
         const double d0 = s0, d1 = s1, d2 = s2, d3 = s3;
-        const double t = cy * cy + cz * cz;
-        acc[0] += d0;
-        acc[1] += d1;
-        acc[2] += d0 * cy;
-        acc[3] += d0 * cz;
-        acc[4] += d2;
-        acc[5] += d0 * (cy * cy);
-        acc[6] += d0 * (cz * cz);
-        acc[7] += d1 * cy;
-        acc[8] += d1 * cz;
-        acc[9] += d0 * (cy * cz);
-        acc[10] += d3 + d1 * t;
-        acc[11] += cy * (d2 + d0 * t);
-        acc[12] += cz * (d2 + d0 * t);
+        if (!vg.reduced) {
+            const double t = cy * cy + cz * cz;
+            acc[0] += d0;
+            acc[1] += d1;
+            acc[2] += d0 * cy;
+            acc[3] += d0 * cz;
+            acc[4] += d2;
+            acc[5] += d0 * (cy * cy);
+            acc[6] += d0 * (cz * cz);
+            acc[7] += d1 * cy;
+            acc[8] += d1 * cz;
+            acc[9] += d0 * (cy * cz);
+            acc[10] += d3 + d1 * t;
+            acc[11] += cy * (d2 + d0 * t);
+            acc[12] += cz * (d2 + d0 * t);
+        } else {   // each moment c_x^a c_y^b c_z^k: row sum d_a times c_y^b times the plane's c_z^k weight
+            const double cy2 = cy * cy;
+            acc[0] += d0 * z0;
+            acc[1] += d1 * z0;
+            acc[2] += d0 * cy * z0;
+            acc[3] += d0 * z1;
+            acc[4] += d2 * z0;
+            acc[5] += d0 * cy2 * z0;
+            acc[6] += d0 * z2;
+            acc[7] += d1 * cy * z0;
+            acc[8] += d1 * z1;
+            acc[9] += d0 * cy * z1;
+            acc[10] += (d3 + d1 * cy2) * z0 + d1 * z2;                   // c_x c^2
+            acc[11] += cy * (d2 + d0 * cy2) * z0 + cy * d0 * z2;         // c_y c^2
+            acc[12] += (d2 + d0 * cy2) * z1 + d0 * z3;                   // c_z c^2
+        }
     }
     block_sum<MOMN>(acc, red);
     if (threadIdx.x == 0) {
@@ -107,16 +131,18 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
 // 1D sums of one axis table of a record about velocity u, on the lanes of
 // one warp: s[a] = sum_j c^a E_j and s[4 + a] = sum_j c^a E_j B_j, a = 0..3,
 // c = xi_j - u (valid in lane 0).
+// On the reduced grid's z axis (zplanes) c^a is the plane weight of xi_z^a.
 __device__ void axis_sums(const double* __restrict__ tab, int NT, const double* __restrict__ xi, int off, int n,
-                          double u, int lane, double* s) {
+                          double u, int lane, double* s, const VGridDev* zplanes = nullptr) {
     double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = lane; j < n; j += 32) {
         const double c = xi[off + j] - u, E = tab[off + j], EB = E * tab[NT + off + j];
         double ca = 1.0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            p[a] += ca * E;
-            p[4 + a] += ca * EB;
+            const double wa = zplanes ? zpow(*zplanes, j, 0.0, a) : ca;
+            p[a] += wa * E;
+            p[4 + a] += wa * EB;
             ca *= c;
         }
     }
@@ -240,7 +266,7 @@ __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__
                 const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
                 const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
                 stT<T, S>(fk + v, fv[j] + dlt);
-                if (wall_mask) {
+                if (wall_mask && (!vg.reduced || q < ny)) {   // mass flux: the G plane on the reduced grid
                     const int iz = q / ny, iy = q - iz * ny;
                     const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
                     for (int s = 0; s < 6; ++s) {
@@ -285,7 +311,8 @@ __global__ void __launch_bounds__(192) k_corr_moments(int Nd, const int* __restr
         const int r = w / 3, d = w % 3;
         const double* tab = (r == 0 ? recNew.tab : recHalf.tab) + (long long)k * NTAB * NT;
         const int off = d == 0 ? 0 : (d == 1 ? nx : nx + ny), n = d == 0 ? nx : (d == 1 ? ny : nz);
-        axis_sums(tab, NT, vg.xi, off, n, Wnew[c * 5 + 1 + d], threadIdx.x & 31, axs[r][d]);
+        axis_sums(tab, NT, vg.xi, off, n, Wnew[c * 5 + 1 + d], threadIdx.x & 31, axs[r][d],
+                  (vg.reduced && d == 2) ? &vg : nullptr);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -358,7 +385,8 @@ __global__ void __launch_bounds__(256) k_wall_rho(int Nd, const int* __restrict_
     __shared__ double red[32 * 6];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const S* fk = f + (long long)k * vg.Nv;
-    for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
+    const long long nmass = vg.reduced ? (long long)vg.nx * vg.ny : vg.Nv;   // mass: the G plane if reduced
+    for (long long v = threadIdx.x; v < nmass; v += blockDim.x) {
         int ix, iy, iz;
         vsplit(v, vg.nx, vg.ny, ix, iy, iz);
         const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
@@ -507,11 +535,13 @@ __global__ void __launch_bounds__(256) k_wall_flux(int Nd, const int* __restrict
             const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
             if (xn > 0.0) {
                 const double g = xn * Store<S>::ld(fk + v);
-                acc[0] += g;
-                acc[1] += g * x0;
-                acc[2] += g * x1;
-                acc[3] += g * x2;
-                acc[4] += g * 0.5 * (x0 * x0 + x1 * x1 + x2 * x2);
+                double psi[5];
+                psi_node(vg, x0, x1, x2, iz, psi);
+                acc[0] += g * psi[0];
+                acc[1] += g * psi[1];
+                acc[2] += g * psi[2];
+                acc[3] += g * psi[3];
+                acc[4] += g * psi[4];
             }
         }
         block_sum<5>(acc, sm);

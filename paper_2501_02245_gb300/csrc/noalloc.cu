@@ -105,6 +105,7 @@ extern "C" gsis_status gsis_corrected_maxwellian_noalloc(const double* W, int n,
                                                          double* f_out, void* cuda_stream) {
     if (!W || !f_out || !vgrid || n < 0) return GSIS_ERR_ARG;
     if (n > NOALLOC_MAX_STATES) return GSIS_ERR_ARG;
+    if (vgrid->reduced != 0) return GSIS_ERR_ARG;   // full 3D grids only
     // each axis is bounded before the node count is summed, so the sum cannot overflow
     long long Nv = 1, NTl = 0;
     for (int d = 0; d < 3; ++d) {

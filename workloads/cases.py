@@ -95,7 +95,8 @@ def shock_1d_case(Ma=2.0, n_cells=200, half_width=25.0, nv=(48, 24, 24), vmax=6.
 def cylinder_case(Ma=5.0, Kn=0.01, n_r=128, n_theta=128, nv=(48, 48, 24),
                   vbox=((-14.0, 14.0), (-12.0, 12.0), (-12.0, 12.0)), wall_T=2.0,
                   adaptive=True, Kn_ref=0.01, r_out=5.0, first_cell_mfp=0.1,
-                  macro_steps=100, cfl=5.0, k_sub=2, iterations=60, presolve_max_blocks=200, relax=0.7):
+                  macro_steps=100, cfl=5.0, k_sub=2, iterations=60, presolve_max_blocks=200, relax=0.7,
+                  reduced=False):
     """Hypersonic flow past a cylinder of unit diameter on a body-fitted O-grid.
 
     First radial cell = first_cell_mfp free-stream mean free paths (= Kn * D).
@@ -103,13 +104,18 @@ def cylinder_case(Ma=5.0, Kn=0.01, n_r=128, n_theta=128, nv=(48, 48, 24),
     Navier-Stokes presolve.  The synthetic correction is under-relaxed (relax)
     against the entropy mode of the stagnation region.  100 pseudo-steps of
     the synthetic solve per GSIS iteration: the residual history of the
-    cylinder is the same with 50 to 400.
+    cylinder is the same with 50 to 400.  reduced: xi_z integrated out (two
+    reduced distributions on the nv[0] x nv[1] grid of the first two axes of
+    vbox; nv[2] and vbox[2] unused).
     """
     u = Ma * np.sqrt(GAMMA)
     Winf = np.array([1.0, u, 0.0, 0.0, 1.0])
     mesh = cylinder_ogrid(n_r, n_theta, 0.5, r_out, first_cell_mfp * Kn, wall_T, Winf)
     W0 = np.tile(Winf, (mesh.ncell, 1))
-    vg = VGrid(tuple(nv), tuple(b[0] for b in vbox), tuple(b[1] for b in vbox))
+    if reduced:
+        vg = VGrid((nv[0], nv[1], 2), (vbox[0][0], vbox[1][0], 0.0), (vbox[0][1], vbox[1][1], 1.0), reduced=True)
+    else:
+        vg = VGrid(tuple(nv), tuple(b[0] for b in vbox), tuple(b[1] for b in vbox))
     return Case(f"cylinder_Ma{Ma:g}_Kn{Kn:g}_{n_r}x{n_theta}", mesh, vg, W0, Kn=Kn,
                 adaptive=adaptive, Kn_ref=Kn_ref, macro_steps=macro_steps, cfl=cfl, k_sub=k_sub,
                 iterations=iterations, presolve_max_blocks=presolve_max_blocks, relax=relax,
