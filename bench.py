@@ -176,9 +176,10 @@ def source_sha(files):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(config, dtype):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current sweep source (else null)."""
+def traffic_per_point(config, dtype):
+    """DRAM bytes per (cell, velocity) point of one sweep launch, from the
+    committed ncu summary, if it was taken on the current sweep source (else
+    None)."""
     p = os.path.join(ROOT, "profiles", "sweep_%s_%s.json" % (config, dtype))
     if not os.path.exists(p):
         return None
@@ -188,7 +189,7 @@ def traffic_from_profile(config, dtype):
                       "paper_2501_02245_gb300/csrc/gsis_device.cuh"])
     if d.get("sweep_src_sha") != sha:
         return None
-    return d.get("dram_bytes_per_launch_full")
+    return d.get("dram_bytes_per_point")
 
 
 def _cpu_model():
@@ -334,7 +335,7 @@ def sweep_roofline(args, rep, steps, peaks, traffic):
     eb = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[args.dtype]
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
         mp = json.load(fh)
-    trf = None if traffic is None else traffic * launches_iter
+    trf = None if traffic is None else traffic * pts * launches_iter   # per GSIS iteration, like achieved
     if args.dtype == "f64":
         fpp = SWEEP_FLOPS_PER_POINT_1D if args.config == "shock" else SWEEP_FLOPS_PER_POINT_2D
         peak = peaks.get("fp64_tflops") if peaks else None
@@ -412,7 +413,7 @@ def run_gsis(args):
             peaks = measured_alu_peaks(stream, local)
         except Exception as exc:   # the roofline then falls back to the derived FP64 peak, and says so
             peaks = {"error": str(exc)}
-    roof = sweep_roofline(args, rep, args.steps, peaks, traffic_from_profile(args.config, args.dtype))
+    roof = sweep_roofline(args, rep, args.steps, peaks, traffic_per_point(args.config, args.dtype))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
@@ -432,6 +433,7 @@ def run_gsis(args):
                                                   line.get("time_to_converged"), t_max / args.steps)
         line["full_kinetic"] = full_kinetic_arm(args, stream, rep, t_max / args.steps)
         line["reduced_2d"] = reduced_arm(args, stream, rep, reference_state, t_max / args.steps)
+        line["other_workloads"] = other_workloads(stream, local)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, nd, nv, nc, cores, cpu, wall = cpu_baseline(args.config)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu,
@@ -544,6 +546,85 @@ def reduced_arm(args, stream, rep_3d, reference_state, ms_per_iter_3d, steps=5):
     return out
 
 
+def _single(config, dtype, stream, warmup, steps):
+    """Throughput of one single-solve workload (warm-up iterations untimed,
+    then `steps` timed with CUDA events on the library's stream)."""
+    import torch
+    from paper_2501_02245_gb300 import Solver
+    case = make_case(config)
+    case.tol = 0.0
+    s = Solver.from_case(case, vdf_dtype=dtype, stream=stream)
+    r0 = s.iterate(0)
+    s.iterate(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = s.iterate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    eb = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[dtype]
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        hbm = json.load(fh)["hbm_gbs"]
+    sweep_ms = r["phase_ms"]["sweep"] / steps
+    pts = r["n_dvm"] * r["n_v"]
+    return {"workload": workload_name(config, dtype), "ms_per_iteration": ms,
+            "updates_per_s": pts / (ms * 1e-3), "n_dvm": r["n_dvm"], "n_v": r["n_v"], "vdf_bytes": r["vdf_bytes"],
+            "presolve_ms": r0["phase_ms"]["presolve"],
+            "phase_ms_per_step": {k: v / steps for k, v in r["phase_ms"].items() if v > 0},
+            "sweep_hbm_frac_per_iteration": 2 * eb * pts / (sweep_ms * 1e-3) / 1e9 / hbm, "eps_last": r["eps"]}
+
+
+def _batch(stream, steps=3):
+    """The 64-shock batch through gsis_iterate_batch (first call: start,
+    autotuning, graph recording; then `steps` timed iterations)."""
+    import torch
+    from workloads import shock_batch_cases
+    from paper_2501_02245_gb300 import Solver, iterate_batch
+    cases = shock_batch_cases()
+    solvers = [Solver.from_case(c, vdf_dtype=c.extra["vdf_dtype"], stream=stream) for c in cases]
+    iterate_batch(solvers, 1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = iterate_batch(solvers, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    for sv in solvers:
+        sv.close()
+    pts = sum(r["n_dvm"] * r["n_v"] for r in reps)
+    eb = {"f32": 4, "bf16": 2}
+    bytes_alg = sum(2 * eb[c.extra["vdf_dtype"]] * r["n_dvm"] * r["n_v"] for c, r in zip(cases, reps))
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        hbm = json.load(fh)["hbm_gbs"]
+    sweep_ms = reps[0]["phase_ms"]["sweep"]
+    return {"workload": workload_name("batch", "mixed"), "ms_per_iteration": ms, "updates_per_s": pts / (ms * 1e-3),
+            "points_per_iteration": pts, "vdf_bytes": sum(r["vdf_bytes"] for r in reps), "sweep_ms": sweep_ms,
+            "sweep_hbm_frac_per_iteration": bytes_alg / (sweep_ms * 1e-3) / 1e9 / hbm}
+
+
+def other_workloads(stream, local):
+    """The other configurations, measured in the same run: the 1D Ma 2 shock
+    (FP64, 200 cells, 48 x 24 x 24), the 3D sphere (BF16 VDF, 96 x 64 x 64,
+    48^3) and the 64-shock batch (FP32/BF16)."""
+    import torch
+    clocks = Clocks(local)
+    clocks.start()
+    out = {}
+    try:
+        out["shock_f64"] = _single("shock", "f64", stream, 3, 5)
+        out["batch"] = _batch(torch.cuda.Stream())
+        out["sphere_bf16"] = _single("sphere", "bf16", stream, 2, 3)
+    except Exception as exc:   # reported, not hidden: the headline line still prints
+        out["error"] = "%s: %s" % (type(exc).__name__, exc)
+    out["clocks"] = clocks.stop()
+    return out
+
+
 def full_kinetic_arm(args, stream, rep_adaptive, adaptive_ms_per_iter, steps=3):
     """The other arm of the cylinder configuration: every cell kinetic (no
     adaptation), same mesh, velocity grid and precision: throughput, VDF
@@ -611,7 +692,7 @@ def run_batch(args):
         peaks = json.load(fh)
     achieved = bytes_alg / (sweep_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profile("batch", "mixed"),
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
             "kernel": "k_sweep_batch (both Gauss-Seidel passes of all 64 solves, one launch)",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
             "algorithmic": "2 passes x 2 x b bytes per (cell, velocity), b = 4 (FP32) / 2 (BF16)"}
