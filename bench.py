@@ -186,7 +186,7 @@ def traffic_per_point(config, dtype):
     with open(p) as fh:
         d = json.load(fh)
     sha = source_sha(["paper_2501_02245_gb300/csrc/sweep.cu", "paper_2501_02245_gb300/csrc/sweep_device.cuh",
-                      "paper_2501_02245_gb300/csrc/gsis_device.cuh"])
+                      "paper_2501_02245_gb300/csrc/sweep_pair.cuh", "paper_2501_02245_gb300/csrc/gsis_device.cuh"])
     if d.get("sweep_src_sha") != sha:
         return None
     return d.get("dram_bytes_per_point")
@@ -426,11 +426,14 @@ def run_gsis(args):
             "roofline": roof, "measured_peaks": peaks, "clocks": ck, "gpu_launches": rep["kernel_launches"]}
     if not args.no_e2e:
         line["e2e"] = e2e(args, case, stream)
+    converged_state = None
     if not args.no_converge and args.config in ("cylinder", "cylinder_full", "shock"):
-        line["time_to_converged"] = time_to_converged(args, case, stream, args.dtype)
+        line["time_to_converged"], converged_state = time_to_converged(args, case, stream, args.dtype,
+                                                                       keep_state=True)
     if not args.no_forms and args.config == "cylinder" and args.dtype == "f64" and rank == 0:
         line["precision_forms"] = precision_forms(args, case, stream, reference_state,
-                                                  line.get("time_to_converged"), t_max / args.steps)
+                                                  line.get("time_to_converged"), t_max / args.steps,
+                                                  converged_state)
         line["full_kinetic"] = full_kinetic_arm(args, stream, rep, t_max / args.steps)
         line["reduced_2d"] = reduced_arm(args, stream, rep, reference_state, t_max / args.steps)
         line["other_workloads"] = other_workloads(stream, local)
@@ -456,29 +459,37 @@ def _error_vs(Wr, qr, W, q):
     return {"rho": rel(W[:, 0], Wr[:, 0]), "T": rel(W[:, 4], Wr[:, 4]), "wall_q": rel(q, qr)}
 
 
-def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_iter):
+def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_iter, converged_state=None):
     """The cylinder with FP32, BF16 and FP16 VDF storage (FP32 sweep
     arithmetic; FP64 moments, conservation correction and synthetic solve):
     throughput, time to the residual thresholds from a fresh context, VDF
     memory, and the error in density, temperature and wall heat flux against
     the FP64 GPU run (the parity-tested path) after the same number of
-    iterations from the same start."""
+    iterations from the same start: at the iteration where the FP64 run first
+    reached epsilon < 2e-4 (near the steady state; the headline error), and
+    early in the transient (the benchmark's warm-up + timed iterations, where
+    a small shift of the transient dominates the difference)."""
     import torch
     from paper_2501_02245_gb300 import Solver
     Wr, qr, n_ref = reference_state
     out = {"reference": "FP64 GPU run of this benchmark after %d GSIS iterations" % n_ref}
+    n_conv = None
+    if converged_state is not None:
+        Wc, qc, n_conv = converged_state
+        out["reference_converged"] = ("FP64 GPU run from a fresh context after %d GSIS iterations (its first "
+                                      "epsilon < 2e-4)" % n_conv)
     thresholds = (1e-3, 2e-4)
     for dt in ("f32", "bf16", "f16"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = Solver.from_case(case, vdf_dtype=dt, stream=stream)
         s.iterate(0)
-        reached, err, it_ms = {}, None, []
+        reached, err, err_conv, it_ms = {}, None, None, []
         eps_min = 1e300
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         n_dvm = vdf = 0
-        for it in range(max(n_ref, 60)):
+        for it in range(max(n_ref, n_conv or 0, 60)):
             e0.record(stream)
             r = s.iterate(1)
             e1.record(stream)
@@ -493,12 +504,15 @@ def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_ite
                     reached[k] = {"iterations": it + 1, "seconds": time.perf_counter() - t0}
             if it + 1 == n_ref:
                 err = _error_vs(Wr, qr, s.W(), s.moments(["wall_q"])["wall_q"])
-            if it + 1 >= n_ref and len(reached) == len(thresholds):
+            if n_conv is not None and it + 1 == n_conv:
+                err_conv = _error_vs(Wc, qc, s.W(), s.moments(["wall_q"])["wall_q"])
+            if it + 1 >= max(n_ref, n_conv or 0) and len(reached) == len(thresholds):
                 break
         s.close()
         ms_it = float(np.median(it_ms)) if it_ms else None
         d = {"ms_per_iteration": ms_it, "updates_per_s": n_dvm * case.vgrid.nv / (ms_it * 1e-3) if ms_it else None,
-             "vdf_bytes": vdf, "error_vs_f64": err, "time_to_converged": reached, "eps_min": eps_min}
+             "vdf_bytes": vdf, "error_vs_f64": err_conv, "error_vs_f64_early": err,
+             "time_to_converged": reached, "eps_min": eps_min}
         if f64_ms_per_iter and ms_it:
             d["speedup_per_iteration_vs_f64"] = f64_ms_per_iter / ms_it
         if f64_ttc:
@@ -738,12 +752,14 @@ def run_batch(args):
     return 0
 
 
-def time_to_converged(args, case, stream, dtype, thresholds=(1e-3, 2e-4), cap=80):
+def time_to_converged(args, case, stream, dtype, thresholds=(1e-3, 2e-4), cap=80, keep_state=False):
     """Wall-clock time (device synchronised) from a fresh context (host data,
     presolve, region) until the residual of Sec. 4 first falls below each
     threshold, at most `cap` GSIS iterations.  The 1e-6 criterion of the paper
     is not reached by these runs (see the convergence status in the design
-    notes), so the precision forms are compared at these thresholds."""
+    notes), so the precision forms are compared at these thresholds.  With
+    keep_state the state (W, wall heat flux) of the last iteration is returned
+    beside the report (not in it)."""
     import torch
     from paper_2501_02245_gb300 import Solver
     torch.cuda.synchronize()
@@ -767,8 +783,9 @@ def time_to_converged(args, case, stream, dtype, thresholds=(1e-3, 2e-4), cap=80
             break
     out["eps_min"] = eps_min
     out["iterations_run"] = it + 1
+    state = (s.W(), s.moments(["wall_q"])["wall_q"], it + 1) if keep_state else None
     s.close()
-    return out
+    return (out, state) if keep_state else out
 
 
 def e2e(args, case, stream):

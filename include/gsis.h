@@ -68,7 +68,17 @@ enum {
     GSIS_FIELD_HOT_QX = 1 << 11, GSIS_FIELD_HOT_QY = 1 << 12, GSIS_FIELD_HOT_QZ = 1 << 13,
     GSIS_FIELD_KN_GLL = 1 << 14, GSIS_FIELD_DVM = 1 << 15,
     GSIS_FIELD_WALL_Q = 1 << 16,   /* heat flux into the wall, per unit area (0 off the wall) */
-    GSIS_NFIELDS = 17
+    /* Eq. full_constitutive at the current state: sigma = sigma_NSF(W) + HoT_sigma, q = q_NSF(W) + HoT_q,
+     * HoT of the last iteration (0 in NS cells) -- equal to the kinetic moments at a converged state */
+    GSIS_FIELD_SXX = 1 << 17, GSIS_FIELD_SYY = 1 << 18, GSIS_FIELD_SZZ = 1 << 19,
+    GSIS_FIELD_SXY = 1 << 20, GSIS_FIELD_SXZ = 1 << 21, GSIS_FIELD_SYZ = 1 << 22,
+    GSIS_FIELD_QX = 1 << 23, GSIS_FIELD_QY = 1 << 24, GSIS_FIELD_QZ = 1 << 25,
+    GSIS_FIELD_P = 1 << 26,        /* pressure rho T */
+    /* force of the gas on the wall per unit wall area (0 off the wall): normal component (pressure) and
+     * tangential vector (shear); from the same wall fluxes as GSIS_FIELD_WALL_Q */
+    GSIS_FIELD_WALL_P = 1 << 27, GSIS_FIELD_WALL_TX = 1 << 28, GSIS_FIELD_WALL_TY = 1 << 29,
+    GSIS_FIELD_WALL_TZ = 1 << 30,
+    GSIS_NFIELDS = 31
 };
 
 /* Device-memory callbacks (for example a framework's caching allocator).
@@ -103,6 +113,12 @@ typedef struct {
                                       0 = default 2^24 (about a second)                              */
     double relax;         /* weight of the synthetic correction: W^{n+1} = W^{n+1/2} + relax *
                              (W_synthetic - W^{n+1/2}); 1 = the plain scheme, (0, 1]; 0 is read as 1 */
+    int    d_r;           /* internal degrees of freedom of the gas (Sec. 2, Eq. general_model): 0 = monatomic,
+                             the Shakhov model with Pr = 2/3, the only form implemented; d_r > 0 (the
+                             two-VDF model, f_0 and f_1) returns GSIS_ERR_UNSUPPORTED, d_r < 0 GSIS_ERR_ARG */
+    double Z_r;           /* internal collision number of Eq. general_model (read only when d_r > 0)         */
+    double A[4];          /* heat-flux relaxation rates A_tt, A_tr, A_rt, A_rr of Eq. mu_kappa and the q_0/q_1
+                             mixing (read only when d_r > 0)                                               */
 } gsis_params;
 
 /* Structured mesh: cells (i, j, k), flat index c = i + ni*(j + nj*k).
@@ -198,7 +214,13 @@ gsis_status gsis_iterate(gsis_ctx* ctx, int max_iter, gsis_report* report);
  * through those sides into the wall divided by their area -- for a DVM cell
  * carried by its current distribution (outgoing half of f, the re-emitted
  * half rho_w M(0, T_w) with zero net mass flux), for an NS cell the Fourier
- * heat flux of the NSF wall flux at the current state; 0 for other cells. */
+ * heat flux of the NSF wall flux at the current state; 0 for other cells.
+ * GSIS_FIELD_WALL_P / _TX.._TZ: the momentum components F_m of the same wall
+ * fluxes (outward area vector S, unit normal n = S/|S|), pressure F_m.n and
+ * shear F_m - (F_m.n) n, summed over the wall sides and divided by their area.
+ * The derived fields (WALL_*, S*, Q*, P) are computed on the device at the
+ * call; before the first gsis_iterate (state W0; HoT, Kn_Gll and the DVM flag
+ * 0) they give GSIS_ERR_STATE. */
 gsis_status gsis_moments(gsis_ctx* ctx, unsigned field_mask, double* dst, int dst_is_device);
 
 /* Copy the compacted VDF of the DVM cells to host memory as FP64:
@@ -245,6 +267,16 @@ gsis_status gsis_debug_set_region(gsis_ctx* ctx, const uint8_t* flags);
  * becomes unusable).  The paper has no counterpart: it runs one solve at a
  * time. */
 gsis_status gsis_iterate_batch(gsis_ctx** ctxs, int n, int iterations, gsis_report* reports);
+
+/* Test hook: batch plans recorded from now on (in this process) use the named
+ * tile shape of the persistent batched sweep instead of the autotuned one
+ * (names as reported by gsis_batch_info, e.g. "vpt2_cb1_w4", or the
+ * velocity-pair shapes "pair1_cb1_w4", "pair2_cb1_w4", "pair1_cb1_w8", which
+ * need FP32/BF16/FP16 members with an even nx: gsis_iterate_batch then returns
+ * GSIS_ERR_ARG for another batch).  NULL or "" restores autotuning.  Every
+ * shape computes the same result.  GSIS_ERR_ARG for an unknown name.  The
+ * paper has no counterpart. */
+gsis_status gsis_debug_set_batch_tile(const char* name);
 
 /* Test hook: run the kinetic sweep of this context with the named tile shape
  * from now on instead of the autotuned one (names as reported by

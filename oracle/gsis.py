@@ -222,17 +222,20 @@ class OracleSolver:
                 corr[r] = F_kin - F_nsf[r]
         return corr
 
-    def wall_heat_flux(self):
-        """Heat flux into the wall per unit area, per cell (0 without wall
-        sides): the energy flux through the cell's diffuse-wall sides divided
-        by their area, carried by the current distribution for a DVM cell
-        (outgoing half of f, re-emitted rho_w M(0, T_w) with zero net mass
-        flux) and by the NSF wall flux at the current state for an NS cell."""
+    def wall_loads(self):
+        """Per cell, per unit wall area: [heat flux into the wall, wall pressure,
+        wall shear stress (3)], 0 without wall sides.  Each wall side's flux
+        F (mass, momentum, energy through its outward area vector S) is carried
+        by the current distribution for a DVM cell (outgoing half of f,
+        re-emitted rho_w M(0, T_w) with zero net mass flux) and by the NSF wall
+        flux at the current state for an NS cell.  The momentum flux is the
+        force on the wall: pressure = F_m . n, shear = F_m - (F_m . n) n with
+        n = S/|S|; sums over the cell's wall sides divided by their area."""
         geo = self.geo
         idx = np.nonzero(geo.bT == BC_WALL)[0]
-        out_num = np.zeros(self.N); out_area = np.zeros(self.N)
+        num = np.zeros((self.N, 5)); area = np.zeros(self.N)
         if len(idx) == 0:
-            return out_num
+            return num
         gu, gT = self.gradients(self.W)
         F_nsf = wall_nsf_flux(geo, self.bc_state, self.W[:, 0], self.W[:, 1:4], self.W[:, 4], gu, gT,
                               self.mu0, self.omega)
@@ -240,12 +243,31 @@ class OracleSolver:
             c = geo.bC[f_i]
             if self.dvm[c]:
                 Mw = self.vg.maxwellian(1.0, np.zeros(3), self.bc_state[geo.bSide[f_i], 4])
-                e = wall_kinetic_flux(self.f[c], geo.bS[f_i], Mw, self.vg)[4]
+                F = wall_kinetic_flux(self.f[c], geo.bS[f_i], Mw, self.vg)
             else:
-                e = F_nsf[r, 4]
-            out_num[c] += e
-            out_area[c] += geo.bSabs[f_i]
-        return np.where(out_area > 0, out_num / np.where(out_area > 0, out_area, 1.0), 0.0)
+                F = F_nsf[r]
+            n = geo.bS[f_i] / geo.bSabs[f_i]
+            Fn = np.dot(F[1:4], n)
+            num[c, 0] += F[4]
+            num[c, 1] += Fn
+            num[c, 2:5] += F[1:4] - Fn * n
+            area[c] += geo.bSabs[f_i]
+        has = area > 0
+        return np.where(has[:, None], num / np.where(has, area, 1.0)[:, None], 0.0)
+
+    def wall_heat_flux(self):
+        """Heat flux into the wall per unit area, per cell (0 without wall
+        sides): the first column of wall_loads."""
+        return self.wall_loads()[:, 0]
+
+    def constitutive(self):
+        """Eq. full_constitutive at the current state: sigma = sigma_NSF(W) +
+        HoT_sigma and q = q_NSF(W) + HoT_q, with the HoT of the last iteration
+        (zero in NS cells and before the first iteration) -- the stress and heat
+        flux of the synthetic equations, equal to the kinetic moments at a
+        converged state."""
+        sig_n, q_n = self.nsf_field(self.W)
+        return sig_n + self.hot_sigma, q_n + self.hot_q
 
     def step(self):
         """One GSIS iteration; returns epsilon."""

@@ -238,7 +238,7 @@ __global__ void k_remap(int Nd, const int* __restrict__ dvm_cell, const int* __r
         for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
             int ix, iy, iz;
             vsplit(v, vg.nx, vg.ny, ix, iy, iz);
-            Store<S>::st(dst + v, eval_rec(sc, tb, vg.NT, vg.nx, vg.ny, ix, iy, iz));
+            Store<S>::st(dst + v, vg.vscale * eval_rec(sc, tb, vg.NT, vg.nx, vg.ny, ix, iy, iz));
         }
     }
 }

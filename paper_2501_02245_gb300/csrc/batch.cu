@@ -8,18 +8,21 @@ namespace gsis {
 // ---------------------------------------------------------------------------- candidates
 struct TileShape {
     int vpt, cb, wpb;
+    bool pair;   // velocity pairs with packed FP32 arithmetic (FP32/BF16/FP16 members with an even nx only)
     const char* name;
 };
 
 static const TileShape kShapes[] = {
-    {1, 1, 4, "vpt1_cb1_w4"}, {2, 1, 4, "vpt2_cb1_w4"}, {4, 1, 4, "vpt4_cb1_w4"},
-    {2, 1, 8, "vpt2_cb1_w8"}, {2, 2, 4, "vpt2_cb2_w4"}, {4, 2, 2, "vpt4_cb2_w2"},
+    {1, 1, 4, false, "vpt1_cb1_w4"}, {2, 1, 4, false, "vpt2_cb1_w4"}, {4, 1, 4, false, "vpt4_cb1_w4"},
+    {2, 1, 8, false, "vpt2_cb1_w8"}, {2, 2, 4, false, "vpt2_cb2_w4"}, {4, 2, 2, false, "vpt4_cb2_w2"},
+    {1, 1, 4, true, "pair1_cb1_w4"}, {2, 1, 4, true, "pair2_cb1_w4"}, {1, 1, 8, true, "pair1_cb1_w8"},
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 int batch_num_shapes() { return kNumShapes; }
 const char* batch_shape_name(int s) { return (s >= 0 && s < kNumShapes) ? kShapes[s].name : "?"; }
-int batch_shape_vtile(int s) { return 32 * kShapes[s].vpt; }
+int batch_shape_vtile(int s) { return (kShapes[s].pair ? 64 : 32) * kShapes[s].vpt; }
+bool batch_shape_pair(int s) { return s >= 0 && s < kNumShapes && kShapes[s].pair; }
 
 int batch_grid(int shape, int nc) { return nc == 1 ? batch_grid_nc1(shape) : batch_grid_nc3(shape); }
 

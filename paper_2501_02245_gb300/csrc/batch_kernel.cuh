@@ -18,7 +18,7 @@
 // candidates listed here on the batch itself and keeps the fastest.
 #pragma once
 #include <algorithm>
-#include "sweep_device.cuh"
+#include "sweep_pair.cuh"
 
 namespace gsis {
 
@@ -83,6 +83,83 @@ __global__ void __launch_bounds__(32 * WPB) k_sweep_batch(const BatchSolve* __re
     }
 }
 
+// The same persistent sweep on pairs of velocities (sweep_pair.cuh): items of
+// 64 * VPT velocities, every member stored in FP32 / BF16 / FP16 with an even
+// nx (the host offers these shapes only for such batches).
+template <typename S, int NC, int VPT, int CB, bool FULL>
+__device__ __forceinline__ void batch_item2_t(const BatchSolve& B, int vtile, int lane, int pass0, int pass1) {
+    const SweepArgs& a = B.a;
+    Vel2<VPT, FULL> V;
+    make_vel2(a.vg, (long long)vtile * (64 * VPT), lane, V);
+    S* f = (S*)B.f;
+    for (int step = pass0; step < pass1; ++step) {
+        const int pass = 1 - step;
+        for (int hh = 0; hh < a.H; ++hh) {
+            const int h = pass ? (a.H - 1 - hh) : hh;
+            const int kb = __ldg(a.hp_off + h), ke = __ldg(a.hp_off + h + 1);
+            const int n = ke - kb;
+            for (int i0 = 0; i0 < n; i0 += CB) {
+                int kk[CB];
+                bool kon[CB];
+#pragma unroll
+                for (int b = 0; b < CB; ++b) {
+                    const int i = i0 + b;
+                    kon[b] = i < n;
+                    kk[b] = pass ? (ke - 1 - i) : (kb + i);
+                }
+                update_cells2<S, NC, VPT, CB>(a, f, kk, kon, V);
+            }
+        }
+    }
+}
+
+template <typename S, int NC, int VPT, int CB>
+__device__ __forceinline__ void batch_item2(const BatchSolve& B, int vtile, int lane, int pass0, int pass1) {
+    if constexpr (NC == 1) {
+        if ((long long)(vtile + 1) * (64 * VPT) <= B.a.vg.Nv) {
+            batch_item2_t<S, NC, VPT, CB, true>(B, vtile, lane, pass0, pass1);
+            return;
+        }
+    }
+    batch_item2_t<S, NC, VPT, CB, false>(B, vtile, lane, pass0, pass1);
+}
+
+template <int NC, int VPT, int CB, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k_sweep_batch2(const BatchSolve* __restrict__ solves,
+                                                           const int2* __restrict__ items, int n_items,
+                                                           int* __restrict__ ticket, int pass0, int pass1) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n_items) return;
+        const int2 it = items[t];
+        const BatchSolve& B = solves[it.x];
+        switch (B.dtype) {
+            case GSIS_F32: batch_item2<float, NC, VPT, CB>(B, it.y, lane, pass0, pass1); break;
+            case GSIS_BF16: batch_item2<__nv_bfloat16, NC, VPT, CB>(B, it.y, lane, pass0, pass1); break;
+            case GSIS_F16: batch_item2<__half, NC, VPT, CB>(B, it.y, lane, pass0, pass1); break;
+            default: break;   // FP64 members never reach the pair shapes
+        }
+    }
+}
+
+template <int NC, int VPT, int CB, int WPB>
+static void launch_t2(const BatchSolve* d_solves, const int2* d_items, int n_items, int* d_ticket, int grid,
+                      cudaStream_t st, int p0, int p1) {
+    k_sweep_batch2<NC, VPT, CB, WPB><<<grid, 32 * WPB, 0, st>>>(d_solves, d_items, n_items, d_ticket, p0, p1);
+}
+
+template <int NC, int VPT, int CB, int WPB>
+static int grid_t2() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep_batch2<NC, VPT, CB, WPB>, 32 * WPB, 0);
+    return std::max(1, sms * std::max(1, per));
+}
+
 template <int NC, int VPT, int CB, int WPB>
 static void launch_t(const BatchSolve* d_solves, const int2* d_items, int n_items, int* d_ticket, int grid,
                      cudaStream_t st, int p0, int p1) {
@@ -108,6 +185,9 @@ static void launch_nc(int shape, const BatchSolve* s, const int2* i, int n, int*
         case 2: launch_t<NC, 4, 1, 4>(s, i, n, t, g, st, p0, p1); break;
         case 3: launch_t<NC, 2, 1, 8>(s, i, n, t, g, st, p0, p1); break;
         case 4: launch_t<NC, 2, 2, 4>(s, i, n, t, g, st, p0, p1); break;
+        case 6: launch_t2<NC, 1, 1, 4>(s, i, n, t, g, st, p0, p1); break;
+        case 7: launch_t2<NC, 2, 1, 4>(s, i, n, t, g, st, p0, p1); break;
+        case 8: launch_t2<NC, 1, 1, 8>(s, i, n, t, g, st, p0, p1); break;
         default: launch_t<NC, 4, 2, 2>(s, i, n, t, g, st, p0, p1); break;
     }
 }
@@ -120,6 +200,9 @@ static int grid_nc(int shape) {
         case 2: return grid_t<NC, 4, 1, 4>();
         case 3: return grid_t<NC, 2, 1, 8>();
         case 4: return grid_t<NC, 2, 2, 4>();
+        case 6: return grid_t2<NC, 1, 1, 4>();
+        case 7: return grid_t2<NC, 2, 1, 4>();
+        case 8: return grid_t2<NC, 1, 1, 8>();
         default: return grid_t<NC, 4, 2, 2>();
     }
 }

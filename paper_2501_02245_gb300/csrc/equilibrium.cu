@@ -38,15 +38,21 @@ __device__ static int psi_terms(int row, const double* u, Term* t, double scale)
     }
 }
 
+// Terms of the base polynomial with a nonzero coefficient (a Maxwellian has only
+// p0; skipping the zero terms leaves its moment sums 19 times shorter, and a
+// zero term contributes exactly zero to them).
 __device__ static int base_terms(const RecSpec& s, Term* t) {
+    const Term all[19] = {
+        {s.p0, 0, 0, 0},
+        {s.p[0], 1, 0, 0}, {s.p[1], 0, 1, 0}, {s.p[2], 0, 0, 1},
+        {s.P2[0], 2, 0, 0}, {s.P2[1], 0, 2, 0}, {s.P2[2], 0, 0, 2},
+        {2.0 * s.P2[3], 1, 1, 0}, {2.0 * s.P2[4], 1, 0, 1}, {2.0 * s.P2[5], 0, 1, 1},
+        {s.r[0], 3, 0, 0}, {s.r[0], 1, 2, 0}, {s.r[0], 1, 0, 2},
+        {s.r[1], 2, 1, 0}, {s.r[1], 0, 3, 0}, {s.r[1], 0, 1, 2},
+        {s.r[2], 2, 0, 1}, {s.r[2], 0, 2, 1}, {s.r[2], 0, 0, 3}};
     int n = 0;
-    t[n++] = {s.p0, 0, 0, 0};
-    t[n++] = {s.p[0], 1, 0, 0}; t[n++] = {s.p[1], 0, 1, 0}; t[n++] = {s.p[2], 0, 0, 1};
-    t[n++] = {s.P2[0], 2, 0, 0}; t[n++] = {s.P2[1], 0, 2, 0}; t[n++] = {s.P2[2], 0, 0, 2};
-    t[n++] = {2.0 * s.P2[3], 1, 1, 0}; t[n++] = {2.0 * s.P2[4], 1, 0, 1}; t[n++] = {2.0 * s.P2[5], 0, 1, 1};
-    t[n++] = {s.r[0], 3, 0, 0}; t[n++] = {s.r[0], 1, 2, 0}; t[n++] = {s.r[0], 1, 0, 2};
-    t[n++] = {s.r[1], 2, 1, 0}; t[n++] = {s.r[1], 0, 3, 0}; t[n++] = {s.r[1], 0, 1, 2};
-    t[n++] = {s.r[2], 2, 0, 1}; t[n++] = {s.r[2], 0, 2, 1}; t[n++] = {s.r[2], 0, 0, 3};
+    for (int i = 0; i < 19; ++i)
+        if (all[i].c != 0.0) t[n++] = all[i];
     return n;
 }
 
@@ -190,9 +196,10 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
         tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * tab[3 * NT + idx];   // C2 = c^2 (plane value if reduced)
         tab[4 * NT + idx] = s.r[d] * c;
         if (d == 0) tab[idx] *= A;
-        if (out.tabf) {
+        if (out.tabf) {   // FP32 copies in stored units: E_x carries the VDF storage scale once
             float* tf = out.tabf + (long long)r * NTAB * NT;
-            for (int t = 0; t < NTAB; ++t) tf[t * NT + idx] = (float)tab[t * NT + idx];
+            for (int t = 0; t < NTAB; ++t)
+                tf[t * NT + idx] = (float)(t == 0 && d == 0 ? tab[idx] * vg.vscale : tab[t * NT + idx]);
         }
     }
     if (out.scalf) {
@@ -292,7 +299,7 @@ __global__ void k_build_gtab(int Nd, Records rec, VGridDev vg, const double* __r
     for (int q = threadIdx.x; q < nyz; q += blockDim.x) {
         const int jy = nx + q % ny, jz = nx + ny + q / ny;
         const double Cy = tab[2 * NT + jy], Cz = tab[2 * NT + jz];
-        const double Eyz = tab[jy] * tab[jz] * it;
+        const double Eyz = tab[jy] * tab[jz] * it * vg.vscale;   // g~/tau in stored units
         const double D = p0 + (tab[NT + jy] + tab[NT + jz]) + 2.0 * pyz * Cy * Cz;
         const double Ryz = tab[4 * NT + jy] + tab[4 * NT + jz];
         const double C2yz = tab[3 * NT + jy] + tab[3 * NT + jz];

@@ -360,6 +360,10 @@ std::map<std::string, int>& tuned_shapes() {   // autotuner cache: batch signatu
     static std::map<std::string, int> m;
     return m;
 }
+int& forced_batch_shape() {   // gsis_debug_set_batch_tile: -1 = autotune
+    static int s = -1;
+    return s;
+}
 
 void destroy_plan(BatchPlan* P) {
     if (!P) return;
@@ -409,6 +413,16 @@ std::string batch_signature(const std::vector<gsis_ctx*>& cs, int nc) {
 // fastest.  Cached per batch signature for the life of the process.
 gsis_status tune_batch(BatchPlan* P) {
     gsis_ctx* o = P->owner;
+    if (forced_batch_shape() >= 0) {   // test hook: the named shape, if this batch can run it
+        bool pairs_ok = true;
+        for (gsis_ctx* c : P->ctxs) pairs_ok = pairs_ok && c->p.vdf_dtype != GSIS_F64 && c->vg.nx % 2 == 0;
+        if (!batch_shape_pair(forced_batch_shape()) || pairs_ok) {
+            P->shape = forced_batch_shape();
+            P->tuned = false;
+            return GSIS_OK;
+        }
+        return set_err(o, GSIS_ERR_ARG, "the forced batch tile needs FP32/BF16/FP16 members with an even nx");
+    }
     const std::string sig = batch_signature(P->ctxs, P->nc);
     auto hit = tuned_shapes().find(sig);
     if (hit != tuned_shapes().end()) {
@@ -437,11 +451,14 @@ gsis_status tune_batch(BatchPlan* P) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int ns = batch_num_shapes();
-    P->tune_ms.assign(ns, 0.0);
+    P->tune_ms.assign(ns, -1.0);   // -1: shape not eligible for this batch
     int best = 1;
     double best_ms = 1e300;
     int2* d_it = nullptr;
+    bool pairs_ok = true;   // the pair shapes need FP32 / BF16 / FP16 storage and an even nx in every member
+    for (gsis_ctx* c : P->ctxs) pairs_ok = pairs_ok && c->p.vdf_dtype != GSIS_F64 && c->vg.nx % 2 == 0;
     for (int sh = 0; sh < ns; ++sh) {
+        if (batch_shape_pair(sh) && !pairs_ok) continue;
         std::vector<int2> it = batch_items(P->ctxs, sh);
         d_it = (int2*)dev_alloc(o, std::max<size_t>(1, it.size()) * sizeof(int2));
         if (!d_it) break;
@@ -615,6 +632,8 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
         p.presolve_max_blocks < 0 || p.wall_layers < 0 || p.adapt_every < 0 || !(p.tol >= 0.0) ||
         !(p.relax >= 0.0 && p.relax <= 1.0))
         return GSIS_ERR_ARG;
+    if (p.d_r < 0) return GSIS_ERR_ARG;
+    if (p.d_r > 0) return GSIS_ERR_UNSUPPORTED;   // the two-VDF model of Eq. general_model is not built
     if (alloc && (!alloc->alloc || !alloc->free)) return GSIS_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -808,7 +827,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->fgeo = (double*)dev_alloc(c, (size_t)N * 3 * 8 * sizeof(double));
     c->bgeo = (double*)dev_alloc(c, (size_t)N * 6 * 8 * sizeof(double));
     c->acell = (double*)dev_alloc(c, (size_t)N * sizeof(double));
-    c->wallq = (double*)dev_alloc(c, (size_t)N * sizeof(double));
+    c->fields = (double*)dev_alloc(c, (size_t)N * FIELDS_N * sizeof(double));
     c->gu = (double*)dev_alloc(c, (size_t)N * 9 * sizeof(double));
     c->gT = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
     c->grho = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
@@ -839,7 +858,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
     if (!c->d_job || !c->d_bar || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wmom ||
-        !c->Wh || !c->fgeo || !c->bgeo || !c->acell || !c->wallq ||
+        !c->Wh || !c->fgeo || !c->bgeo || !c->acell || !c->fields ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
         !c->lamf || !c->F0 || !c->dFa || !c->dFb || !c->gu || !c->gT ||
         !c->grho || !c->gU || !c->hot || !c->kin || !c->nsf || !c->kn_gll || !c->wall_den || !c->wall_in ||
@@ -899,6 +918,7 @@ gsis_status gsis_set_velocity_grid(gsis_ctx* c, const gsis_vgrid_desc* vd) {
     c->vg.nx = n3[0]; c->vg.ny = n3[1]; c->vg.nz = n3[2];
     c->vg.NT = n3[0] + n3[1] + n3[2];
     c->vg.reduced = red ? 1 : 0;
+    c->vg.vscale = c->p.vdf_dtype == GSIS_F16 ? 4096.0 : 1.0;
     c->vg.Nv = Nv;
     c->vg.w = w;
     c->vg.xi = c->d_xi;
@@ -971,14 +991,21 @@ gsis_status gsis_moments(gsis_ctx* c, unsigned mask, double* dst, int dst_is_dev
     if (!dst) return set_err(c, GSIS_ERR_ARG, "NULL destination");
     if (!c->mesh_set) return set_err(c, GSIS_ERR_STATE, "no mesh");
     if (mask == 0 || mask >= (1u << GSIS_NFIELDS)) return set_err(c, GSIS_ERR_ARG, "bad field mask");
+    const unsigned derived = ~((1u << 16) - 1) & ((1u << GSIS_NFIELDS) - 1);   // WALL_Q and above
+    if ((mask & derived) && !c->started)
+        return set_err(c, GSIS_ERR_STATE, "derived fields need the first gsis_iterate");
     const int N = c->m.N;
-    std::vector<double> W((size_t)N * 5), hot((size_t)N * HOTN), kn(N, 0.0), wq(N, 0.0);
+    std::vector<double> W((size_t)N * 5), hot((size_t)N * HOTN), kn(N, 0.0), fl;
     std::vector<int> c2d(N, -1);
-    if (c->started && (mask & GSIS_FIELD_WALL_Q) && c->has_wall) {
-        launch_wall_heat(c, c->wallq);
-        cudaMemcpyAsync(wq.data(), c->wallq, wq.size() * 8, cudaMemcpyDeviceToHost, c->stream);
-    }
     if (c->started) {
+        const unsigned wall_bits = GSIS_FIELD_WALL_Q | GSIS_FIELD_WALL_P | GSIS_FIELD_WALL_TX | GSIS_FIELD_WALL_TY |
+                                   GSIS_FIELD_WALL_TZ;
+        const bool wall = (mask & wall_bits) != 0, cons = (mask & derived & ~wall_bits) != 0;
+        if (wall || cons) {
+            launch_fields(c, wall, cons);
+            fl.resize((size_t)N * FIELDS_N);
+            cudaMemcpyAsync(fl.data(), c->fields, fl.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        }
         cudaMemcpyAsync(W.data(), c->W, W.size() * 8, cudaMemcpyDeviceToHost, c->stream);
         cudaMemcpyAsync(hot.data(), c->hot, hot.size() * 8, cudaMemcpyDeviceToHost, c->stream);
         cudaMemcpyAsync(kn.data(), c->kn_gll, kn.size() * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -1003,7 +1030,9 @@ gsis_status gsis_moments(gsis_ctx* c, unsigned mask, double* dst, int dst_is_dev
             else if (b < 14) v = hot[(size_t)cc * HOTN + (b - 5)];
             else if (b == 14) v = kn[cc];
             else if (b == 15) v = c2d[cc] >= 0 ? 1.0 : 0.0;
-            else v = wq[cc];
+            else if (b == 16) v = fl[(size_t)cc * FIELDS_N + FIELD_WALL];                 // wall heat flux
+            else if (b < 27) v = fl[(size_t)cc * FIELDS_N + (b - 17)];                    // sigma, q, p
+            else v = fl[(size_t)cc * FIELDS_N + FIELD_WALL + 1 + (b - 27)];               // wall p, shear
             out[(size_t)cc * nsel + o++] = v;
         }
     }
@@ -1032,6 +1061,7 @@ gsis_status gsis_get_vdf(gsis_ctx* c, double* dst, int* cells, long long capacit
         cudaGetLastError();
         return set_err(c, GSIS_ERR_CUDA, "gsis_get_vdf copy failed");
     }
+    const double iscale = 1.0 / c->vg.vscale;   // stored values carry the VDF storage scale
     for (long long i = 0; i < n; ++i) {
         double v;
         switch (c->p.vdf_dtype) {
@@ -1042,7 +1072,7 @@ gsis_status gsis_get_vdf(gsis_ctx* c, double* dst, int* cells, long long capacit
             default: { uint16_t h; std::memcpy(&h, &raw[(size_t)i * 2], 2);
                        __half_raw hr; hr.x = h; v = (double)__half2float(__half(hr)); break; }
         }
-        dst[i] = v;
+        dst[i] = v * iscale;
     }
     if (cells) std::memcpy(cells, dc.data(), dc.size() * 4);
     return GSIS_OK;
@@ -1192,6 +1222,20 @@ gsis_status gsis_debug_set_macro_path(gsis_ctx* c, int path) {
 const char* gsis_tuning_info(gsis_ctx* c) {
     if (!c) return "";
     return c->sweep_info.c_str();
+}
+
+gsis_status gsis_debug_set_batch_tile(const char* name) {
+    std::lock_guard<std::mutex> lk(batch_mutex());
+    if (!name || !*name) {
+        forced_batch_shape() = -1;
+        return GSIS_OK;
+    }
+    for (int sh = 0; sh < batch_num_shapes(); ++sh)
+        if (std::string(batch_shape_name(sh)) == name) {
+            forced_batch_shape() = sh;
+            return GSIS_OK;
+        }
+    return GSIS_ERR_ARG;
 }
 
 const char* gsis_batch_info(gsis_ctx** ctxs, int n) {

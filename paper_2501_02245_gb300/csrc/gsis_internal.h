@@ -25,6 +25,8 @@ constexpr int RS = 16;          // scalars per distribution record
 constexpr int NTAB = 5;         // axis tables per record: E, B, C, C2, R
 constexpr int MOMN = 19;        // 13 velocity moments + 6 wall half-range fluxes
 constexpr int HOTN = 9;         // sigma xx,yy,zz,xy,xz,yz; q x,y,z
+constexpr int FIELDS_N = 15;    // derived fields per cell: constitutive sigma (6), q (3), p; wall loads
+constexpr int FIELD_WALL = 10;  // wall heat flux, pressure, shear x/y/z
 
 // record scalar slots
 enum { RS_P0 = 0, RS_P2XY = 1, RS_P2XZ = 2, RS_P2YZ = 3, RS_OFFD = 4, RS_UX = 5, RS_UY = 6, RS_UZ = 7,
@@ -46,6 +48,13 @@ struct VGridDev {
     // enters a face flux of a 2D mesh), and the xi_z^k weight of plane iz is
     // zpow(iz, k) (1 for G and k = 0, 1 for H and k = 2, else 0)
     int reduced = 0;
+    // Storage scale of the VDF: stored value = vscale * f.  FP16 storage uses
+    // 2^12 so that the Maxwellian tails that carry the heat flux stay above
+    // FP16's subnormal range (its largest values, about 4 for a dense cold
+    // cell, stay far below 65504); 1 for the other types.  The kinetic step
+    // is linear in f: only its sources (g~/tau, boundary and interface
+    // distributions) carry the scale; moments and wall sums divide it out.
+    double vscale = 1.0;
 };
 
 // xi_z^k weight of z node iz for a moment: on a 3D grid the node value cz^k
@@ -166,7 +175,7 @@ struct gsis_ctx {
     double *F0 = nullptr, *dFa = nullptr, *dFb = nullptr;   // [N][15] Euler flux tensor and its changes (relaxation)
     double *fgeo = nullptr, *bgeo = nullptr; // face geometry (see MacroArgs)
     double* acell = nullptr;                 // [N] sound speed of the current pseudo-time state
-    double* wallq = nullptr;                 // [N] wall heat flux output (gsis_moments)
+    double* fields = nullptr;                // [N][FIELDS_N] derived fields of gsis_moments
     double *gu = nullptr, *gT = nullptr, *grho = nullptr, *gU = nullptr;
     double *hot = nullptr, *kin = nullptr, *nsf = nullptr, *kn_gll = nullptr;
     double *eps_buf = nullptr, *h_eps = nullptr;
@@ -242,6 +251,7 @@ struct BatchSolve;
 int batch_num_shapes();
 const char* batch_shape_name(int shape);
 int batch_shape_vtile(int shape);
+bool batch_shape_pair(int shape);
 int batch_grid(int shape, int nc);
 void launch_sweep_batch(int shape, int nc, const BatchSolve* d_solves, const int2* d_items, int n_items,
                         int* d_ticket, int grid, cudaStream_t st, int pass0, int pass1);
@@ -260,7 +270,10 @@ void launch_prim_to_cons(gsis_ctx* c, const double* Wprim, double* Ucons);
 void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim);
 void launch_blend(gsis_ctx* c, const double* Wh, double w, double* W);
 void launch_face_geometry(gsis_ctx* c);
-void launch_wall_heat(gsis_ctx* c, double* out);
+// Derived per-cell fields of gsis_moments into c->fields: with wall, the wall
+// loads (FIELD_WALL + heat flux, pressure, shear x/y/z); with cons, the
+// constitutive stress and heat flux of Eq. full_constitutive and the pressure.
+void launch_fields(gsis_ctx* c, bool wall, bool cons);
 // capturing: the launches are being recorded into a CUDA graph (then the
 // per-phase kernels replace the cooperative persistent launch)
 void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term, bool capturing = false);

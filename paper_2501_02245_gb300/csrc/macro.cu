@@ -460,36 +460,69 @@ void launch_wall_corr(gsis_ctx* c) {
     c->launches++;
 }
 
-// Heat flux into the wall per unit area for every cell with wall sides: the
-// energy component of the kinetic wall flux (DVM cells, wall_kin of the
-// current f) or of the NSF wall flux at the current state (NS cells), summed
+// Wall loads per unit wall area for every cell with wall sides, written to
+// out[c * FIELDS_N + FIELD_WALL + (0: heat flux into the wall, 1: pressure,
+// 2..4: shear vector)]: the wall fluxes F (kinetic, wall_kin of the current f,
+// for DVM cells; the NSF wall flux at the current state for NS cells), with
+// pressure F_m.n and shear F_m - (F_m.n) n of the momentum part F_m, summed
 // over the wall sides and divided by their area.
-__global__ void k_wall_heat(MacroArgs a, const int* __restrict__ cell2dvm, const double* __restrict__ W,
-                            const double* __restrict__ gu, const double* __restrict__ gT,
-                            const double* __restrict__ wall_kin, double* __restrict__ out) {
+__global__ void k_wall_loads(MacroArgs a, const int* __restrict__ cell2dvm, const double* __restrict__ W,
+                             const double* __restrict__ gu, const double* __restrict__ gT,
+                             const double* __restrict__ wall_kin, double* __restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.N) return;
-    double num = 0.0, area = 0.0;
+    double num[5] = {0, 0, 0, 0, 0}, area = 0.0;
     for (int s = 0; s < 6; ++s) {
         if (a.nbr[c * 6 + s] >= 0 || a.side_bc[c * 6 + s] != GSIS_BC_WALL) continue;
+        double F[5];
         if (cell2dvm[c] >= 0) {
-            num += wall_kin[((long long)c * 6 + s) * 5 + 4];
+            for (int q = 0; q < 5; ++q) F[q] = wall_kin[((long long)c * 6 + s) * 5 + q];
         } else {
-            double F[5];
             wall_nsf_flux(a, W + c * 5, gu + (long long)c * 9, gT + (long long)c * 3, c, s, F);
-            num += F[4];
         }
-        area += a.bgeo[((long long)c * 6 + s) * 8];
+        const double* G = a.bgeo + ((long long)c * 6 + s) * 8;   // |S|, unit normal
+        const double Fn = F[1] * G[1] + F[2] * G[2] + F[3] * G[3];
+        num[0] += F[4];
+        num[1] += Fn;
+        for (int i = 0; i < 3; ++i) num[2 + i] += F[1 + i] - Fn * G[1 + i];
+        area += G[0];
     }
-    out[c] = area > 0.0 ? num / area : 0.0;
+    double* o = out + (long long)c * FIELDS_N + FIELD_WALL;
+    for (int q = 0; q < 5; ++q) o[q] = area > 0.0 ? num[q] / area : 0.0;
 }
 
-void launch_wall_heat(gsis_ctx* c, double* out) {
+// Eq. full_constitutive at the current state, out[c * FIELDS_N + 0..8]:
+// sigma = sigma_NSF(W) + HoT_sigma (xx, yy, zz, xy, xz, yz), q = q_NSF(W) +
+// HoT_q, with the HoT of the last kinetic step (zero in NS cells); and the
+// pressure rho T at index 9.
+__global__ void k_constitutive(int N, const double* __restrict__ W, const double* __restrict__ gu,
+                               const double* __restrict__ gT, const double* __restrict__ hot, double mu0,
+                               double omega, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double sig[6], q[3];
+    nsf_of(viscosity(W[c * 5 + 4], mu0, omega), gu + (long long)c * 9, gT + (long long)c * 3, sig, q);
+    double* o = out + (long long)c * FIELDS_N;
+    const double* h = hot + (long long)c * HOTN;
+    for (int k = 0; k < 6; ++k) o[k] = sig[k] + h[k];
+    for (int k = 0; k < 3; ++k) o[6 + k] = q[k] + h[6 + k];
+    o[9] = W[c * 5] * W[c * 5 + 4];
+}
+
+void launch_fields(gsis_ctx* c, bool wall, bool cons) {
     const int N = c->m.N;
-    launch_wall_flux(c);                  // kinetic wall fluxes of the current f
-    launch_gradients(c, c->W, false);     // gradients of the current state for the NSF wall flux
-    k_wall_heat<<<(N + 127) / 128, 128, 0, c->stream>>>(margs(c), c->cell2dvm, c->W, c->gu, c->gT, c->wall_kin, out);
-    c->launches++;
+    if (wall && c->has_wall) launch_wall_flux(c);   // kinetic wall fluxes of the current f
+    launch_gradients(c, c->W, false);               // gradients of the current state
+    if (wall) {
+        k_wall_loads<<<(N + 127) / 128, 128, 0, c->stream>>>(margs(c), c->cell2dvm, c->W, c->gu, c->gT,
+                                                            c->wall_kin, c->fields);
+        c->launches++;
+    }
+    if (cons) {
+        k_constitutive<<<(N + 127) / 128, 128, 0, c->stream>>>(N, c->W, c->gu, c->gT, c->hot, c->mu0, c->p.omega,
+                                                               c->fields);
+        c->launches++;
+    }
 }
 
 // Cell residual R_c = -sum_F F.S_out (gathering the interior face fluxes in

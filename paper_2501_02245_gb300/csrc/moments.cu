@@ -22,6 +22,7 @@
 // n terms carries a relative rounding error below n * 2^-24 (< 4e-6 for
 // n = 64) of the sum of |terms|, far under the storage rounding of BF16/FP16
 // (2^-9 / 2^-12 per value) and comparable to FP32 storage rounding.
+#include <type_traits>
 #include "gsis_device.cuh"
 
 namespace gsis {
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     block_sum<MOMN>(acc, red);
     if (threadIdx.x == 0) {
         double* m = mom + (long long)k * MOMN;
-        for (int q = 0; q < MOMN; ++q) m[q] = acc[q] * vg.w;
+        const double wv = vg.w / vg.vscale;   // stored values carry the VDF storage scale
+        for (int q = 0; q < MOMN; ++q) m[q] = acc[q] * wv;
     }
 }
 
@@ -214,6 +216,54 @@ __device__ void shift_moments13(const double* m, const double d[3], double* o) {
 // cell adds the correction's outgoing wall sums to those of f^{n+1/2}.
 constexpr int CORR_UNROLL = 4;
 
+// Storage of the corrected value f + delta.  Near convergence delta is far
+// below half a unit in the last place of a BF16 or FP16 value, so rounding
+// to nearest would drop it every time (a systematic bias: the correction of
+// Eq. updatef would stop acting).  Reduced-precision storage therefore
+// rounds stochastically here: up with probability equal to the fraction of
+// the unit in the last place that the value carries, so the stored value is
+// unbiased and the increments survive on average over the velocities.  The
+// random bits come from a hash of the cell, the velocity and the new value's
+// own bits (deterministic, different from iteration to iteration because
+// the values change; no seed, so the same launch can be replayed in a graph).
+__device__ __forceinline__ unsigned mix32(unsigned x) {   // integer hash (avalanche), bits well mixed
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+template <typename T, typename S>
+__device__ __forceinline__ void st_corrected(S* p, T v, unsigned key) {
+    stT<T, S>(p, v);
+}
+template <>
+__device__ __forceinline__ void st_corrected<float, __nv_bfloat16>(__nv_bfloat16* p, float v, unsigned key) {
+    unsigned b = __float_as_uint(v);
+    if ((b & 0x7f800000u) == 0x7f800000u) {   // inf / nan: nearest
+        *p = __float2bfloat16_rn(v);
+        return;
+    }
+    const unsigned r = mix32(key ^ b) & 0xffffu;   // uniform below the 16 dropped bits of the magnitude
+    b += r;
+    *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+template <>
+__device__ __forceinline__ void st_corrected<float, __half>(__half* p, float v, unsigned key) {
+    const __half lo = __float2half_rz(v);                       // toward zero
+    const unsigned short lb = __half_as_ushort(lo);
+    if ((lb & 0x7c00u) == 0x7c00u) {                            // inf / nan
+        *p = __float2half_rn(v);
+        return;
+    }
+    const __half hi = __ushort_as_half((unsigned short)(lb + 1));   // next value away from zero
+    const float flo = __half2float(lo), fhi = __half2float(hi);
+    const float frac = (fabsf(v) - fabsf(flo)) / (fabsf(fhi) - fabsf(flo));   // in [0, 1)
+    const float u = (float)(mix32(key ^ __float_as_uint(v)) >> 8) * (1.0f / 16777216.0f);
+    *p = u < frac ? hi : lo;
+}
+
 template <typename S, typename T>
 __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__ dvm_cell,
                                                  const int* __restrict__ side_bc, const double* __restrict__ Sout,
@@ -265,7 +315,7 @@ __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__
                 const T aN = fma(xa[ix], rv[nyz + q], xa[nx + ix]);
                 const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
                 const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
-                stT<T, S>(fk + v, fv[j] + dlt);
+                st_corrected<T, S>(fk + v, fv[j] + dlt, (unsigned)k * 0x9e3779b9u ^ (unsigned)v * 0x85ebca6bu);
                 if (wall_mask && (!vg.reduced || q < ny)) {   // mass flux: the G plane on the reduced grid
                     const int iz = q / ny, iy = q - iz * ny;
                     const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
@@ -286,7 +336,9 @@ __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__
     if (threadIdx.x == 0) {
         const double* mh = momh + (long long)k * MOMN;
         double* m = mom + (long long)k * MOMN;
-        for (int s = 0; s < 6; ++s) m[13 + s] = mh[13 + s] + (((wall_mask >> s) & 1) ? vg.w * acc[s] : 0.0);
+        // (the increment is in stored units: its record copies carry the VDF storage scale)
+        const double wv = std::is_same<T, double>::value ? vg.w : vg.w / vg.vscale;
+        for (int s = 0; s < 6; ++s) m[13 + s] = mh[13 + s] + (((wall_mask >> s) & 1) ? wv * acc[s] : 0.0);
     }
 }
 
@@ -390,7 +442,7 @@ __global__ void __launch_bounds__(256) k_wall_rho(int Nd, const int* __restrict_
         int ix, iy, iz;
         vsplit(v, vg.nx, vg.ny, ix, iy, iz);
         const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
-        const double fv = Store<S>::ld(fk + v);
+        const double fv = Store<S>::ld(fk + v) / vg.vscale;
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
             if ((wall_mask >> s) & 1) {
@@ -534,7 +586,7 @@ __global__ void __launch_bounds__(256) k_wall_flux(int Nd, const int* __restrict
             const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
             const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
             if (xn > 0.0) {
-                const double g = xn * Store<S>::ld(fk + v);
+                const double g = xn * (Store<S>::ld(fk + v) / vg.vscale);
                 double psi[5];
                 psi_node(vg, x0, x1, x2, iz, psi);
                 acc[0] += g * psi[0];

@@ -32,7 +32,7 @@
 // 1D, 2D and 3D meshes); the rest is skipped.
 #include <map>
 #include <string>
-#include "sweep_device.cuh"
+#include "sweep_pair.cuh"
 
 namespace gsis {
 
@@ -69,6 +69,50 @@ __global__ void __launch_bounds__(32 * G) k_sweep(SweepArgs a, S* __restrict__ f
         sweep_tile<S, T, NC, G, VPT, CB, false>(a, f, pass);
 }
 
+// The same tile on pairs of velocities (FP32 arithmetic, sweep_pair.cuh): a
+// block owns 64 * VPT consecutive velocities, lane l the pairs 2l + 64u.
+template <typename S, int NC, int G, int VPT, int CB, bool FULL>
+__device__ __forceinline__ void sweep_tile2(const SweepArgs& a, S* __restrict__ f, int pass) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Vel2<VPT, FULL> V;
+    make_vel2(a.vg, (long long)blockIdx.x * (64 * VPT), lane, V);
+    for (int hh = 0; hh < a.H; ++hh) {
+        const int h = pass ? (a.H - 1 - hh) : hh;
+        const int kb = __ldg(a.hp_off + h), ke = __ldg(a.hp_off + h + 1);
+        const int n = ke - kb;
+        for (int i0 = w; i0 < n; i0 += G * CB) {
+            int kk[CB];
+            bool kon[CB];
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int i = i0 + b * G;
+                kon[b] = i < n;
+                kk[b] = pass ? (ke - 1 - i) : (kb + i);
+            }
+            update_cells2<S, NC, VPT, CB>(a, f, kk, kon, V);
+        }
+        if (G > 1) __syncthreads();
+    }
+}
+
+template <typename S, int NC, int G, int VPT, int CB>
+__global__ void __launch_bounds__(32 * G) k_sweep2(SweepArgs a, S* __restrict__ f, int pass) {
+    if ((long long)(blockIdx.x + 1) * (64 * VPT) <= a.vg.Nv)
+        sweep_tile2<S, NC, G, VPT, CB, true>(a, f, pass);
+    else
+        sweep_tile2<S, NC, G, VPT, CB, false>(a, f, pass);
+}
+
+template <typename S, int G, int VPT, int CB>
+static void sweep2_t(gsis_ctx* c, const SweepArgs& a, int pass) {
+    const unsigned blocks = (unsigned)((c->vg.Nv + 64 * VPT - 1) / (64 * VPT));
+    S* f = (S*)c->f;
+    if (c->normal_components == 2)
+        k_sweep2<S, 2, G, VPT, CB><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass);
+    else
+        k_sweep2<S, 3, G, VPT, CB><<<blocks, 32 * G, 0, c->stream>>>(a, f, pass);
+}
+
 template <typename S, typename T, int G, int VPT, int CB>
 static void sweep_t(gsis_ctx* c, const SweepArgs& a, int pass) {
     const unsigned blocks = (unsigned)((c->vg.Nv + 32 * VPT - 1) / (32 * VPT));
@@ -93,9 +137,15 @@ struct SweepShape {
 static const SweepShape kShapesF64[] = {
     {2, 1, 2, "g2_v1_c2"}, {1, 1, 2, "g1_v1_c2"}, {4, 1, 1, "g4_v1_c1"}, {2, 1, 1, "g2_v1_c1"},
     {8, 1, 1, "g8_v1_c1"}, {16, 1, 1, "g16_v1_c1"}};
+// (FP32 arithmetic: the p shapes update pairs of velocities with packed FP32
+// instructions, sweep_pair.cuh; they need an even nx and a 2D or 3D mesh.)
 static const SweepShape kShapesF32[] = {
     {8, 1, 1, "g8_v1_c1"}, {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"},
-    {4, 4, 1, "g4_v4_c1"}, {8, 4, 1, "g8_v4_c1"}, {4, 2, 2, "g4_v2_c2"}};
+    {4, 4, 1, "g4_v4_c1"}, {8, 4, 1, "g8_v4_c1"}, {4, 2, 2, "g4_v2_c2"},
+    {8, 1, 1, "p8_v1_c1"}, {4, 2, 1, "p4_v2_c1"}, {8, 2, 1, "p8_v2_c1"}, {4, 1, 1, "p4_v1_c1"}};
+constexpr int kFirstPairShape = 6;
+static bool pair_shape(int dtype, int shape) { return dtype != GSIS_F64 && shape >= kFirstPairShape && shape < 10; }
+static bool pair_ok(gsis_ctx* c) { return c->vg.nx % 2 == 0 && c->normal_components >= 2; }
 
 // Candidates after the register-stencil shapes: the shared-memory window
 // sweep (sweep_ring.cu) with 8 warps x 32, 4 warps x 32 and 8 warps x 64
@@ -123,6 +173,10 @@ static void sweep_f32_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape
         case 3: sweep_t<S, float, 4, 4, 1>(c, a, pass); break;
         case 4: sweep_t<S, float, 8, 4, 1>(c, a, pass); break;
         case 5: sweep_t<S, float, 4, 2, 2>(c, a, pass); break;
+        case 6: sweep2_t<S, 8, 1, 1>(c, a, pass); break;
+        case 7: sweep2_t<S, 4, 2, 1>(c, a, pass); break;
+        case 8: sweep2_t<S, 8, 2, 1>(c, a, pass); break;
+        case 9: sweep2_t<S, 4, 1, 1>(c, a, pass); break;
         default: sweep_t<S, float, 8, 1, 1>(c, a, pass); break;
     }
 }
@@ -145,6 +199,7 @@ static void launch_sweep_shape(gsis_ctx* c, const SweepArgs& a, int pass, int sh
         if (launch_sweep_ring(c, a, pass, shape - nb)) return;
         shape = 0;   // does not fit: register-stencil sweep
     }
+    if (pair_shape(c->p.vdf_dtype, shape) && !pair_ok(c)) shape = 0;   // odd nx or 1D: single velocities
     switch (c->p.vdf_dtype) {
         case GSIS_F64: sweep_f64_shape(c, a, pass, shape); break;
         case GSIS_F32: sweep_f32_shape<float>(c, a, pass, shape); break;
@@ -204,6 +259,8 @@ gsis_status force_sweep_shape(gsis_ctx* c, const char* name) {
             if (ring_bytes(c, which == 2 ? 64 : 32) == 0 || (c->p.vdf_dtype == GSIS_F64 && which == 2))
                 return set_err(c, GSIS_ERR_ARG, std::string("sweep tile ") + name + " does not fit this problem");
         }
+        if (pair_shape(c->p.vdf_dtype, sh) && !pair_ok(c))
+            return set_err(c, GSIS_ERR_ARG, std::string("sweep tile ") + name + " needs an even nx and a 2D/3D mesh");
         c->sweep_shape = sh;
         c->tuned_Nd = c->Nd;
         c->sweep_forced = true;
@@ -247,6 +304,7 @@ gsis_status tune_sweep(gsis_ctx* c) {
     for (int sh = 0; sh < ns; ++sh) {
         const int nb = base_shapes(c->p.vdf_dtype);
         if (sh >= nb && ring_bytes(c, sh - nb == 2 ? 64 : 32) == 0) continue;   // window does not fit
+        if (pair_shape(c->p.vdf_dtype, sh) && !pair_ok(c)) continue;
         if (sh >= nb && c->p.vdf_dtype == GSIS_F64 && sh - nb == 2) continue;
         launch_sweep_shape(c, a, 1, sh);
         launch_sweep_shape(c, a, 0, sh);

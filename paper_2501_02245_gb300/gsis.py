@@ -19,14 +19,16 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_STATE", "ERR_OOM", "ERR_CUDA", "ERR_NONFIN
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 DTYPE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 FIELDS = ["rho", "ux", "uy", "uz", "T", "hot_sxx", "hot_syy", "hot_szz", "hot_sxy", "hot_sxz", "hot_syz",
-          "hot_qx", "hot_qy", "hot_qz", "kn_gll", "dvm", "wall_q"]
+          "hot_qx", "hot_qy", "hot_qz", "kn_gll", "dvm", "wall_q",
+          "sxx", "syy", "szz", "sxy", "sxz", "syz", "qx", "qy", "qz", "p",
+          "wall_p", "wall_tx", "wall_ty", "wall_tz"]
 PHASES = ["adapt", "cell_eq", "sweep", "moments", "macro", "correct", "residual", "presolve"]
 
 EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
             "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
             "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments", "gsis_debug_set_macro_path",
-            "gsis_probe_fma_peak"]
+            "gsis_probe_fma_peak", "gsis_debug_set_batch_tile"]
 MACRO_PATHS = {"auto": 0, "fused": 1, "multi": 2, "persistent": 3, "persistent_stall": 4}
 
 
@@ -42,7 +44,8 @@ class Params(ctypes.Structure):
                 ("vdf_dtype", ctypes.c_int), ("macro_steps", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("k_sub", ctypes.c_int), ("dt", ctypes.c_double), ("tol", ctypes.c_double),
                 ("presolve_max_blocks", ctypes.c_int), ("spin_limit", ctypes.c_ulonglong),
-                ("relax", ctypes.c_double)]
+                ("relax", ctypes.c_double), ("d_r", ctypes.c_int), ("Z_r", ctypes.c_double),
+                ("A", ctypes.c_double * 4)]
 
 
 class Allocator(ctypes.Structure):
@@ -108,6 +111,8 @@ def load():
     lib.gsis_debug_vdf_moments.restype = c_int
     lib.gsis_debug_set_macro_path.argtypes = [vp, c_int]
     lib.gsis_debug_set_macro_path.restype = c_int
+    lib.gsis_debug_set_batch_tile.argtypes = [ctypes.c_char_p]
+    lib.gsis_debug_set_batch_tile.restype = c_int
     lib.gsis_probe_fma_peak.argtypes = [c_int, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]
     lib.gsis_probe_fma_peak.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
@@ -172,7 +177,8 @@ class Solver:
                    float(params.get("cfl", 5.0)), int(params.get("k_sub", 2)), float(params.get("dt", 0.0)),
                    float(params.get("tol", 1e-6)), int(params.get("presolve_max_blocks", 0)),
                    int(params.get("spin_limit", 0)),
-                   float(params.get("relax", 1.0)))
+                   float(params.get("relax", 1.0)), int(params.get("d_r", 0)), float(params.get("Z_r", 0.0)),
+                   (ctypes.c_double * 4)(*params.get("A", (0.0, 0.0, 0.0, 0.0))))
         self._alloc = None
         alloc_ptr = None
         stream_ptr = None
@@ -340,6 +346,14 @@ def iterate_batch(solvers, n):
         d["phase_ms"] = {PHASES[i]: rep.phase_ms[i] for i in range(8)}
         out.append(d)
     return out
+
+
+def set_batch_tile(name):
+    """Force the tile shape of batch plans recorded from now on (test hook);
+    None or "" restores autotuning."""
+    st = load().gsis_debug_set_batch_tile(name.encode() if name else None)
+    if st != GSIS_OK:
+        raise GsisError(st, "unknown batch tile %r" % name)
 
 
 def batch_info(solvers):

@@ -54,6 +54,17 @@ def test_init_rejects_bad_parameters(lib):
     assert lib.gsis_init(None, None, None, ctypes.byref(ctx)) == GSIS_ERR_ARG
 
 
+def test_init_refuses_internal_degrees_of_freedom(lib):
+    """d_r < 0 is invalid; d_r > 0 (the two-VDF model) is valid but not built."""
+    from paper_2501_02245_gb300.gsis import Params, GSIS_ERR_ARG, GSIS_ERR_UNSUPPORTED
+    ctx = ctypes.c_void_p()
+    base = dict(Kn=0.1, omega=0.74, adaptive=0, Kn_ref=0.0, adapt_every=5, wall_layers=2, vdf_dtype=0,
+                macro_steps=10, cfl=5.0, k_sub=2, dt=0.0, tol=1e-6, presolve_max_blocks=0, spin_limit=0)
+    for d_r, want in ((-1, GSIS_ERR_ARG), (2, GSIS_ERR_UNSUPPORTED)):
+        p = Params(**base, d_r=d_r, Z_r=2.667, A=(ctypes.c_double * 4)(0.786, -0.201, -0.059, 0.842))
+        assert lib.gsis_init(ctypes.byref(p), None, None, ctypes.byref(ctx)) == want
+
+
 def test_null_safety(lib):
     lib.gsis_free(None)
     assert lib.gsis_last_error(None) == b"NULL context"

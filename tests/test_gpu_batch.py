@@ -103,3 +103,47 @@ def test_batch_of_mixed_dimensions_matches_single_solves():
         assert e <= 4 * UNIT[dt], "%s %s batch vs single: %.3e" % (case.name, dt, e)
     for s in batch:
         s.close()
+
+
+@pytest.mark.parametrize("tile", ["pair1_cb1_w4", "pair2_cb1_w4", "pair1_cb1_w8", "vpt2_cb1_w4"])
+def test_batch_velocity_pair_tiles(tile):
+    """The persistent batched sweep on pairs of velocities (packed FP32
+    arithmetic; FP32/BF16/FP16 members with even nx) forced by the test hook:
+    every solve agrees with the same solve iterated alone within one storage
+    rounding unit, with a ragged last item (nv not a multiple of 64)."""
+    from paper_2501_02245_gb300 import Solver, iterate_batch, batch_info
+    from paper_2501_02245_gb300.gsis import set_batch_tile
+    specs = [(1.6, 23, (16, 8, 8), "f32"), (2.4, 37, (20, 10, 9), "bf16"), (3.1, 19, (24, 10, 10), "f16"),
+             (2.0, 26, (18, 9, 7), "f32")]
+    cases = []
+    for Ma, n, nv, dt in specs:
+        cases.append((shock_1d_case(Ma=Ma, n_cells=n, half_width=n / 4.0, nv=nv, vmax=8.0 + Ma, macro_steps=30), dt))
+    set_batch_tile(tile)
+    try:
+        batch = [Solver.from_case(c, vdf_dtype=dt) for c, dt in cases]
+        iterate_batch(batch, 3)
+        assert "tile=" + tile in batch_info(batch)
+    finally:
+        set_batch_tile(None)
+    for (case, dt), sb in zip(cases, batch):
+        single = Solver.from_case(case, vdf_dtype=dt)
+        single.iterate(3)
+        e = w_rel_err(sb.W(), single.W())
+        single.close()
+        assert e <= 4 * UNIT[dt], "%s %s batch vs single: %.3e" % (case.name, dt, e)
+    for s in batch:
+        s.close()
+
+
+def test_batch_pair_tile_refused_with_an_fp64_member():
+    from paper_2501_02245_gb300 import Solver, iterate_batch, GsisError
+    from paper_2501_02245_gb300.gsis import set_batch_tile
+    set_batch_tile("pair1_cb1_w4")
+    try:
+        batch = [Solver.from_case(c, vdf_dtype=dt) for c, dt in _cases()]
+        with pytest.raises(GsisError):
+            iterate_batch(batch, 1)
+        for s in batch:
+            s.close()
+    finally:
+        set_batch_tile(None)

@@ -293,3 +293,39 @@ def test_diverging_run_reports_nonfinite():
     assert ei.value.status == gsis.GSIS_ERR_STATE
     s.close()
 
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("bf16", 3e-3)])
+def test_full_size_cylinder_moments_reproduce_the_state(dtype, tol):
+    """The benchmark's own configuration (128 x 128 O-grid, 48 x 48 x 24
+    velocities, Ma 5, Kn 0.01, adaptive; a short presolve), where the oracle
+    cannot run: after the iterations the VDF of every kinetic cell, reduced
+    directly over all 55,296 velocities, carries the cell's density, velocity
+    and temperature (Eq. updatef leaves exactly the moments of W^{n+1};
+    reduced-precision storage: to its rounding), and the moments the
+    iteration carries forward equal that direct reduction."""
+    from helpers import moment_scales
+    case = cylinder_case(presolve_max_blocks=5)
+    case.tol = 0.0
+    s, hg, reps = _gpu(case, 2, vdf_dtype=dtype)
+    nd = reps[-1]["n_dvm"]
+    assert nd > 8000 and reps[-1]["n_v"] == 55296
+    direct = s.vdf_moments(nd, direct=True)
+    carried = s.vdf_moments(nd, direct=False)
+    # kinetic cells in the order of the compacted list: by hyperplane i + j (+ k), then flat index
+    flags = s.dvm_flags()
+    idx = np.nonzero(flags)[0]
+    ni, nj = case.mesh.ni, case.mesh.nj
+    hyper = idx % ni + (idx // ni) % nj + idx // (ni * nj)
+    cells = idx[np.lexsort((idx, hyper))]
+    assert len(cells) == nd
+    Wk = hg[-1][cells]
+    rho = direct[:, 0]
+    T = (direct[:, 4] + direct[:, 5] + direct[:, 6]) / (3.0 * rho)
+    assert np.max(np.abs(rho / Wk[:, 0] - 1.0)) < tol
+    assert np.max(np.abs(T / Wk[:, 4] - 1.0)) < tol
+    assert np.max(np.abs(direct[:, 1:4]) / (rho * np.sqrt(Wk[:, 4]))[:, None]) < tol
+    # carried moments are formed from the unrounded correction; the direct reduction sees the storage
+    # rounding of every corrected value (BF16: 2^-9 relative)
+    err = (np.abs(carried - direct) / moment_scales(direct)).max()
+    assert err < (1e-11 if dtype == "f64" else 3e-3), err
+    s.close()

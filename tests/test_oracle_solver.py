@@ -312,3 +312,85 @@ def test_wall_heat_flux_free_molecular_closed_form():
     assert len(walls) == 6                       # the first radial layer
     # velocity quadrature across the xi.n = 0 kink: 0.05 % for faces aligned with the grid, 0.7 % oblique
     assert np.max(np.abs(q[walls] / exact - 1)) < 1e-2
+
+
+def test_wall_loads_free_molecular_closed_forms():
+    """A DVM wall cell holding the Maxwellian of a gas drifting at speed U
+    along its wall face, next to a diffuse wall at T_w (kinetic theory of
+    free-molecular surface loads): the incoming half carries, per unit area,
+    the mass flux rho sqrt(T/2pi), the normal momentum rho T/2 and the
+    tangential momentum rho U sqrt(T/2pi); the emitted half rho_w M(0, T_w)
+    (rho_w sqrt(T_w) = rho sqrt(T)) adds the normal momentum
+    rho sqrt(T T_w)/2 and no tangential momentum.  So the wall pressure is
+    rho (T + sqrt(T T_w))/2, the shear rho U sqrt(T/2pi) along the drift,
+    and the heat flux into the wall rho sqrt(T/2pi) (2 (T - T_w) + U^2/2)."""
+    case = cylinder_case(Ma=2.0, Kn=0.1, n_r=4, n_theta=6, nv=(40, 40, 40), adaptive=False,
+                         vbox=((-9, 9), (-9, 9), (-9, 9)), presolve_max_blocks=0)
+    o = OracleSolver(case)
+    o.initialise()
+    Tg, rho, U = 1.3, 0.8, 0.6
+    geo = o.geo
+    Tw = case.mesh.bc_state[0][4]
+    walls = np.nonzero(geo.bT == BC_WALL)[0]
+    assert len(walls) == 6
+    tang = {}
+    for f_i in walls:
+        c = geo.bC[f_i]
+        n = geo.bn[f_i]
+        t = np.array([-n[1], n[0], 0.0])          # along the wall face, in the flow plane
+        tang[c] = (n, t)
+        o.f[c] = M.maxwellian(rho, U * t, Tg, o.vg.xi)
+    L = o.wall_loads()
+    a = rho * np.sqrt(Tg / (2 * np.pi))
+    for c, (n, t) in tang.items():
+        q, p, tau = L[c, 0], L[c, 1], L[c, 2:5]
+        # velocity quadrature across the xi.n = 0 kink (oblique faces): 1 %
+        assert abs(p / (0.5 * rho * (Tg + np.sqrt(Tg * Tw))) - 1) < 1e-2
+        assert np.linalg.norm(tau - a * U * t) < 1e-2 * a * U
+        assert abs(np.dot(tau, n)) < 1e-12                 # shear is tangential by construction
+        assert abs(q / (a * (2 * (Tg - Tw) + 0.5 * U * U)) - 1) < 1e-2
+    others = np.setdiff1d(np.arange(o.N), list(tang))
+    assert np.all(L[others] == 0.0)
+
+
+def test_wall_loads_of_ns_cells_at_rest_at_wall_temperature():
+    """An NS wall cell of a uniform gas at rest at T_w: the NSF wall flux has
+    no viscous stress and no heat flux, so the wall pressure is rho T_w and
+    the shear and heat flux vanish."""
+    case = cylinder_case(Ma=2.0, Kn=0.1, n_r=4, n_theta=6, nv=(8, 8, 4), adaptive=False,
+                         presolve_max_blocks=0)
+    o = OracleSolver(case)
+    o.initialise()
+    Tw = case.mesh.bc_state[0][4]
+    o.W[:] = [0.7, 0.0, 0.0, 0.0, Tw]
+    o.dvm[:] = False
+    L = o.wall_loads()
+    walls = np.unique(o.geo.bC[o.geo.bT == BC_WALL])
+    assert np.allclose(L[walls, 1], 0.7 * Tw, rtol=1e-13)
+    assert np.max(np.abs(L[walls][:, [0, 2, 3, 4]])) < 1e-13
+
+
+def test_constitutive_fields_are_the_kinetic_moments_at_the_half_step():
+    """Eq. full_constitutive: sigma_NSF(W) + HoT is the kinetic stress and
+    heat flux of f^{n+1/2} in DVM cells when evaluated at W = W^{n+1/2} (the
+    NSF parts cancel), and the NSF values in NS cells."""
+    case = cylinder_case(Ma=2.0, Kn=0.1, n_r=5, n_theta=8, nv=(10, 10, 6), adaptive=True, Kn_ref=0.05,
+                         vbox=((-8, 8), (-8, 8), (-8, 8)), presolve_max_blocks=2)
+    case.macro_steps = 10
+    o = OracleSolver(case)
+    o.initialise()
+    o.step()
+    assert 0 < o.dvm.sum() < o.N
+    o.W = o.W_half.copy()
+    sig, q = o.constitutive()
+    sig_n, q_n = o.nsf_field(o.W_half)
+    # the kinetic moments of f^{n+1/2}: f^{n+1} minus the correction of Eq. updatef
+    W_new = o.W_history[-1]
+    for c in np.nonzero(o.dvm)[0]:
+        fh = o.f[c] - (o.vg.corrected_maxwellian(W_new[c, 0], W_new[c, 1:4], W_new[c, 4]) -
+                       o.vg.corrected_maxwellian(o.W_half[c, 0], o.W_half[c, 1:4], o.W_half[c, 4]))
+        _, _, _, sk, qk = o.vg.moments(fh)
+        assert np.max(np.abs(sig[c] - sk)) < 1e-11 * max(1.0, np.max(np.abs(sk)))
+        assert np.max(np.abs(q[c] - qk)) < 1e-11 * max(1.0, np.max(np.abs(qk)))
+    ns = ~o.dvm
+    assert np.array_equal(sig[ns], sig_n[ns]) and np.array_equal(q[ns], q_n[ns])
