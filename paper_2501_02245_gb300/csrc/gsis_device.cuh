@@ -49,9 +49,59 @@ template <> __device__ __forceinline__ void stT<float, float>(float* p, float v)
 template <> __device__ __forceinline__ void stT<float, __nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ void stT<float, __half>(__half* p, float v) { *p = __float2half_rn(v); }
 
+// One 16-byte load of VEC16<S> consecutive stored values (p 16-byte aligned),
+// converted to the arithmetic type T.
+template <typename S> struct Vec16 { static constexpr int N = 16 / (int)sizeof(S); };
+template <typename T, typename S> __device__ __forceinline__ void ld16(const S* p, T* out);
+template <> __device__ __forceinline__ void ld16<double, double>(const double* p, double* out) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    out[0] = v.x; out[1] = v.y;
+}
+template <> __device__ __forceinline__ void ld16<float, float>(const float* p, float* out) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+__device__ __forceinline__ void bf16x2_to_f(unsigned w, float* o) {   // element 0 in the low half
+    o[0] = __uint_as_float(w << 16);
+    o[1] = __uint_as_float(w & 0xffff0000u);
+}
+__device__ __forceinline__ void f16x2_to_f(unsigned w, float* o) {
+    const float2 t = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    o[0] = t.x;
+    o[1] = t.y;
+}
+template <> __device__ __forceinline__ void ld16<float, __nv_bfloat16>(const __nv_bfloat16* p, float* out) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    bf16x2_to_f(v.x, out); bf16x2_to_f(v.y, out + 2); bf16x2_to_f(v.z, out + 4); bf16x2_to_f(v.w, out + 6);
+}
+template <> __device__ __forceinline__ void ld16<float, __half>(const __half* p, float* out) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    f16x2_to_f(v.x, out); f16x2_to_f(v.y, out + 2); f16x2_to_f(v.z, out + 4); f16x2_to_f(v.w, out + 6);
+}
+
 // ---------------------------------------------------------------- small math
-__device__ __forceinline__ double minmod(double a, double b) {
-    return (a > 0.0 && b > 0.0) ? fmin(a, b) : ((a < 0.0 && b < 0.0) ? fmax(a, b) : 0.0);
+// minmod(a, b): 0 unless a and b share a sign, else the one nearer zero.
+template <typename T>
+__device__ __forceinline__ T minmod_t(T a, T b) {
+    const T m = fabs(a) < fabs(b) ? a : b;
+    return a * b > T(0) ? m : T(0);
+}
+
+// Half the minmod, 0.5 minmod(a, b).  FP64: decisions on the bit patterns and the halving as a decrement of the exponent field, all on the
+// integer pipe (GB300 issues FP64 at 1/64 of the FP32 rate).  Magnitudes of
+// IEEE doubles order like their bit patterns with the sign bit cleared, and
+// +-0 never shares a sign, so the result equals 0.5 minmod_t(a, b) for every
+// result of magnitude >= 2^-1021; a smaller one (300 orders of magnitude
+// below any value of the scheme) gives 0.
+template <typename T> __device__ __forceinline__ T hmm_t(T a, T b);
+template <> __device__ __forceinline__ float hmm_t<float>(float a, float b) { return 0.5f * minmod_t<float>(a, b); }
+template <> __device__ __forceinline__ double hmm_t<double>(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    const bool a_smaller = ma < mb;
+    const long long m = a_smaller ? ia : ib, mm = a_smaller ? ma : mb;
+    const bool ok = (ia ^ ib) >= 0 && mm >= (2LL << 52);   // same sign, |result| >= 2^-1021 (so nonzero)
+    return ok ? __longlong_as_double(m - (1LL << 52)) : 0.0;
 }
 
 // mu0 T^omega as exp(omega ln T): within a few ulp of the power (relative

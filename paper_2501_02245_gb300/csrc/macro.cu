@@ -57,7 +57,7 @@ __device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double*
                                                double* gT, double* grho, double* gU, double* acell, int c) {
     const double* wc = Wp + c * 5;
     if (acell) acell[c] = sqrt(GAMMA * wc[4]);
-    const double Uc = sqrt(wc[1] * wc[1] + wc[2] * wc[2] + wc[3] * wc[3]);
+    const double Uc = with_rho_U ? sqrt(wc[1] * wc[1] + wc[2] * wc[2] + wc[3] * wc[3]) : 0.0;
     double g[6][3];
     for (int q = 0; q < 6; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0;
     for (int s = 0; s < 6; ++s) {
@@ -323,17 +323,18 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     const double* G = a.fgeo + ((long long)L * 3 + d) * 8;
     const double Sabs = G[0];
     const double nn[3] = {G[1], G[2], G[3]};
-    double qL[5], qR[5], slL[5] = {0, 0, 0, 0, 0}, slR[5] = {0, 0, 0, 0, 0};
+    // MUSCL face states: q -/+ 0.5 minmod of the one-sided differences (the
+    // halved limiter on the integer pipe), first order where the second
+    // neighbour is missing
+    double qL[5], qR[5], mL[5] = {0, 0, 0, 0, 0}, mR[5] = {0, 0, 0, 0, 0};
     prim5(Wm + L * 5, qL);
     prim5(Wm + Rr * 5, qR);
     {
-        const int lo = a.nbr[L * 6 + 2 * d], hi = Rr;
+        const int lo = a.nbr[L * 6 + 2 * d];
         if (lo >= 0) {
             double ql[5];
             prim5(Wm + lo * 5, ql);
-            for (int q = 0; q < 5; ++q) slL[q] = minmod(qL[q] - ql[q], qR[q] - qL[q]);
-
-            (void)hi;
+            for (int q = 0; q < 5; ++q) mL[q] = hmm_t<double>(qL[q] - ql[q], qR[q] - qL[q]);
         }
     }
     {
@@ -341,12 +342,11 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
         if (hi >= 0) {
             double qh[5];
             prim5(Wm + hi * 5, qh);
-            for (int q = 0; q < 5; ++q) slR[q] = minmod(qR[q] - qL[q], qh[q] - qR[q]);
-
+            for (int q = 0; q < 5; ++q) mR[q] = hmm_t<double>(qR[q] - qL[q], qh[q] - qR[q]);
         }
     }
     double fl[5], fr[5];
-    for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + 0.5 * slL[q]; fr[q] = qR[q] - 0.5 * slR[q]; }
+    for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + mL[q]; fr[q] = qR[q] - mR[q]; }
     double Fv[5];
     kfvs(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, Fv);
     for (int q = 0; q < 5; ++q) Fv[q] *= Sabs;
@@ -527,7 +527,7 @@ void launch_fields(gsis_ctx* c, bool wall, bool cons) {
 
 // Cell residual R_c = -sum_F F.S_out (gathering the interior face fluxes in
 // side order, boundary faces evaluated here), lambda|S| per side, the
-// diagonal D and dU0 = R/D.
+// reciprocal 1/D of the diagonal (in D) and dU0 = R/D.
 __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const double* Wm, const double* U,
                                                   const double* Un, const double* gu, const double* gT,
                                                   const double* hot, const double* Ff, const double* lamf,
@@ -594,8 +594,8 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
         for (int q = 0; q < 5; ++q) Rc[q] -= Vdt * (U[c * 5 + q] - Un[c * 5 + q]);
         Dc += Vdt;
     }
-    D[c] = Dc;
     const double iD = 1.0 / Dc;
+    D[c] = iD;   // the relaxation sweeps multiply by the reciprocal
     for (int q = 0; q < 5; ++q) {
         R[c * 5 + q] = Rc[q];
         dU[c * 5 + q] = Rc[q] * iD;
@@ -635,7 +635,7 @@ __device__ __forceinline__ void relax_one(const MacroArgs& a, const double* U, c
             off[q] += 0.5 * (dFS - ls * dUin[n * 5 + q]);
         }
     }
-    const double iD = 1.0 / D[c];
+    const double iD = D[c];   // 1 / D
     for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) * iD;
     if (dFout) flux_change(U, dUout, F0, dFout, c);
 }
@@ -648,6 +648,7 @@ __global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double*
     if (c < a.N) relax_one(a, U, R, D, lamS, dUin, dUout, dFin, dFout, F0, c);
 }
 
+
 __device__ __forceinline__ void update_one(double* U, const double* dU, double* Wm, int c) {
     for (int q = 0; q < 5; ++q) U[c * 5 + q] += dU[c * 5 + q];
     cons_to_prim(U + c * 5, Wm + c * 5);
@@ -656,6 +657,20 @@ __device__ __forceinline__ void update_one(double* U, const double* dU, double* 
 __global__ void k_update(int N, double* __restrict__ U, const double* __restrict__ dU, double* __restrict__ Wm) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < N) update_one(U, dU, Wm, c);
+}
+
+// The last Jacobi sweep of a pseudo-step followed by the update of the
+// cell's own state (U += dU, primitive Wm): the sweep reads U only through the
+// flux change, which the last sweep does not form, so each cell may update
+// its state in place (one launch instead of two, the same values).
+__global__ void k_relax_update(MacroArgs a, double* __restrict__ U, const double* __restrict__ R,
+                               const double* __restrict__ D, const double* __restrict__ lamS,
+                               const double* __restrict__ dUin, double* __restrict__ dUout,
+                               const double* __restrict__ dFin, double* __restrict__ Wm) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    relax_one(a, U, R, D, lamS, dUin, dUout, dFin, nullptr, nullptr, c);
+    update_one(U, dUout, Wm, c);
 }
 
 // The whole pseudo-time block of one solve in one thread-block cluster of
@@ -949,13 +964,19 @@ void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term, bool cap
         double* dout = c->dU2;
         for (int s = 0; s < c->p.k_sub; ++s) {
             double* fin = (s & 1) ? c->dFb : c->dFa;
-            double* fout = s + 1 < c->p.k_sub ? ((s & 1) ? c->dFa : c->dFb) : nullptr;
-            k_relax<<<nb, TB, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout, fin, fout, c->F0);
+            if (s + 1 < c->p.k_sub) {
+                double* fout = (s & 1) ? c->dFa : c->dFb;
+                k_relax<<<nb, TB, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout, fin, fout, c->F0);
+            } else {
+                k_relax_update<<<nb, TB, 0, c->stream>>>(a, c->U, c->R, c->D, c->lamS, din, dout, fin, c->Wm);
+            }
             c->launches++;
             double* t = din; din = dout; dout = t;
         }
-        k_update<<<nb, TB, 0, c->stream>>>(N, c->U, din, c->Wm);
-        c->launches++;
+        if (c->p.k_sub == 0) {
+            k_update<<<nb, TB, 0, c->stream>>>(N, c->U, din, c->Wm);
+            c->launches++;
+        }
     }
 }
 

@@ -10,7 +10,9 @@
 //   m[13+s] = sum_{xi.S_s > 0} w (xi.S_s) f for wall sides s (outgoing mass
 //   flux through the wall face, for the diffuse-wall density).
 //
-// Row factoring: a thread owns whole x-rows (fixed iy, iz) of the cell's VDF.
+// Row factoring: a thread owns whole x-rows (fixed iy, iz) of the cell's VDF,
+// read as 16-byte loads where the rows are aligned (a warp's scalar loads
+// would touch 32 rows each and cost one L1 wavefront per row per value).
 // Per point it accumulates only sum f c_x^k, k = 0..3 (c_x^k from shared
 // memory), and folds the row sums into the 13 moments with the row constants
 // c_y, c_z once per row.  The correction pass (k_correct) gets the moments of
@@ -27,8 +29,56 @@
 
 namespace gsis {
 
+// ---------------------------------------------------------------- outgoing wall sums by rows
+// On one x-row (fixed xi_y, xi_z) the normal speed through a wall side of area
+// vector S is xi.S = xi_x S_x + r with r = xi_y S_y + xi_z S_z, monotone in ix
+// (xi_x increases with ix), so the outgoing nodes (xi.S > 0) form one range
+// [lo, hi) of ix, found by bisection.  Over the row, with A_j = sum_range xi_x^j f,
+//   sum_range (xi.S) f = S_x A_1 + r A_0 = m_0,
+//   sum_range (xi.S) xi_x^j f = S_x A_{j+1} + r A_j = m_j,
+// so a row costs one to four sums per outgoing node and no FP64 per node.
+__device__ __forceinline__ void out_range(const double* __restrict__ xi, int nx, double Sx, double r, int& lo,
+                                          int& hi) {
+    int a = 0, b = nx;
+    if (Sx > 0.0) {          // first node with xi.S > 0
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (fma(xi[m], Sx, r) > 0.0) b = m; else a = m + 1;
+        }
+        lo = a; hi = nx;
+    } else if (Sx < 0.0) {   // first node with xi.S <= 0
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (fma(xi[m], Sx, r) > 0.0) a = m + 1; else b = m;
+        }
+        lo = 0; hi = a;
+    } else {
+        lo = 0; hi = r > 0.0 ? nx : 0;
+    }
+}
+
+// The conserved-quantity weights psi (mass, momentum x/y/z, energy) on row
+// (xi_y = x1, xi_z = x2, plane iz) as a + b xi_x + c xi_x^2: (1, xi_x, xi_y,
+// xi_z, |xi|^2 / 2) on the 3D grid and the G plane of the reduced grid (whose
+// xi_z entries are 0), (0, 0, 0, 0, 1/2) on the H plane.
+__device__ __forceinline__ void psi_row(const VGridDev& vg, double x1, double x2, int iz, double* a, double* b,
+                                        double* c) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) a[q] = b[q] = c[q] = 0.0;
+    if (vg.reduced && iz != 0) {
+        a[4] = 0.5;
+        return;
+    }
+    a[0] = 1.0;
+    b[1] = 1.0;
+    a[2] = x1;
+    a[3] = x2;
+    a[4] = 0.5 * (x1 * x1 + x2 * x2);
+    c[4] = 0.5;
+}
+
 template <typename S, typename T>
-__global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__ dvm_cell,
+__global__ void __launch_bounds__(256, 3) k_moments(int Nd, const int* __restrict__ dvm_cell,
                                                  const double* __restrict__ Wref, const int* __restrict__ side_bc,
                                                  const double* __restrict__ Sout, const S* __restrict__ f, VGridDev vg,
                                                  double* __restrict__ mom) {
@@ -40,14 +90,16 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     const int nx = vg.nx, ny = vg.ny, nz = vg.nz;
     const int c = dvm_cell[k];
     const double ux = Wref[c * 5 + 1], uy = Wref[c * 5 + 2], uz = Wref[c * 5 + 3];
-    T* scx = sh;                 // c_x, c_x^2, c_x^3
+    T* scx = sh;                 // c_x, c_x^2, c_x^3, xi_x
     T* scx2 = sh + nx;
     T* scx3 = sh + 2 * nx;
+    T* sxi = sh + 3 * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const double cx = vg.xi[i] - ux;
         scx[i] = (T)cx;
         scx2[i] = (T)(cx * cx);
         scx3[i] = (T)(cx * cx * cx);
+        sxi[i] = (T)vg.xi[i];
     }
     __syncthreads();
     int wall_mask = 0;
@@ -58,35 +110,41 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
     for (int q = 0; q < MOMN; ++q) acc[q] = 0.0;
     const S* fk = f + (long long)k * vg.Nv;
     const int rows = ny * nz;
+    // Rows start on 16-byte boundaries when nx is a multiple of the values per
+    // 16 bytes (the VDF allocation is 256-byte aligned and a cell holds whole rows).
+    constexpr int V = Vec16<S>::N;
+    const bool vec = nx % V == 0;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
         const int iy = r % ny, iz = r / ny;
         const int jy = nx + iy, jz = nx + ny + iz;
         const double xy = vg.xi[jy], xz = vg.xi[jz];
         const double cy = xy - uy, cz = xz - uz;
-        // plane weights of c_z^k on the reduced grid; the wall-flux sums below carry mass, which
-        // only the G plane holds there
+        // plane weights of c_z^k on the reduced grid
         double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
         if (vg.reduced) {
             z0 = zpow(vg, iz, cz, 0); z1 = zpow(vg, iz, cz, 1); z2 = zpow(vg, iz, cz, 2); z3 = zpow(vg, iz, cz, 3);
         }
-        const bool mass_row = !vg.reduced || iz == 0;
         const S* row = fk + (long long)r * nx;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-        for (int ix = 0; ix < nx; ++ix) {
-            const T fv = ldT<T, S>(row + ix);
-            s0 += fv;
-            s1 += fv * scx[ix];
-            s2 += fv * scx2[ix];
-            s3 += fv * scx3[ix];
-            if (wall_mask && mass_row) {
+        if (vec) {   // the row as 16-byte loads (same order of the sums)
+            for (int ix0 = 0; ix0 < nx; ix0 += V) {
+                T fv[V];
+                ld16<T, S>(row + ix0, fv);
 #pragma unroll
-                for (int s = 0; s < 6; ++s) {
-                    if ((wall_mask >> s) & 1) {
-                        const double* Sw = Sout + ((long long)c * 6 + s) * 3;
-                        const double xn = vg.xi[ix] * Sw[0] + xy * Sw[1] + xz * Sw[2];
-                        if (xn > 0.0) acc[13 + s] += xn * (double)fv;
-                    }
+                for (int j = 0; j < V; ++j) {
+                    s0 += fv[j];
+                    s1 += fv[j] * scx[ix0 + j];
+                    s2 += fv[j] * scx2[ix0 + j];
+                    s3 += fv[j] * scx3[ix0 + j];
                 }
+            }
+        } else {
+            for (int ix = 0; ix < nx; ++ix) {
+                const T fv = ldT<T, S>(row + ix);
+                s0 += fv;
+                s1 += fv * scx[ix];
+                s2 += fv * scx2[ix];
+                s3 += fv * scx3[ix];
             }
         }
         const double d0 = s0, d1 = s1, d2 = s2, d3 = s3;
@@ -121,6 +179,30 @@ __global__ void __launch_bounds__(256) k_moments(int Nd, const int* __restrict__
             acc[11] += cy * (d2 + d0 * cy2) * z0 + cy * d0 * z2;         // c_y c^2
             acc[12] += (d2 + d0 * cy2) * z1 + d0 * z3;                   // c_z c^2
         }
+    }
+    if (wall_mask) {   // outgoing mass flux through each wall side, row by row (mass rows only)
+        double wsum[6] = {0, 0, 0, 0, 0, 0};
+        const int mrows = vg.reduced ? ny : rows;
+        for (int r = threadIdx.x; r < mrows; r += blockDim.x) {
+            const double xy = vg.xi[nx + r % ny], xz = vg.xi[nx + ny + r / ny];
+            const S* row = fk + (long long)r * nx;
+            for (int s = 0; s < 6; ++s) {
+                if (!((wall_mask >> s) & 1)) continue;
+                const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+                const double rr = xy * Sw[1] + xz * Sw[2];
+                int lo, hi;
+                out_range(vg.xi, nx, Sw[0], rr, lo, hi);
+                T a0 = T(0), a1 = T(0);
+                for (int ix = lo; ix < hi; ++ix) {
+                    const T fv = ldT<T, S>(row + ix);
+                    a0 += fv;
+                    a1 += fv * sxi[ix];
+                }
+                wsum[s] += Sw[0] * (double)a1 + rr * (double)a0;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 6; ++s) acc[13 + s] = wsum[s];
     }
     block_sum<MOMN>(acc, red);
     if (threadIdx.x == 0) {
@@ -210,11 +292,15 @@ __device__ void shift_moments13(const double* m, const double d[3], double* o) {
 // with per-x values (E, E B) and per-(y, z) values e = E_y E_z,
 // p = p0 + B_y + B_z held in shared memory each point costs
 //   a_N = E_x p_N + (E B)_x,  a_H likewise,  f += e_N a_N - e_H a_H
-// (five operations).  Each thread loads four points before it stores any (the
-// loads and stores go through the same pointer, so the compiler would not
-// move a load above an earlier store), keeping four loads in flight.  A wall
+// (five operations).  Where the x-rows hold whole 16-byte chunks a thread
+// loads and stores 16 bytes (2 to 8 values) at a time, two chunks in flight,
+// else four scalar points; every thread loads before it stores (the loads and
+// stores go through the same pointer, so the compiler would not move a load
+// above an earlier store).  Both forms compute the same values in the same
+// order (bitwise equal results).  A wall
 // cell adds the correction's outgoing wall sums to those of f^{n+1/2}.
 constexpr int CORR_UNROLL = 4;
+constexpr int CORR_VEC_UNROLL = 2;
 
 // Storage of the corrected value f + delta.  Near convergence delta is far
 // below half a unit in the last place of a BF16 or FP16 value, so rounding
@@ -235,33 +321,32 @@ __device__ __forceinline__ unsigned mix32(unsigned x) {   // integer hash (avala
     return x;
 }
 template <typename T, typename S>
-__device__ __forceinline__ void st_corrected(S* p, T v, unsigned key) {
-    stT<T, S>(p, v);
+__device__ __forceinline__ S rounded(T v, unsigned key) {
+    S o;
+    stT<T, S>(&o, v);
+    return o;
 }
 template <>
-__device__ __forceinline__ void st_corrected<float, __nv_bfloat16>(__nv_bfloat16* p, float v, unsigned key) {
+__device__ __forceinline__ __nv_bfloat16 rounded<float, __nv_bfloat16>(float v, unsigned key) {
     unsigned b = __float_as_uint(v);
-    if ((b & 0x7f800000u) == 0x7f800000u) {   // inf / nan: nearest
-        *p = __float2bfloat16_rn(v);
-        return;
-    }
+    if ((b & 0x7f800000u) == 0x7f800000u) return __float2bfloat16_rn(v);   // inf / nan: nearest
     const unsigned r = mix32(key ^ b) & 0xffffu;   // uniform below the 16 dropped bits of the magnitude
     b += r;
-    *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
 }
 template <>
-__device__ __forceinline__ void st_corrected<float, __half>(__half* p, float v, unsigned key) {
+__device__ __forceinline__ __half rounded<float, __half>(float v, unsigned key) {
     const __half lo = __float2half_rz(v);                       // toward zero
     const unsigned short lb = __half_as_ushort(lo);
-    if ((lb & 0x7c00u) == 0x7c00u) {                            // inf / nan
-        *p = __float2half_rn(v);
-        return;
-    }
+    if ((lb & 0x7c00u) == 0x7c00u) return __float2half_rn(v);  // inf / nan
     const __half hi = __ushort_as_half((unsigned short)(lb + 1));   // next value away from zero
     const float flo = __half2float(lo), fhi = __half2float(hi);
     const float frac = (fabsf(v) - fabsf(flo)) / (fabsf(fhi) - fabsf(flo));   // in [0, 1)
     const float u = (float)(mix32(key ^ __float_as_uint(v)) >> 8) * (1.0f / 16777216.0f);
-    *p = u < frac ? hi : lo;
+    return u < frac ? hi : lo;
+}
+__device__ __forceinline__ unsigned corr_key(int k, int v) {
+    return (unsigned)k * 0x9e3779b9u ^ (unsigned)v * 0x85ebca6bu;
 }
 
 template <typename S, typename T>
@@ -299,37 +384,66 @@ __global__ void __launch_bounds__(256) k_correct(int Nd, const int* __restrict__
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     S* fk = f + (long long)k * vg.Nv;
-    const int Nv = (int)vg.Nv, step = blockDim.x, sx = step % nx, sq = step / nx;
-    int ix = threadIdx.x % nx, q = threadIdx.x / nx;
-    for (int v0 = threadIdx.x; v0 < Nv; v0 += CORR_UNROLL * step) {
-        T fv[CORR_UNROLL];
-#pragma unroll
-        for (int j = 0; j < CORR_UNROLL; ++j) {
-            const int v = v0 + j * step;
-            fv[j] = v < Nv ? ldT<T, S>(fk + v) : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < CORR_UNROLL; ++j) {
-            const int v = v0 + j * step;
-            if (v < Nv) {
-                const T aN = fma(xa[ix], rv[nyz + q], xa[nx + ix]);
-                const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
-                const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
-                st_corrected<T, S>(fk + v, fv[j] + dlt, (unsigned)k * 0x9e3779b9u ^ (unsigned)v * 0x85ebca6bu);
-                if (wall_mask && (!vg.reduced || q < ny)) {   // mass flux: the G plane on the reduced grid
-                    const int iz = q / ny, iy = q - iz * ny;
-                    const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
-                    for (int s = 0; s < 6; ++s) {
-                        if (!((wall_mask >> s) & 1)) continue;
-                        const double* Sw = Sout + ((long long)c * 6 + s) * 3;
-                        const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
-                        if (xn > 0.0) acc[s] += xn * (double)dlt;
-                    }
-                }
+    const int Nv = (int)vg.Nv, step = blockDim.x;
+    // the increment at velocity (ix, q) and the outgoing wall sums of it
+    auto delta = [&](int ix, int q) -> T {
+        const T aN = fma(xa[ix], rv[nyz + q], xa[nx + ix]);
+        const T aH = fma(xa[2 * nx + ix], rv[3 * nyz + q], xa[3 * nx + ix]);
+        const T dlt = fma(rv[q], aN, -(rv[2 * nyz + q] * aH));
+        if (wall_mask && (!vg.reduced || q < ny)) {   // mass flux: the G plane on the reduced grid
+            const int iz = q / ny, iy = q - iz * ny;
+            const double x0 = vg.xi[ix], x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
+            for (int s = 0; s < 6; ++s) {
+                if (!((wall_mask >> s) & 1)) continue;
+                const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+                const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
+                if (xn > 0.0) acc[s] += xn * (double)dlt;
             }
-            ix += sx;
-            q += sq;
-            if (ix >= nx) { ix -= nx; ++q; }
+        }
+        return dlt;
+    };
+    constexpr int V = Vec16<S>::N;
+    if (nx % V == 0) {
+        // 16-byte chunks of V consecutive velocities (one x-row holds whole chunks;
+        // rows start on 16-byte boundaries), two chunks in flight per thread
+        const int nch = Nv / V;
+        for (int ch0 = threadIdx.x; ch0 < nch; ch0 += CORR_VEC_UNROLL * step) {
+            T fv[CORR_VEC_UNROLL][V];
+#pragma unroll
+            for (int u = 0; u < CORR_VEC_UNROLL; ++u) {
+                const int ch = ch0 + u * step;
+                if (ch < nch) ld16<T, S>(fk + (long long)ch * V, fv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < CORR_VEC_UNROLL; ++u) {
+                const int ch = ch0 + u * step;
+                if (ch >= nch) continue;
+                const int v0 = ch * V, q = v0 / nx, ix0 = v0 - q * nx;
+                alignas(16) S out[V];
+#pragma unroll
+                for (int j = 0; j < V; ++j)
+                    out[j] = rounded<T, S>(fv[u][j] + delta(ix0 + j, q), corr_key(k, v0 + j));
+                *reinterpret_cast<uint4*>(fk + (long long)v0) = *reinterpret_cast<const uint4*>(out);
+            }
+        }
+    } else {
+        const int sx = step % nx, sq = step / nx;
+        int ix = threadIdx.x % nx, q = threadIdx.x / nx;
+        for (int v0 = threadIdx.x; v0 < Nv; v0 += CORR_UNROLL * step) {
+            T fv[CORR_UNROLL];
+#pragma unroll
+            for (int j = 0; j < CORR_UNROLL; ++j) {
+                const int v = v0 + j * step;
+                fv[j] = v < Nv ? ldT<T, S>(fk + v) : T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < CORR_UNROLL; ++j) {
+                const int v = v0 + j * step;
+                if (v < Nv) fk[v] = rounded<T, S>(fv[j] + delta(ix, q), corr_key(k, v));
+                ix += sx;
+                q += sq;
+                if (ix >= nx) { ix -= nx; ++q; }
+            }
         }
     }
     if (wall_mask) block_sum<6>(acc, red);
@@ -421,7 +535,7 @@ void launch_correct(gsis_ctx* c) {
 // with the latest outgoing half of f (the forward pass takes the values of
 // the cell-equilibrium step, computed from f^n).  One block per DVM cell;
 // cells without a wall side return at once.
-template <typename S>
+template <typename S, typename T>
 __global__ void __launch_bounds__(256) k_wall_rho(int Nd, const int* __restrict__ dvm_cell,
                                                   const int* __restrict__ side_bc, const double* __restrict__ Sout,
                                                   const S* __restrict__ f, VGridDev vg,
@@ -435,28 +549,38 @@ __global__ void __launch_bounds__(256) k_wall_rho(int Nd, const int* __restrict_
         if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
     if (!wall_mask) return;
     __shared__ double red[32 * 6];
+    extern __shared__ double sh_raw[];
+    T* sxi = reinterpret_cast<T*>(sh_raw);   // xi_x
+    const int nx = vg.nx, ny = vg.ny;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) sxi[i] = (T)vg.xi[i];
+    __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const S* fk = f + (long long)k * vg.Nv;
-    const long long nmass = vg.reduced ? (long long)vg.nx * vg.ny : vg.Nv;   // mass: the G plane if reduced
-    for (long long v = threadIdx.x; v < nmass; v += blockDim.x) {
-        int ix, iy, iz;
-        vsplit(v, vg.nx, vg.ny, ix, iy, iz);
-        const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
-        const double fv = Store<S>::ld(fk + v) / vg.vscale;
+    const int rows = vg.reduced ? ny : ny * vg.nz;   // mass: the G plane if reduced
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double x1 = vg.xi[nx + r % ny], x2 = vg.xi[nx + ny + r / ny];
+        const S* row = fk + (long long)r * nx;
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
-            if ((wall_mask >> s) & 1) {
-                const double* Sw = Sout + ((long long)c * 6 + s) * 3;
-                const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
-                if (xn > 0.0) acc[s] += xn * fv;
+            if (!((wall_mask >> s) & 1)) continue;
+            const double* Sw = Sout + ((long long)c * 6 + s) * 3;
+            const double rr = x1 * Sw[1] + x2 * Sw[2];
+            int lo, hi;
+            out_range(vg.xi, nx, Sw[0], rr, lo, hi);
+            T a0 = T(0), a1 = T(0);
+            for (int ix = lo; ix < hi; ++ix) {
+                const T fv = ldT<T, S>(row + ix);
+                a0 += fv;
+                a1 += fv * sxi[ix];
             }
+            acc[s] += Sw[0] * (double)a1 + rr * (double)a0;
         }
     }
     block_sum<6>(acc, red);
     if (threadIdx.x == 0) {
         for (int s = 0; s < 6; ++s) {
             if ((wall_mask >> s) & 1) {
-                const double v = acc[s] * vg.w / wall_den[c * 6 + s];
+                const double v = acc[s] * (vg.w / vg.vscale) / wall_den[c * 6 + s];
                 rho_w[(long long)k * 6 + s] = v;
                 if (rho_wf) rho_wf[(long long)k * 6 + s] = (float)v;
             }
@@ -464,36 +588,29 @@ __global__ void __launch_bounds__(256) k_wall_rho(int Nd, const int* __restrict_
     }
 }
 
-void launch_wall_rho(gsis_ctx* c) {
+template <typename S, typename T>
+static void wall_rho_t(gsis_ctx* c) {
     const int Nd = (int)c->Nd;
-    if (Nd == 0 || !c->has_wall) return;
-    switch (c->p.vdf_dtype) {
-        case GSIS_F64:
-            k_wall_rho<double><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout, (const double*)c->f,
-                                                          c->vg, c->wall_den, c->rho_w, c->rho_wf);
-            break;
-        case GSIS_F32:
-            k_wall_rho<float><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout, (const float*)c->f,
-                                                         c->vg, c->wall_den, c->rho_w, c->rho_wf);
-            break;
-        case GSIS_BF16:
-            k_wall_rho<__nv_bfloat16><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
-                                                                 (const __nv_bfloat16*)c->f, c->vg, c->wall_den,
-                                                                 c->rho_w, c->rho_wf);
-            break;
-        default:
-            k_wall_rho<__half><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
-                                                          (const __half*)c->f, c->vg, c->wall_den, c->rho_w,
-                                                          c->rho_wf);
-            break;
-    }
+    k_wall_rho<S, T><<<Nd, 256, c->vg.nx * sizeof(T), c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                                   (const S*)c->f, c->vg, c->wall_den, c->rho_w,
+                                                                   c->rho_wf);
     c->launches++;
+}
+
+void launch_wall_rho(gsis_ctx* c) {
+    if (c->Nd == 0 || !c->has_wall) return;
+    switch (c->p.vdf_dtype) {
+        case GSIS_F64: wall_rho_t<double, double>(c); break;
+        case GSIS_F32: wall_rho_t<float, float>(c); break;
+        case GSIS_BF16: wall_rho_t<__nv_bfloat16, float>(c); break;
+        default: wall_rho_t<__half, float>(c); break;
+    }
 }
 
 template <typename S, typename T>
 static void moments_t(gsis_ctx* c, const double* Wref, double* out) {
     const int Nd = (int)c->Nd;
-    const size_t smem = (size_t)3 * c->vg.nx * sizeof(T);
+    const size_t smem = (size_t)4 * c->vg.nx * sizeof(T);
     k_moments<S, T><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (const S*)c->f,
                                                   c->vg, out);
     c->launches++;
@@ -565,7 +682,7 @@ void launch_half_state(gsis_ctx* c) {
 // DVM cell, carried by the face distribution of f^{n+1/2}: the cell's values
 // for outgoing velocities and rho_w M_w (rho_w from zero net mass flux) for
 // incoming ones: F = sum_{xi.S>0} w (xi.S) psi f + rho_w wall_in.
-template <typename S>
+template <typename S, typename T>
 __global__ void __launch_bounds__(256) k_wall_flux(int Nd, const int* __restrict__ dvm_cell,
                                                    const int* __restrict__ side_bc, const double* __restrict__ Sout,
                                                    const S* __restrict__ f, VGridDev vg,
@@ -574,63 +691,79 @@ __global__ void __launch_bounds__(256) k_wall_flux(int Nd, const int* __restrict
     const int k = blockIdx.x;
     if (k >= Nd) return;
     const int c = dvm_cell[k];
+    int wall_mask = 0;
+    for (int s = 0; s < 6; ++s)
+        if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
+    if (!wall_mask) return;
     __shared__ double sm[32 * 5];
+    extern __shared__ double sh_raw[];
+    T* sx1 = reinterpret_cast<T*>(sh_raw);   // xi_x, xi_x^2, xi_x^3
+    T* sx2 = sx1 + vg.nx;
+    T* sx3 = sx2 + vg.nx;
+    const int nx = vg.nx, ny = vg.ny, rows = ny * vg.nz;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double x = vg.xi[i];
+        sx1[i] = (T)x;
+        sx2[i] = (T)(x * x);
+        sx3[i] = (T)(x * x * x);
+    }
+    __syncthreads();
+    const S* fk = f + (long long)k * vg.Nv;
     for (int s = 0; s < 6; ++s) {
-        if (side_bc[c * 6 + s] != GSIS_BC_WALL) continue;
+        if (!((wall_mask >> s) & 1)) continue;
         const double* Sw = Sout + ((long long)c * 6 + s) * 3;
-        const S* fk = f + (long long)k * vg.Nv;
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for (long long v = threadIdx.x; v < vg.Nv; v += blockDim.x) {
-            int ix, iy, iz;
-            vsplit(v, vg.nx, vg.ny, ix, iy, iz);
-            const double x0 = vg.xi[ix], x1 = vg.xi[vg.nx + iy], x2 = vg.xi[vg.nx + vg.ny + iz];
-            const double xn = x0 * Sw[0] + x1 * Sw[1] + x2 * Sw[2];
-            if (xn > 0.0) {
-                const double g = xn * (Store<S>::ld(fk + v) / vg.vscale);
-                double psi[5];
-                psi_node(vg, x0, x1, x2, iz, psi);
-                acc[0] += g * psi[0];
-                acc[1] += g * psi[1];
-                acc[2] += g * psi[2];
-                acc[3] += g * psi[3];
-                acc[4] += g * psi[4];
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            const int iy = r % ny, iz = r / ny;
+            const double x1 = vg.xi[nx + iy], x2 = vg.xi[nx + ny + iz];
+            const double rr = x1 * Sw[1] + x2 * Sw[2];
+            int lo, hi;
+            out_range(vg.xi, nx, Sw[0], rr, lo, hi);
+            const S* row = fk + (long long)r * nx;
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            for (int ix = lo; ix < hi; ++ix) {
+                const T fv = ldT<T, S>(row + ix);
+                a0 += fv;
+                a1 += fv * sx1[ix];
+                a2 += fv * sx2[ix];
+                a3 += fv * sx3[ix];
             }
+            const double m0 = Sw[0] * (double)a1 + rr * (double)a0;
+            const double m1 = Sw[0] * (double)a2 + rr * (double)a1;
+            const double m2 = Sw[0] * (double)a3 + rr * (double)a2;
+            double pa[5], pb[5], pc[5];
+            psi_row(vg, x1, x2, iz, pa, pb, pc);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[q] += pa[q] * m0 + pb[q] * m1 + pc[q] * m2;
         }
         block_sum<5>(acc, sm);
         if (threadIdx.x == 0) {
             const long long o = ((long long)c * 6 + s) * 5;
-            const double rw = acc[0] * vg.w / wall_den[c * 6 + s];
-            for (int q = 0; q < 5; ++q) wall_kin[o + q] = acc[q] * vg.w + rw * wall_in[o + q];
+            const double wv = vg.w / vg.vscale;   // stored values carry the VDF storage scale
+            const double rw = acc[0] * wv / wall_den[c * 6 + s];
+            for (int q = 0; q < 5; ++q) wall_kin[o + q] = acc[q] * wv + rw * wall_in[o + q];
         }
+        __syncthreads();   // sm is reused by the next wall side
     }
 }
 
-void launch_wall_flux(gsis_ctx* c) {
+template <typename S, typename T>
+static void wall_flux_t(gsis_ctx* c) {
     const int Nd = (int)c->Nd;
-    if (Nd == 0 || !c->has_wall) return;
-    switch (c->p.vdf_dtype) {
-        case GSIS_F64:
-            k_wall_flux<double><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
-                                                            (const double*)c->f, c->vg, c->wall_den, c->wall_in,
-                                                            c->wall_kin);
-            break;
-        case GSIS_F32:
-            k_wall_flux<float><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
-                                                           (const float*)c->f, c->vg, c->wall_den, c->wall_in,
-                                                           c->wall_kin);
-            break;
-        case GSIS_BF16:
-            k_wall_flux<__nv_bfloat16><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
-                                                                   (const __nv_bfloat16*)c->f, c->vg, c->wall_den,
-                                                                   c->wall_in, c->wall_kin);
-            break;
-        default:
-            k_wall_flux<__half><<<Nd, 256, 0, c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
-                                                            (const __half*)c->f, c->vg, c->wall_den, c->wall_in,
-                                                            c->wall_kin);
-            break;
-    }
+    k_wall_flux<S, T><<<Nd, 256, 3 * c->vg.nx * sizeof(T), c->stream>>>(Nd, c->dvm_cell, c->m.side_bc, c->m.Sout,
+                                                                        (const S*)c->f, c->vg, c->wall_den,
+                                                                        c->wall_in, c->wall_kin);
     c->launches++;
+}
+
+void launch_wall_flux(gsis_ctx* c) {
+    if (c->Nd == 0 || !c->has_wall) return;
+    switch (c->p.vdf_dtype) {
+        case GSIS_F64: wall_flux_t<double, double>(c); break;
+        case GSIS_F32: wall_flux_t<float, float>(c); break;
+        case GSIS_BF16: wall_flux_t<__nv_bfloat16, float>(c); break;
+        default: wall_flux_t<__half, float>(c); break;
+    }
 }
 
 // HoT = kinetic - NSF(W^{n+1/2}) in DVM cells, zero in NS cells (Eq. full_constitutive).

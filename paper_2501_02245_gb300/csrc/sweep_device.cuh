@@ -36,30 +36,6 @@ struct SweepArgs {
     VGridDev vg;
 };
 
-// minmod(a, b): 0 unless a and b share a sign, else the one nearer zero.
-template <typename T>
-__device__ __forceinline__ T minmod_t(T a, T b) {
-    const T m = fabs(a) < fabs(b) ? a : b;
-    return a * b > T(0) ? m : T(0);
-}
-
-// Half the minmod, 0.5 minmod(a, b), and x > 0.  FP64: decisions on the bit
-// patterns and the halving as a decrement of the exponent field, all on the
-// integer pipe (GB300 issues FP64 at 1/64 of the FP32 rate).  Magnitudes of
-// IEEE doubles order like their bit patterns with the sign bit cleared, and
-// +-0 never shares a sign, so the result equals 0.5 minmod_t(a, b) for every
-// result of magnitude >= 2^-1021; a smaller one (300 orders of magnitude
-// below any value of the scheme) gives 0.
-template <typename T> __device__ __forceinline__ T hmm_t(T a, T b);
-template <> __device__ __forceinline__ float hmm_t<float>(float a, float b) { return 0.5f * minmod_t<float>(a, b); }
-template <> __device__ __forceinline__ double hmm_t<double>(double a, double b) {
-    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
-    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
-    const bool a_smaller = ma < mb;
-    const long long m = a_smaller ? ia : ib, mm = a_smaller ? ma : mb;
-    const bool ok = (ia ^ ib) >= 0 && mm >= (2LL << 52);   // same sign, |result| >= 2^-1021 (so nonzero)
-    return ok ? __longlong_as_double(m - (1LL << 52)) : 0.0;
-}
 // -x if s else x (FP64: a flip of the sign bit on the integer pipe).
 template <typename T> __device__ __forceinline__ T neg_if(T x, bool s);
 template <> __device__ __forceinline__ float neg_if<float>(float x, bool s) {
@@ -68,6 +44,7 @@ template <> __device__ __forceinline__ float neg_if<float>(float x, bool s) {
 template <> __device__ __forceinline__ double neg_if<double>(double x, bool s) {
     return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
 }
+// x > 0 (FP64: on the bit pattern, integer pipe).
 template <typename T> __device__ __forceinline__ bool pos_t(T x);
 template <> __device__ __forceinline__ bool pos_t<float>(float x) { return x > 0.0f; }
 template <> __device__ __forceinline__ bool pos_t<double>(double x) { return __double_as_longlong(x) > 0; }
