@@ -691,9 +691,11 @@ def run_batch(args):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     reps = iterate_batch(solvers, args.steps)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)

@@ -344,9 +344,16 @@ struct BatchPlan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // around the sweep and the whole iteration
+    // Branch streams of the recorded graph: the per-solve stages of different
+    // solves are independent, so they are recorded on BATCH_BRANCHES streams
+    // forked from and joined back into the capture stream, which makes them
+    // parallel branches of the graph (small solves' launches fill the GPU together).
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> branch_ev;        // [0]: fork, [1 + j]: join of branch j
     long long launches_per_iter = 0;
     std::string info;
 };
+constexpr int BATCH_BRANCHES = 16;
 
 std::mutex& batch_mutex() {
     static std::mutex m;
@@ -371,6 +378,10 @@ void destroy_plan(BatchPlan* P) {
     if (P->graph) cudaGraphDestroy(P->graph);
     for (cudaEvent_t& e : P->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->branch_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : P->branch)
+        if (st) cudaStreamDestroy(st);
     if (P->own_stream && P->stream) {
         cudaStreamSynchronize(P->stream);
         cudaStreamDestroy(P->stream);
@@ -547,17 +558,51 @@ gsis_status build_plan(BatchPlan* P) {
     }
     for (cudaEvent_t& e : P->ev)
         if (!e && cudaEventCreate(&e) != cudaSuccess) return set_err(o, GSIS_ERR_CUDA, "batch timing events");
+    const int nbr = std::min(n, BATCH_BRANCHES);
+    while ((int)P->branch.size() < nbr) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return set_err(o, GSIS_ERR_CUDA, "batch branch stream");
+        P->branch.push_back(st);
+    }
+    while ((int)P->branch_ev.size() < nbr + 1) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return set_err(o, GSIS_ERR_CUDA, "batch branch event");
+        P->branch_ev.push_back(e);
+    }
+    // Record fn(solve i) for the given solves on the branch streams (solve i on
+    // branch i mod nbr), between a fork from and a join into the capture stream.
+    // main() is recorded on the capture stream between the fork and the join.
+    auto branched = [&](const std::vector<int>& solves, auto fn, auto main) {
+        cudaEventRecord(P->branch_ev[0], P->stream);
+        for (int j = 0; j < nbr; ++j) cudaStreamWaitEvent(P->branch[j], P->branch_ev[0], 0);
+        main();
+        for (size_t t = 0; t < solves.size(); ++t) {
+            gsis_ctx* c = P->ctxs[solves[t]];
+            c->stream = P->branch[t % nbr];
+            fn(c);
+            c->stream = P->stream;
+        }
+        for (int j = 0; j < nbr; ++j) {
+            cudaEventRecord(P->branch_ev[1 + j], P->branch[j]);
+            cudaStreamWaitEvent(P->stream, P->branch_ev[1 + j], 0);
+        }
+    };
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    auto none = []() {};
     cudaError_t ce = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
         cudaEventRecordWithFlags(P->ev[2], P->stream, cudaEventRecordExternal);
-        for (gsis_ctx* c : P->ctxs) stage_cell_eq(c);
+        branched(all, [](gsis_ctx* c) { stage_cell_eq(c); }, none);
         cudaEventRecordWithFlags(P->ev[0], P->stream, cudaEventRecordExternal);
         bool walls = false;
         for (gsis_ctx* c : P->ctxs) walls = walls || c->has_wall;
         if (walls) {   // wall densities refreshed between the passes
             launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
                                0, 1);
-            for (gsis_ctx* c : P->ctxs) launch_wall_rho(c);
+            branched(all, [](gsis_ctx* c) { launch_wall_rho(c); }, none);
             launch_sweep_batch(P->shape, P->nc, P->d_solves, P->d_items, P->n_items, P->d_ticket, P->grid, P->stream,
                                1, 2);
         } else {   // both passes in one launch
@@ -565,16 +610,16 @@ gsis_status build_plan(BatchPlan* P) {
                                0, 2);
         }
         cudaEventRecordWithFlags(P->ev[1], P->stream, cudaEventRecordExternal);
-        for (gsis_ctx* c : P->ctxs) stage_moments(c);
-        if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream, P->macro_cluster);
-        for (int i : P->big) {
-            gsis_ctx* c = P->ctxs[i];
-            macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0, true);
-        }
-        for (gsis_ctx* c : P->ctxs) {
+        branched(all, [](gsis_ctx* c) { stage_moments(c); }, none);
+        // the fused launch of the small solves, the large solves' synthetic solves beside it
+        branched(P->big, [](gsis_ctx* c) { macro_block(c, c->p.macro_steps, true, c->p.dt > 0.0, true); },
+                 [&]() {
+                     if (P->n_jobs) launch_macro_fused(P->d_jobs, P->n_jobs, P->stream, P->macro_cluster);
+                 });
+        branched(all, [](gsis_ctx* c) {
             stage_residual(c, true);
             stage_correct(c);
-        }
+        }, none);
         cudaEventRecordWithFlags(P->ev[3], P->stream, cudaEventRecordExternal);
         ce = cudaStreamEndCapture(P->stream, &P->graph);
     }

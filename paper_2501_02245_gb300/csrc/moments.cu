@@ -29,6 +29,26 @@
 
 namespace gsis {
 
+// n consecutive T values from shared memory as 16-byte loads (p 16-byte
+// aligned, n a multiple of 16 / sizeof(T)): a warp reading the same address
+// gets it by broadcast in one instruction per 16 bytes.
+template <typename T, int N>
+__device__ __forceinline__ void lds16(const T* p, T* o) {
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const float4 q = *reinterpret_cast<const float4*>(p + i);
+            o[i] = q.x; o[i + 1] = q.y; o[i + 2] = q.z; o[i + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const double2 q = *reinterpret_cast<const double2*>(p + i);
+            o[i] = q.x; o[i + 1] = q.y;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- outgoing wall sums by rows
 // On one x-row (fixed xi_y, xi_z) the normal speed through a wall side of area
 // vector S is xi.S = xi_x S_x + r with r = xi_y S_y + xi_z S_z, monotone in ix
@@ -128,14 +148,17 @@ __global__ void __launch_bounds__(256, 3) k_moments(int Nd, const int* __restric
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         if (vec) {   // the row as 16-byte loads (same order of the sums)
             for (int ix0 = 0; ix0 < nx; ix0 += V) {
-                T fv[V];
+                T fv[V], x1[V], x2[V], x3[V];
                 ld16<T, S>(row + ix0, fv);
+                lds16<T, V>(scx + ix0, x1);
+                lds16<T, V>(scx2 + ix0, x2);
+                lds16<T, V>(scx3 + ix0, x3);
 #pragma unroll
                 for (int j = 0; j < V; ++j) {
                     s0 += fv[j];
-                    s1 += fv[j] * scx[ix0 + j];
-                    s2 += fv[j] * scx2[ix0 + j];
-                    s3 += fv[j] * scx3[ix0 + j];
+                    s1 += fv[j] * x1[j];
+                    s2 += fv[j] * x2[j];
+                    s3 += fv[j] * x3[j];
                 }
             }
         } else {
@@ -336,6 +359,16 @@ __device__ __forceinline__ __nv_bfloat16 rounded<float, __nv_bfloat16>(float v, 
 }
 template <>
 __device__ __forceinline__ __half rounded<float, __half>(float v, unsigned key) {
+    const unsigned b = __float_as_uint(v);
+    const unsigned mag = b & 0x7fffffffu;
+    if (mag >= 0x38800000u && mag < 0x477fe000u) {
+        // |v| in FP16's normal range (2^-14 up to the last binade below 65504): FP16
+        // keeps the top 10 of FP32's 23 fraction bits, so adding 13 uniform random
+        // bits below them and truncating toward zero rounds up with probability
+        // equal to the dropped fraction (as for BF16)
+        const unsigned r = mix32(key ^ b) & 0x1fffu;
+        return __float2half_rz(__uint_as_float(b + r));
+    }
     const __half lo = __float2half_rz(v);                       // toward zero
     const unsigned short lb = __half_as_ushort(lo);
     if ((lb & 0x7c00u) == 0x7c00u) return __float2half_rn(v);  // inf / nan
@@ -611,7 +644,13 @@ template <typename S, typename T>
 static void moments_t(gsis_ctx* c, const double* Wref, double* out) {
     const int Nd = (int)c->Nd;
     const size_t smem = (size_t)4 * c->vg.nx * sizeof(T);
-    k_moments<S, T><<<Nd, 256, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (const S*)c->f,
+    // threads own whole x-rows: a block size that divides the rows evenly keeps
+    // every warp busy until the final reduction (256 unless 192 or 128 fits better)
+    const int rows = c->vg.ny * c->vg.nz;
+    int tb = 256;
+    for (int b : {256, 192, 128})
+        if ((rows + b - 1) / b * b - rows < (rows + tb - 1) / tb * tb - rows) tb = b;
+    k_moments<S, T><<<Nd, tb, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (const S*)c->f,
                                                   c->vg, out);
     c->launches++;
 }
