@@ -88,11 +88,27 @@ __device__ static void solve5(double A[5][5], double b[5], double x[5]) {
     }
 }
 
-// One warp per record.
+// Four records per warp, eight lanes (a "group") per record: the FP64
+// operations of a warp instruction cost the same whatever the number of active
+// lanes, so the per-record serial parts (the 5 x 5 solve, the reductions) run
+// for four records at once.  Lanes of a group split the 1D nodes and the 30
+// entries of the correction system; every shuffle is segmented to the group.
+constexpr int REC_LANES = 8;
+constexpr int REC_PER_WARP = 32 / REC_LANES;
+
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = REC_LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, REC_LANES);
+    return v;
+}
+
 __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Records out, VGridDev vg) {
-    const int lane = threadIdx.x & 31;
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (r >= nrec) return;
+    const int lane = threadIdx.x & 31, sl = lane & (REC_LANES - 1);
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp * REC_PER_WARP >= nrec) return;   // the whole warp is past the last record
+    const int r0 = warp * REC_PER_WARP + (lane / REC_LANES);
+    const bool valid = r0 < nrec;              // groups past the end compute a copy and store nothing
+    const int r = valid ? r0 : nrec - 1;
     const RecSpec s = specs[r];
     const int NT = vg.NT, nx = vg.nx, ny = vg.ny;
     double* tab = out.tab + (long long)r * NTAB * NT;
@@ -111,19 +127,23 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
 #pragma unroll
     for (int d = 0; d < 3; ++d) {   // the axes' node ranges in turn (static axis index for the sums)
         const int lo = d == 0 ? 0 : (d == 1 ? nx : nx + ny), hi = d == 0 ? nx : (d == 1 ? nx + ny : NT);
-        for (int idx = lo + lane; idx < hi; idx += 32) {
+        for (int idx = lo + sl; idx < hi; idx += REC_LANES) {
             if (vg.reduced && d == 2) {
                 const int p = idx - nx - ny;
-                tab[idx] = p ? sq2piT * T : sq2piT;
-                tab[2 * NT + idx] = 0.0;
-                tab[3 * NT + idx] = p ? 3.0 * T : T;
+                if (valid) {
+                    tab[idx] = p ? sq2piT * T : sq2piT;
+                    tab[2 * NT + idx] = 0.0;
+                    tab[3 * NT + idx] = p ? 3.0 * T : T;
+                }
                 continue;
             }
             const double c = vg.xi[idx] - s.u[d];
             const double e = exp(-(c * c) * i2T);
-            tab[idx] = e;
-            tab[2 * NT + idx] = c;
-            tab[3 * NT + idx] = c * c;
+            if (valid) {
+                tab[idx] = e;
+                tab[2 * NT + idx] = c;
+                tab[3 * NT + idx] = c * c;
+            }
             double pw = e;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -134,37 +154,43 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
     }
     double Cs[3][6];
     for (int d = 0; d < 3; ++d)
-        for (int k = 0; k < 6; ++k) Cs[d][k] = warp_sum(part[d][k]);
+        for (int k = 0; k < 6; ++k) Cs[d][k] = group_sum(part[d][k]);
     if (vg.reduced) {   // exact xi_z integrals int c_z^k e_z dxi_z of the Gaussian (k = 0..5)
         const double zk[6] = {1.0, 0.0, T, 0.0, 3.0 * T * T, 0.0};
         for (int k = 0; k < 6; ++k) Cs[2][k] = sq2piT * zk[k];
     }
 
-    double coef[12];   // p0', p'(3), P2'(diag 3), alpha(5)
-    // the 5 right-hand sides and 25 matrix entries of the correction system,
-    // one per lane (lanes 0-4: rhs, 5-29: A), gathered on lane 0
-    double mine = 0.0;
-    if (s.correct) {   // the same for every lane of the warp
+    // the 5 right-hand sides (entries 0-4) and 25 matrix entries (5-29) of the
+    // correction system, entry e on lane e % 8 of the group (slot e / 8), gathered
+    // on the group's first lane
+    double mine[4] = {0.0, 0.0, 0.0, 0.0};
+    if (s.correct) {
         Term tp[7], tq[19];
         const double wa = vg.w * A;
-        if (lane < 5) {
-            const int na = psi_terms(lane, s.u, tp, 1.0);
-            const int nb = base_terms(s, tq);
-            mine = s.U[lane] - wa * poly_moment(tp, na, tq, nb, Cs);
-        } else if (lane < 30) {
-            const int ra = (lane - 5) / 5, rb = (lane - 5) % 5;
-            const int na = psi_terms(ra, s.u, tp, 1.0);
-            const int nbb = psi_terms(rb, s.u, tq, rb == 4 ? 2.0 : 1.0);
-            mine = wa * poly_moment(tp, na, tq, nbb, Cs);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int e = sl + REC_LANES * m;
+            if (e < 5) {
+                const int na = psi_terms(e, s.u, tp, 1.0);
+                const int nb = base_terms(s, tq);
+                mine[m] = s.U[e] - wa * poly_moment(tp, na, tq, nb, Cs);
+            } else if (e < 30) {
+                const int ra = (e - 5) / 5, rb = (e - 5) % 5;
+                const int na = psi_terms(ra, s.u, tp, 1.0);
+                const int nbb = psi_terms(rb, s.u, tq, rb == 4 ? 2.0 : 1.0);
+                mine[m] = wa * poly_moment(tp, na, tq, nbb, Cs);
+            }
         }
     }
     double Am[5][5], rhs[5];
-    for (int t = 0; t < 30; ++t) {
-        const double v = __shfl_sync(0xffffffffu, mine, t);
-        if (t < 5) rhs[t] = v;
-        else Am[(t - 5) / 5][(t - 5) % 5] = v;
+#pragma unroll
+    for (int e = 0; e < 30; ++e) {
+        const double v = __shfl_sync(0xffffffffu, mine[e / REC_LANES], e % REC_LANES, REC_LANES);
+        if (e < 5) rhs[e] = v;
+        else Am[(e - 5) / 5][(e - 5) % 5] = v;
     }
-    if (lane == 0) {
+    double coef[7];   // p0', p'(3), P2'(diag 3)
+    if (sl == 0) {
         double pp[3] = {s.p[0], s.p[1], s.p[2]};
         double p2d[3] = {s.P2[0], s.P2[1], s.P2[2]};
         double p0 = s.p0;
@@ -181,34 +207,36 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
         }
         coef[0] = p0;
         for (int d = 0; d < 3; ++d) { coef[1 + d] = pp[d]; coef[4 + d] = p2d[d]; }
-        for (int k = 0; k < 5; ++k) coef[7 + k] = alpha[k];
-        scal[RS_P0] = p0;
-        scal[RS_P2XY] = s.P2[3];
-        scal[RS_P2XZ] = s.P2[4];
-        scal[RS_P2YZ] = s.P2[5];
-        scal[RS_OFFD] = (s.P2[3] != 0.0 || s.P2[4] != 0.0 || s.P2[5] != 0.0) ? 1.0 : 0.0;
-        scal[RS_UX] = s.u[0];
-        scal[RS_UY] = s.u[1];
-        scal[RS_UZ] = s.u[2];
-        for (int k = 0; k < 5; ++k) scal[RS_ALPHA0 + k] = alpha[k];
-        for (int q = RS_ALPHA0 + 5; q < RS; ++q) scal[q] = 0.0;
-    }
-    for (int k = 0; k < 7; ++k) coef[k] = __shfl_sync(0xffffffffu, coef[k], 0);
-    for (int idx = lane; idx < NT; idx += 32) {
-        const int d = idx < nx ? 0 : (idx < nx + ny ? 1 : 2);
-        const double c = tab[2 * NT + idx];
-        tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * tab[3 * NT + idx];   // C2 = c^2 (plane value if reduced)
-        tab[4 * NT + idx] = s.r[d] * c;
-        if (d == 0) tab[idx] *= A;
-        if (out.tabf) {   // FP32 copies in stored units: E_x carries the VDF storage scale once
-            float* tf = out.tabf + (long long)r * NTAB * NT;
-            for (int t = 0; t < NTAB; ++t)
-                tf[t * NT + idx] = (float)(t == 0 && d == 0 ? tab[idx] * vg.vscale : tab[t * NT + idx]);
+        if (valid) {
+            scal[RS_P0] = p0;
+            scal[RS_P2XY] = s.P2[3];
+            scal[RS_P2XZ] = s.P2[4];
+            scal[RS_P2YZ] = s.P2[5];
+            scal[RS_OFFD] = (s.P2[3] != 0.0 || s.P2[4] != 0.0 || s.P2[5] != 0.0) ? 1.0 : 0.0;
+            scal[RS_UX] = s.u[0];
+            scal[RS_UY] = s.u[1];
+            scal[RS_UZ] = s.u[2];
+            for (int k = 0; k < 5; ++k) scal[RS_ALPHA0 + k] = alpha[k];
+            for (int q = RS_ALPHA0 + 5; q < RS; ++q) scal[q] = 0.0;
         }
     }
-    if (out.scalf) {
-        __syncwarp();
-        if (lane < RS) out.scalf[(long long)r * RS + lane] = (float)scal[lane];
+    for (int k = 0; k < 7; ++k) coef[k] = __shfl_sync(0xffffffffu, coef[k], 0, REC_LANES);
+    __syncwarp();   // the table values of the first loop, written by other lanes of the group, are read below
+    if (valid) {
+        for (int idx = sl; idx < NT; idx += REC_LANES) {
+            const int d = idx < nx ? 0 : (idx < nx + ny ? 1 : 2);
+            const double c = tab[2 * NT + idx];
+            tab[NT + idx] = coef[1 + d] * c + coef[4 + d] * tab[3 * NT + idx];   // C2 = c^2 (plane value if reduced)
+            tab[4 * NT + idx] = s.r[d] * c;
+            if (d == 0) tab[idx] *= A;
+            if (out.tabf) {   // FP32 copies in stored units: E_x carries the VDF storage scale once
+                float* tf = out.tabf + (long long)r * NTAB * NT;
+                for (int t = 0; t < NTAB; ++t)
+                    tf[t * NT + idx] = (float)(t == 0 && d == 0 ? tab[idx] * vg.vscale : tab[t * NT + idx]);
+            }
+        }
+        if (out.scalf)
+            for (int q = sl; q < RS; q += REC_LANES) out.scalf[(long long)r * RS + q] = (float)scal[q];
     }
 }
 
@@ -216,14 +244,16 @@ __global__ void k_build_records(const RecSpec* __restrict__ specs, int nrec, Rec
 void build_records_raw(const RecSpec* d_specs, int nrec, const Records& out, const VGridDev& vg, cudaStream_t st) {
     if (nrec <= 0) return;
     const int threads = 128;
-    const int blocks = (nrec * 32 + threads - 1) / threads;
+    const int warps = (nrec + REC_PER_WARP - 1) / REC_PER_WARP;
+    const int blocks = (warps * 32 + threads - 1) / threads;
     k_build_records<<<blocks, threads, 0, st>>>(d_specs, nrec, out, vg);
 }
 
 void launch_build_records(gsis_ctx* c, const Records& out, int nrec, const RecSpec* d_specs) {
     if (nrec <= 0) return;
     const int threads = 128;
-    const int blocks = (nrec * 32 + threads - 1) / threads;
+    const int warps = (nrec + REC_PER_WARP - 1) / REC_PER_WARP;
+    const int blocks = (warps * 32 + threads - 1) / threads;
     k_build_records<<<blocks, threads, 0, c->stream>>>(d_specs, nrec, out, c->vg);
     c->launches++;
 }

@@ -852,6 +852,17 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     m.nbr = upload(c, nbr);
     m.side_bc = upload(c, side_bc);
     m.hyper = upload(c, hyper);
+    {
+        std::vector<int> bs;
+        for (int cc = 0; cc < N; ++cc)
+            for (int s = 0; s < 6; ++s) {
+                const int b = side_bc[(size_t)cc * 6 + s];
+                if (nbr[(size_t)cc * 6 + s] < 0 && (b == GSIS_BC_FARFIELD || b == GSIS_BC_WALL)) bs.push_back(cc * 6 + s);
+            }
+        m.nbside = (int)bs.size();
+        if (bs.empty()) bs.push_back(0);   // a valid pointer, never read
+        m.bside = upload(c, bs);
+    }
     std::vector<int> bct(md->bc_type, md->bc_type + 6);
     std::vector<double> bcs(&md->bc_state[0][0], &md->bc_state[0][0] + 30);
     c->d_bc_type = upload(c, bct);
@@ -864,6 +875,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->dU = (double*)dev_alloc(c, N5); c->dU2 = (double*)dev_alloc(c, N5); c->R = (double*)dev_alloc(c, N5);
     c->D = (double*)dev_alloc(c, N * sizeof(double));
     c->lamS = (double*)dev_alloc(c, (size_t)N * 6 * sizeof(double));
+    c->Fbnd = (double*)dev_alloc(c, (size_t)N * 36 * sizeof(double));
     c->Ff = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
     c->lamf = (double*)dev_alloc(c, (size_t)N * 3 * sizeof(double));
     c->F0 = (double*)dev_alloc(c, (size_t)N * 15 * sizeof(double));
@@ -902,7 +914,7 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
     c->specs = (RecSpec*)dev_alloc(c, (size_t)std::max(N, 6) * sizeof(RecSpec));
     c->recGhost.scal = (double*)dev_alloc(c, (size_t)N * RS * sizeof(double));
     c->recBC.scal = (double*)dev_alloc(c, 6 * RS * sizeof(double));
-    if (!c->d_job || !c->d_bar || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !c->W || !c->Wmom ||
+    if (!c->d_job || !c->d_bar || !m.cen || !m.vol || !m.Sout || !m.xf || !m.lsq_w || !m.nbr || !m.side_bc || !m.hyper || !m.bside || !c->Fbnd || !c->W || !c->Wmom ||
         !c->Wh || !c->fgeo || !c->bgeo || !c->acell || !c->fields ||
         !c->Wp || !c->Wm || !c->U || !c->Un || !c->dU || !c->dU2 || !c->R || !c->D || !c->lamS || !c->Ff ||
         !c->lamf || !c->F0 || !c->dFa || !c->dFb || !c->gu || !c->gT ||

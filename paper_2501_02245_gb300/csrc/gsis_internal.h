@@ -89,6 +89,8 @@ struct Mesh {
     double bc_state[6][5];
     double *vol = nullptr, *cen = nullptr, *Sout = nullptr, *xf = nullptr, *lsq_w = nullptr;
     int *nbr = nullptr, *side_bc = nullptr, *hyper = nullptr;
+    int* bside = nullptr;   // far-field and wall sides, c * 6 + s (their fluxes are formed in the face phase)
+    int nbside = 0;
 };
 
 struct Ctx;
@@ -106,6 +108,8 @@ struct MacroArgs {
     const double* bc_state;   // [6][5]
     const double* fgeo;       // [N][3][8] high face of each direction: |S|, n (3), e (3), distance of centres
     const double* bgeo;       // [N][6][8] each side: |S|, n (3), unit cell-to-face vector (3), its length
+    const int* bside;         // [nbside] far-field and wall sides, c * 6 + s
+    int nbside;
     double mu0, omega;
 };
 
@@ -118,6 +122,7 @@ struct MacroJob {
     const double *Un, *hot, *wall_corr;
     double *gu, *gT, *Ff, *lamf, *R, *D, *lamS, *dU, *dU2, *acell;
     double *F0, *dFa, *dFb;   // Euler flux tensor of U and its changes for the relaxation increments [N][15]
+    double* Fbnd;             // [N][6][6] boundary-side flux F.S_out (5) and lambda |S|
 };
 
 constexpr int MACRO_FUSED_THREADS = 512;
@@ -171,6 +176,7 @@ struct gsis_ctx {
     double *W = nullptr, *Wh = nullptr, *Wp = nullptr, *Wm = nullptr, *U = nullptr, *Un = nullptr;
     double* Wmom = nullptr;        // [N][5] the state the moments of f^{n+1/2} (momh) were taken about
     double *dU = nullptr, *dU2 = nullptr, *R = nullptr, *D = nullptr, *lamS = nullptr;
+    double* Fbnd = nullptr;                  // [N][6][6] boundary-side fluxes of the synthetic solve
     double *Ff = nullptr, *lamf = nullptr;   // interior face fluxes [N][3][5] and lambda|S| [N][3] (high faces)
     double *F0 = nullptr, *dFa = nullptr, *dFb = nullptr;   // [N][15] Euler flux tensor and its changes (relaxation)
     double *fgeo = nullptr, *bgeo = nullptr; // face geometry (see MacroArgs)

@@ -44,6 +44,8 @@ static MacroArgs margs(gsis_ctx* c) {
     a.bc_state = c->d_bc_state;
     a.fgeo = c->fgeo;
     a.bgeo = c->bgeo;
+    a.bside = c->m.bside;
+    a.nbside = c->m.nbside;
     a.mu0 = c->mu0;
     a.omega = c->p.omega;
     return a;
@@ -391,13 +393,6 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     lamf[(long long)L * 3 + d] = lam * Sabs;
 }
 
-__global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ gu,
-                            const double* __restrict__ gT, const double* __restrict__ hot,
-                            const double* __restrict__ acell, int ndir, double* __restrict__ Ff,
-                            double* __restrict__ lamf) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < a.N * ndir) face_flux_one(a, Wm, gu, gT, hot, acell, ndir, Ff, lamf, t);
-}
 
 // NSF flux through wall side s of cell c at state w (prim) with cell gradients
 // gu, gT: no mass flux, cell pressure, NSF stress and heat flux at u = 0,
@@ -525,23 +520,78 @@ void launch_fields(gsis_ctx* c, bool wall, bool cons) {
     }
 }
 
-// Cell residual R_c = -sum_F F.S_out (gathering the interior face fluxes in
-// side order, boundary faces evaluated here), lambda|S| per side, the
-// reciprocal 1/D of the diagonal (in D) and dU0 = R/D.
-__device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const double* Wm, const double* U,
-                                                  const double* Un, const double* gu, const double* gT,
-                                                  const double* hot, const double* Ff, const double* lamf,
-                                                  const double* wall_corr, double cfl, double dt, double* R, double* D,
-                                                  double* lamS, double* dU, double* F0, double* dF, int c) {
+// Flux F.S_out through boundary side s of cell c and lambda |S| of the side,
+// into Fbnd[c][s][0..5]: far field, the kinetic flux-vector splitting against
+// the far-field state with the cell's HoT; wall, the NSF wall flux plus the
+// wall correction.  Formed in the face phase (boundary side j of a.bside), so
+// that the residual phase only gathers.
+__device__ __forceinline__ void boundary_flux_one(const MacroArgs& a, const double* Wm, const double* gu,
+                                                  const double* gT, const double* hot, const double* wall_corr,
+                                                  double* Fbnd, int j) {
+    const int cs = a.bside[j], c = cs / 6, s = cs - 6 * c;
+    const int bc = a.side_bc[cs];
     const double* wc = Wm + c * 5;
     const double rho_c = wc[0], T_c = wc[4], p_c = rho_c * T_c;
     const double u_c[3] = {wc[1], wc[2], wc[3]};
+    const double* So = a.Sout + (long long)cs * 3;
+    const double* st = a.bc_state + s * 5;
+    const double* G = a.bgeo + (long long)cs * 8;
+    const double Sabs = G[0];
+    const double nn[3] = {G[1], G[2], G[3]};
+    const double* h = hot + (long long)c * HOTN;
+    double Fb[5];
+    const double bdist = G[7];
+    if (bc == GSIS_BC_FARFIELD) {
+        kfvs(rho_c, u_c, p_c, st[0], st + 1, st[0] * st[4], nn, Fb);
+        for (int q = 0; q < 5; ++q) Fb[q] *= Sabs;
+        const double SigS[3] = {h[0] * So[0] + h[3] * So[1] + h[4] * So[2],
+                                h[3] * So[0] + h[1] * So[1] + h[5] * So[2],
+                                h[4] * So[0] + h[5] * So[1] + h[2] * So[2]};
+        const double ufb[3] = {0.5 * (u_c[0] + st[1]), 0.5 * (u_c[1] + st[2]), 0.5 * (u_c[2] + st[3])};
+        Fb[1] += SigS[0];
+        Fb[2] += SigS[1];
+        Fb[3] += SigS[2];
+        Fb[4] += (SigS[0] * ufb[0] + SigS[1] * ufb[1] + SigS[2] * ufb[2]) +
+                 (h[6] * So[0] + h[7] * So[1] + h[8] * So[2]);
+    } else {
+        wall_nsf_flux(a, wc, gu + (long long)c * 9, gT + (long long)c * 3, c, s, Fb);
+        const double* wcr = wall_corr + (long long)cs * 5;
+        for (int q = 0; q < 5; ++q) Fb[q] += wcr[q];
+    }
+    const double a_c = sqrt(GAMMA * p_c / rho_c);
+    const double mu_c = viscosity(T_c, a.mu0, a.omega);
+    const double lam = fabs(u_c[0] * nn[0] + u_c[1] * nn[1] + u_c[2] * nn[2]) + a_c +
+                       5.0 * mu_c / (rho_c * 2.0 * bdist);
+    double* o = Fbnd + (long long)cs * 6;
+    for (int q = 0; q < 5; ++q) o[q] = Fb[q];
+    o[5] = lam * Sabs;
+}
+
+// Face phase of the per-phase kernels: interior faces (N * ndir threads), then
+// the far-field and wall sides.
+__global__ void k_face_flux(MacroArgs a, const double* __restrict__ Wm, const double* __restrict__ gu,
+                            const double* __restrict__ gT, const double* __restrict__ hot,
+                            const double* __restrict__ acell, int ndir, double* __restrict__ Ff,
+                            double* __restrict__ lamf, const double* __restrict__ wall_corr,
+                            double* __restrict__ Fbnd) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nf = a.N * ndir;
+    if (t < nf) face_flux_one(a, Wm, gu, gT, hot, acell, ndir, Ff, lamf, t);
+    else if (t < nf + a.nbside) boundary_flux_one(a, Wm, gu, gT, hot, wall_corr, Fbnd, t - nf);
+}
+
+// Cell residual R_c = -sum_F F.S_out (gathering the face fluxes in side
+// order: interior faces from Ff, far-field and wall sides from Fbnd), lambda|S|
+// per side, the reciprocal 1/D of the diagonal (in D) and dU0 = R/D.
+__device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const double* Wm, const double* U,
+                                                  const double* Un, const double* gu, const double* gT,
+                                                  const double* hot, const double* Ff, const double* lamf,
+                                                  const double* Fbnd, double cfl, double dt, double* R, double* D,
+                                                  double* lamS, double* dU, double* F0, double* dF, int c) {
     double Rc[5] = {0, 0, 0, 0, 0};
     double lam_sum = 0.0;
     for (int s = 0; s < 6; ++s) {
         const int n = a.nbr[c * 6 + s];
         const int bc = a.side_bc[c * 6 + s];
-        const double* So = a.Sout + ((long long)c * 6 + s) * 3;
         const int d = s >> 1;
         if (n >= 0) {
             const bool isL = (s & 1) != 0;
@@ -552,38 +602,11 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
             const double ls = lamf[(long long)L * 3 + d];
             lamS[(long long)c * 6 + s] = ls;
             lam_sum += ls;
-        } else if (bc == GSIS_BC_FARFIELD || bc == GSIS_BC_WALL) {
-            const double* st = a.bc_state + s * 5;
-            const double* G = a.bgeo + ((long long)c * 6 + s) * 8;
-            const double Sabs = G[0];
-            const double nn[3] = {G[1], G[2], G[3]};
-            const double* h = hot + (long long)c * HOTN;
-            double Fb[5];
-            const double bdist = G[7];
-            if (bc == GSIS_BC_FARFIELD) {
-                kfvs(rho_c, u_c, p_c, st[0], st + 1, st[0] * st[4], nn, Fb);
-                for (int q = 0; q < 5; ++q) Fb[q] *= Sabs;
-                const double SigS[3] = {h[0] * So[0] + h[3] * So[1] + h[4] * So[2],
-                                        h[3] * So[0] + h[1] * So[1] + h[5] * So[2],
-                                        h[4] * So[0] + h[5] * So[1] + h[2] * So[2]};
-                const double ufb[3] = {0.5 * (u_c[0] + st[1]), 0.5 * (u_c[1] + st[2]), 0.5 * (u_c[2] + st[3])};
-                Fb[1] += SigS[0];
-                Fb[2] += SigS[1];
-                Fb[3] += SigS[2];
-                Fb[4] += (SigS[0] * ufb[0] + SigS[1] * ufb[1] + SigS[2] * ufb[2]) +
-                         (h[6] * So[0] + h[7] * So[1] + h[8] * So[2]);
-            } else {
-                wall_nsf_flux(a, wc, gu + (long long)c * 9, gT + (long long)c * 3, c, s, Fb);
-                const double* wcr = wall_corr + ((long long)c * 6 + s) * 5;
-                for (int q = 0; q < 5; ++q) Fb[q] += wcr[q];
-            }
+        } else if (bc == GSIS_BC_FARFIELD || bc == GSIS_BC_WALL) {   // formed in the face phase
+            const double* Fb = Fbnd + ((long long)c * 6 + s) * 6;
             for (int q = 0; q < 5; ++q) Rc[q] -= Fb[q];
-            const double a_c = sqrt(GAMMA * p_c / rho_c);
-            const double mu_c = viscosity(T_c, a.mu0, a.omega);
-            const double lam = fabs(u_c[0] * nn[0] + u_c[1] * nn[1] + u_c[2] * nn[2]) + a_c +
-                               5.0 * mu_c / (rho_c * 2.0 * bdist);
-            lamS[(long long)c * 6 + s] = lam * Sabs;
-            lam_sum += lam * Sabs;
+            lamS[(long long)c * 6 + s] = Fb[5];
+            lam_sum += Fb[5];
         } else {
             lamS[(long long)c * 6 + s] = 0.0;
         }
@@ -610,11 +633,11 @@ __global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, cons
                                 const double* __restrict__ Un, const double* __restrict__ gu,
                                 const double* __restrict__ gT, const double* __restrict__ hot,
                                 const double* __restrict__ Ff, const double* __restrict__ lamf,
-                                const double* __restrict__ wall_corr, double cfl, double dt,
+                                const double* __restrict__ Fbnd, double cfl, double dt,
                                 double* __restrict__ R, double* __restrict__ D, double* __restrict__ lamS,
                                 double* __restrict__ dU, double* __restrict__ F0, double* __restrict__ dF) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < a.N) cell_residual_one(a, Wm, U, Un, gu, gT, hot, Ff, lamf, wall_corr, cfl, dt, R, D, lamS, dU, F0, dF, c);
+    if (c < a.N) cell_residual_one(a, Wm, U, Un, gu, gT, hot, Ff, lamf, Fbnd, cfl, dt, R, D, lamS, dU, F0, dF, c);
 }
 
 // One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D,
@@ -697,11 +720,13 @@ __global__ void __launch_bounds__(MACRO_FUSED_THREADS, 1) k_macro_fused(const Ma
         for (int c = first; c < N; c += stride)
             gradients_cell(a, J.Wm, 0, J.gu, J.gT, nullptr, nullptr, J.acell, c);
         fused_sync(cs);
-        for (int t = first; t < N * J.ndir; t += stride)
-            face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.acell, J.ndir, J.Ff, J.lamf, t);
+        for (int t = first; t < N * J.ndir + a.nbside; t += stride) {
+            if (t < N * J.ndir) face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.acell, J.ndir, J.Ff, J.lamf, t);
+            else boundary_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.wall_corr, J.Fbnd, t - N * J.ndir);
+        }
         fused_sync(cs);
         for (int c = first; c < N; c += stride)
-            cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.wall_corr, J.cfl, J.dt, J.R,
+            cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.Fbnd, J.cfl, J.dt, J.R,
                               J.D, J.lamS, J.dU, J.F0, J.k_sub > 0 ? J.dFa : nullptr, c);
         fused_sync(cs);
         double* din = J.dU;
@@ -763,6 +788,7 @@ MacroJob macro_job(gsis_ctx* c, int steps, bool time_term) {
     J.F0 = c->F0;
     J.dFa = c->dFa;
     J.dFb = c->dFb;
+    J.Fbnd = c->Fbnd;
     return J;
 }
 
@@ -858,11 +884,13 @@ __global__ void __launch_bounds__(MACRO_PERSISTENT_THREADS, 2)
         for (int c = first; c < N; c += stride)
             gradients_cell(a, J.Wm, 0, J.gu, J.gT, nullptr, nullptr, J.acell, c);
         if (!grid_barrier(bar, expected, spin_limit)) return;
-        for (int t = first; t < N * J.ndir; t += stride)
-            face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.acell, J.ndir, J.Ff, J.lamf, t);
+        for (int t = first; t < N * J.ndir + a.nbside; t += stride) {
+            if (t < N * J.ndir) face_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.acell, J.ndir, J.Ff, J.lamf, t);
+            else boundary_flux_one(a, J.Wm, J.gu, J.gT, J.hot, J.wall_corr, J.Fbnd, t - N * J.ndir);
+        }
         if (!grid_barrier(bar, expected, spin_limit)) return;
         for (int c = first; c < N; c += stride)
-            cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.wall_corr, J.cfl, J.dt, J.R,
+            cell_residual_one(a, J.Wm, J.U, J.Un, J.gu, J.gT, J.hot, J.Ff, J.lamf, J.Fbnd, J.cfl, J.dt, J.R,
                               J.D, J.lamS, J.dU, J.F0, J.k_sub > 0 ? J.dFa : nullptr, c);
         if (!grid_barrier(bar, expected, spin_limit)) return;
         double* din = J.dU;
@@ -950,14 +978,15 @@ void macro_block(gsis_ctx* c, int steps, bool with_hot, bool time_term, bool cap
     const int TB = 64;
     const int nb = (N + TB - 1) / TB;
     const int ndir = c->normal_components;   // index directions that carry flux
-    const int nf = (N * ndir + TB - 1) / TB;
+    const int nf = (N * ndir + c->m.nbside + TB - 1) / TB;   // faces, then the boundary sides
     MacroArgs a = margs(c);
     const double dt = time_term ? c->p.dt : 0.0;
     for (int it = 0; it < steps; ++it) {
         launch_gradients(c, c->Wm, false);
-        k_face_flux<<<nf, TB, 0, c->stream>>>(a, c->Wm, c->gu, c->gT, c->hot, c->acell, ndir, c->Ff, c->lamf);
+        k_face_flux<<<nf, TB, 0, c->stream>>>(a, c->Wm, c->gu, c->gT, c->hot, c->acell, ndir, c->Ff, c->lamf,
+                                               c->wall_corr, c->Fbnd);
         k_cell_residual<<<nb, TB, 0, c->stream>>>(a, c->Wm, c->U, c->Un, c->gu, c->gT, c->hot, c->Ff, c->lamf,
-                                                  c->wall_corr, c->p.cfl, dt, c->R, c->D, c->lamS, c->dU, c->F0,
+                                                  c->Fbnd, c->p.cfl, dt, c->R, c->D, c->lamS, c->dU, c->F0,
                                                   c->p.k_sub > 0 ? c->dFa : nullptr);
         c->launches += 2;
         double* din = c->dU;
