@@ -110,6 +110,7 @@ struct MacroArgs {
     const double* bgeo;       // [N][6][8] each side: |S|, n (3), unit cell-to-face vector (3), its length
     const int* bside;         // [nbside] far-field and wall sides, c * 6 + s
     int nbside;
+    int nd;                   // face normals have components 0..nd-1 only (normal_components)
     double mu0, omega;
 };
 

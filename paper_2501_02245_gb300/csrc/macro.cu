@@ -46,6 +46,7 @@ static MacroArgs margs(gsis_ctx* c) {
     a.bgeo = c->bgeo;
     a.bside = c->m.bside;
     a.nbside = c->m.nbside;
+    a.nd = c->normal_components;
     a.mu0 = c->mu0;
     a.omega = c->p.omega;
     return a;
@@ -280,13 +281,18 @@ __device__ void kfvs(double rL, const double* uL, double pL, double rR, const do
 }
 
 // Euler flux tensor of conserved state U: F[q * 3 + i] = flux of component q
-// along axis i (so that F.S is euler_flux_dot(U, S)), one division.
+// along axis i (so that F.S is euler_flux_dot(U, S)), one division.  Only the
+// axes i < ND are formed: on a mesh whose face normals have no component
+// along the others (ND = normal_components), F.S never reads them.
+template <int ND>
 __device__ __forceinline__ void euler_tensor(const double* U, double* F) {
     const double r = U[0], ir = 1.0 / r;
     const double u[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
     const double p = (GAMMA - 1.0) * (U[4] - 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
         F[i] = U[1 + i];
+#pragma unroll
         for (int j = 0; j < 3; ++j) F[(1 + j) * 3 + i] = U[1 + j] * u[i] + (i == j ? p : 0.0);
         F[12 + i] = (U[4] + p) * u[i];
     }
@@ -294,13 +300,18 @@ __device__ __forceinline__ void euler_tensor(const double* U, double* F) {
 
 // Change of the Euler flux tensor of cell c for the relaxation increment
 // dU_c, F(U_c + dU_c) - F(U_c), with F(U_c) kept in F0 for the pseudo-step:
-// each neighbour then reads the 15 values instead of evaluating both fluxes
+// each neighbour then reads the values instead of evaluating both fluxes
 // (and their divisions) itself.
+template <int ND>
 __device__ __forceinline__ void flux_change(const double* U, const double* dU, const double* F0, double* dF, int c) {
     double Up[5], F1[15];
+#pragma unroll
     for (int q = 0; q < 5; ++q) Up[q] = U[c * 5 + q] + dU[c * 5 + q];
-    euler_tensor(Up, F1);
-    for (int q = 0; q < 15; ++q) dF[(long long)c * 15 + q] = F1[q] - F0[(long long)c * 15 + q];
+    euler_tensor<ND>(Up, F1);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int i = 0; i < ND; ++i) dF[(long long)c * 15 + q * 3 + i] = F1[q * 3 + i] - F0[(long long)c * 15 + q * 3 + i];
 }
 
 __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u, p)
@@ -624,8 +635,11 @@ __device__ __forceinline__ void cell_residual_one(const MacroArgs& a, const doub
         dU[c * 5 + q] = Rc[q] * iD;
     }
     if (dF) {   // relaxation sweeps follow: the flux tensor of U_c and its change for dU_c
-        euler_tensor(U + c * 5, F0 + (long long)c * 15);
-        flux_change(U, dU, F0, dF, c);
+        switch (a.nd) {
+            case 1: euler_tensor<1>(U + c * 5, F0 + (long long)c * 15); flux_change<1>(U, dU, F0, dF, c); break;
+            case 2: euler_tensor<2>(U + c * 5, F0 + (long long)c * 15); flux_change<2>(U, dU, F0, dF, c); break;
+            default: euler_tensor<3>(U + c * 5, F0 + (long long)c * 15); flux_change<3>(U, dU, F0, dF, c); break;
+        }
     }
 }
 
@@ -643,24 +657,42 @@ __global__ void k_cell_residual(MacroArgs a, const double* __restrict__ Wm, cons
 // One Jacobi sweep: dU_new = (R - 1/2 sum_j [dF_j . S_out - lambda|S| dU_j]) / D,
 // dF_j = F(U_j + dU_j) - F(U_j) read from the neighbour's flux-change tensor
 // (dFin); with dFout the cell's own tensor for dU_new follows for the next sweep.
-__device__ __forceinline__ void relax_one(const MacroArgs& a, const double* U, const double* R, const double* D,
-                                          const double* lamS, const double* dUin, double* dUout, const double* dFin,
-                                          double* dFout, const double* F0, int c) {
-    double off[5] = {0, 0, 0, 0, 0};
+// The two sums are accumulated apart (FMA chains over the normal components
+// that can be nonzero) and combined once.
+template <int ND>
+__device__ __forceinline__ void relax_nd(const MacroArgs& a, const double* U, const double* R, const double* D,
+                                         const double* lamS, const double* dUin, double* dUout, const double* dFin,
+                                         double* dFout, const double* F0, int c) {
+    double fs[5] = {0, 0, 0, 0, 0}, ld[5] = {0, 0, 0, 0, 0};
     for (int s = 0; s < 6; ++s) {
         const int n = a.nbr[c * 6 + s];
         if (n < 0) continue;
         const double* So = a.Sout + ((long long)c * 6 + s) * 3;
         const double* dF = dFin + (long long)n * 15;
         const double ls = lamS[(long long)c * 6 + s];
+#pragma unroll
         for (int q = 0; q < 5; ++q) {
-            const double dFS = dF[q * 3] * So[0] + dF[q * 3 + 1] * So[1] + dF[q * 3 + 2] * So[2];
-            off[q] += 0.5 * (dFS - ls * dUin[n * 5 + q]);
+            double t = fs[q];
+#pragma unroll
+            for (int i = 0; i < ND; ++i) t = fma(dF[q * 3 + i], So[i], t);
+            fs[q] = t;
+            ld[q] = fma(ls, dUin[n * 5 + q], ld[q]);
         }
     }
     const double iD = D[c];   // 1 / D
-    for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - off[q]) * iD;
-    if (dFout) flux_change(U, dUout, F0, dFout, c);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dUout[c * 5 + q] = (R[c * 5 + q] - 0.5 * (fs[q] - ld[q])) * iD;
+    if (dFout) flux_change<ND>(U, dUout, F0, dFout, c);
+}
+
+__device__ __forceinline__ void relax_one(const MacroArgs& a, const double* U, const double* R, const double* D,
+                                          const double* lamS, const double* dUin, double* dUout, const double* dFin,
+                                          double* dFout, const double* F0, int c) {
+    switch (a.nd) {
+        case 1: relax_nd<1>(a, U, R, D, lamS, dUin, dUout, dFin, dFout, F0, c); break;
+        case 2: relax_nd<2>(a, U, R, D, lamS, dUin, dUout, dFin, dFout, F0, c); break;
+        default: relax_nd<3>(a, U, R, D, lamS, dUin, dUout, dFin, dFout, F0, c); break;
+    }
 }
 
 __global__ void k_relax(MacroArgs a, const double* __restrict__ U, const double* __restrict__ R,
