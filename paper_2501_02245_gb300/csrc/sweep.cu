@@ -142,9 +142,8 @@ static const SweepShape kShapesF64[] = {
 static const SweepShape kShapesF32[] = {
     {8, 1, 1, "g8_v1_c1"}, {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"},
     {4, 4, 1, "g4_v4_c1"}, {8, 4, 1, "g8_v4_c1"}, {4, 2, 2, "g4_v2_c2"},
-    {8, 1, 1, "p8_v1_c1"}, {4, 2, 1, "p4_v2_c1"}, {8, 2, 1, "p8_v2_c1"}, {4, 1, 1, "p4_v1_c1"},
-    {4, 4, 1, "p4_v4_c1"}, {2, 2, 1, "p2_v2_c1"}};
-constexpr int kFirstPairShape = 6, kPairShapeEnd = 12;
+    {8, 1, 1, "p8_v1_c1"}, {4, 2, 1, "p4_v2_c1"}, {8, 2, 1, "p8_v2_c1"}, {4, 1, 1, "p4_v1_c1"}};
+constexpr int kFirstPairShape = 6, kPairShapeEnd = 10;
 static bool pair_shape(int dtype, int shape) {
     return dtype != GSIS_F64 && shape >= kFirstPairShape && shape < kPairShapeEnd;
 }
@@ -180,8 +179,6 @@ static void sweep_f32_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape
         case 7: sweep2_t<S, 4, 2, 1>(c, a, pass); break;
         case 8: sweep2_t<S, 8, 2, 1>(c, a, pass); break;
         case 9: sweep2_t<S, 4, 1, 1>(c, a, pass); break;
-        case 10: sweep2_t<S, 4, 4, 1>(c, a, pass); break;
-        case 11: sweep2_t<S, 2, 2, 1>(c, a, pass); break;
         default: sweep_t<S, float, 8, 1, 1>(c, a, pass); break;
     }
 }
