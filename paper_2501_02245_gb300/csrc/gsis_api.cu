@@ -806,6 +806,18 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
             }
         // directions 0..D-1 carry flux and normal components 0..D-1 can be nonzero
         c->normal_components = std::max(max_dir, any_z ? 3 : (any_y ? 2 : 1));
+        // the face flux may also drop the other gradient components when the LSQ gradients have none
+        // (dim) and neighbouring cell centres differ in no other coordinate
+        const int nc = c->normal_components;
+        bool flat = nc < 3 && md->dim <= nc;
+        for (int cc = 0; flat && cc < N; ++cc)
+            for (int s = 0; s < 6; ++s) {
+                const int nb = nbr[(size_t)cc * 6 + s];
+                if (nb < 0) continue;
+                for (int k = nc; k < 3; ++k)
+                    if (md->centers[(size_t)nb * 3 + k] != md->centers[(size_t)cc * 3 + k]) flat = false;
+            }
+        c->face_nd = flat ? nc : 3;
     }
     // least-squares weights over the first dim coordinates
     const int dim = md->dim;

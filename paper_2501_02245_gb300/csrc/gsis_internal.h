@@ -111,6 +111,7 @@ struct MacroArgs {
     const int* bside;         // [nbside] far-field and wall sides, c * 6 + s
     int nbside;
     int nd;                   // face normals have components 0..nd-1 only (normal_components)
+    int fnd;                  // and cell-to-cell vectors and gradients too (face_nd; else 3)
     double mu0, omega;
 };
 
@@ -160,6 +161,8 @@ struct gsis_ctx {
 
     gsis::Mesh m;
     int normal_components = 3;     // 1: only x, 2: x and y, 3: x, y, z components of face normals are nonzero
+    int face_nd = 3;               // normal_components when the LSQ gradients and the cell-to-cell vectors
+                                   // have no other components either (mesh dim and cell centres), else 3
     bool has_wall = false;         // some boundary side is a diffuse wall
     int* d_bc_type = nullptr;      // [6]
     double* d_bc_state = nullptr;  // [6][5]

@@ -47,6 +47,7 @@ static MacroArgs margs(gsis_ctx* c) {
     a.bside = c->m.bside;
     a.nbside = c->m.nbside;
     a.nd = c->normal_components;
+    a.fnd = c->face_nd;
     a.mu0 = c->mu0;
     a.omega = c->p.omega;
     return a;
@@ -55,9 +56,11 @@ static MacroArgs margs(gsis_ctx* c) {
 // ---------------------------------------------------------------------------- gradients
 // Least-squares gradient (face neighbours plus boundary face centres with the
 // boundary value: far field -> boundary state; wall -> u = 0, |u| = 0, T = T_w,
-// rho = cell value).  gu[c][j][i] = d u_j / d x_i.
-__device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double* Wp, int with_rho_U, double* gu,
-                                               double* gT, double* grho, double* gU, double* acell, int c) {
+// rho = cell value).  gu[c][j][i] = d u_j / d x_i.  ND: the LSQ weights have
+// components 0..ND-1 only (MacroArgs::fnd); the others are written as zero.
+template <int ND>
+__device__ __forceinline__ void gradients_nd(const MacroArgs& a, const double* Wp, int with_rho_U, double* gu,
+                                             double* gT, double* grho, double* gU, double* acell, int c) {
     const double* wc = Wp + c * 5;
     if (acell) acell[c] = sqrt(GAMMA * wc[4]);
     const double Uc = with_rho_U ? sqrt(wc[1] * wc[1] + wc[2] * wc[2] + wc[3] * wc[3]) : 0.0;
@@ -86,9 +89,8 @@ __device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double*
         const int nq = with_rho_U ? 6 : 4;
         for (int q = 0; q < nq; ++q) {
             const double dphi = val[q] - phic[q];
-            g[q][0] += w[0] * dphi;
-            g[q][1] += w[1] * dphi;
-            g[q][2] += w[2] * dphi;
+#pragma unroll
+            for (int i = 0; i < ND; ++i) g[q][i] += w[i] * dphi;
         }
     }
     for (int j = 0; j < 3; ++j)
@@ -99,6 +101,15 @@ __device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double*
             grho[(long long)c * 3 + i] = g[4][i];
             gU[(long long)c * 3 + i] = g[5][i];
         }
+    }
+}
+
+__device__ __forceinline__ void gradients_cell(const MacroArgs& a, const double* Wp, int with_rho_U, double* gu,
+                                               double* gT, double* grho, double* gU, double* acell, int c) {
+    switch (a.fnd) {
+        case 1: gradients_nd<1>(a, Wp, with_rho_U, gu, gT, grho, gU, acell, c); break;
+        case 2: gradients_nd<2>(a, Wp, with_rho_U, gu, gT, grho, gU, acell, c); break;
+        default: gradients_nd<3>(a, Wp, with_rho_U, gu, gT, grho, gU, acell, c); break;
     }
 }
 
@@ -252,9 +263,14 @@ void launch_cons_to_prim(gsis_ctx* c, const double* Ucons, double* Wprim) {
 // face of unit normal n in the direction sign*n (half-range moments of the
 // normal Gaussian N(u.n, T); tangential thermal motion in closed form),
 // added to F.
+// (ND: the normal has components 0..ND-1 only; the others are exact zeros,
+// so the terms they multiply are left out.)
+template <int ND>
 __device__ __forceinline__ void half_range_add(double r, const double* u, double T, const double* n, double sign,
                                                double* F) {
-    const double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+    double un = u[0] * n[0];
+#pragma unroll
+    for (int i = 1; i < ND; ++i) un += u[i] * n[i];
     // s = un / sqrt(T) and sqrt(T) = T / sqrt(T) from one reciprocal square root
     // (instead of a square root and two FP64 divisions)
     const double ist = rsqrt(T), st = T * ist, s = un * ist;
@@ -263,9 +279,12 @@ __device__ __forceinline__ void half_range_add(double r, const double* u, double
     const double M0 = un * P + D;
     const double M1 = (un * un + T) * P + un * D;
     const double M2 = (un * un * un + 3.0 * un * T) * P + (un * un + 2.0 * T) * D;
-    const double ut[3] = {u[0] - un * n[0], u[1] - un * n[1], u[2] - un * n[2]};
+    double ut[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ut[i] = i < ND ? u[i] - un * n[i] : u[i];
     F[0] += r * M0;
-    for (int i = 0; i < 3; ++i) F[1 + i] += r * (M1 * n[i] + ut[i] * M0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[1 + i] += r * (i < ND ? M1 * n[i] + ut[i] * M0 : ut[i] * M0);
     F[4] += 0.5 * r * (M2 + (ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2] + 2.0 * T) * M0);
 }
 
@@ -273,11 +292,12 @@ __device__ __forceinline__ void half_range_add(double r, const double* u, double
 // left Maxwellian's molecules moving along +n plus the right one's moving
 // along -n -- the Euler flux that the discrete-velocity upwind scheme carries
 // for Maxwellian states.
+template <int ND = 3>
 __device__ void kfvs(double rL, const double* uL, double pL, double rR, const double* uR, double pR,
                      const double* n, double* F) {
     for (int q = 0; q < 5; ++q) F[q] = 0.0;
-    half_range_add(rL, uL, pL / rL, n, 1.0, F);
-    half_range_add(rR, uR, pR / rR, n, -1.0, F);
+    half_range_add<ND>(rL, uL, pL / rL, n, 1.0, F);
+    half_range_add<ND>(rR, uR, pR / rR, n, -1.0, F);
 }
 
 // Euler flux tensor of conserved state U: F[q * 3 + i] = flux of component q
@@ -322,9 +342,14 @@ __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u
 // (area vector S pointing L -> R).  Writes the total face flux (inviscid +
 // viscous + HoT) F.S to Ff[c][d][5] and lambda |S| to lamf[c][d]; faces that
 // do not exist (boundary) get lamf = -1.
-__device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* Wm, const double* gu,
-                                              const double* gT, const double* hot, const double* acell, int ndir,
-                                              double* Ff, double* lamf, int t) {
+// ND: on a mesh whose face normals, cell-to-cell vectors and gradients have
+// components 0..ND-1 only (MacroArgs::fnd), the NSF part is formed from those
+// components of the velocity and temperature gradients (the velocity components
+// beyond ND are rounding-level in such a flow and carry no gradient terms).
+template <int ND>
+__device__ __forceinline__ void face_flux_nd(const MacroArgs& a, const double* Wm, const double* gu,
+                                             const double* gT, const double* hot, const double* acell, int ndir,
+                                             double* Ff, double* lamf, int t) {
     const int L = t / ndir, d = t % ndir;
     const int Rr = a.nbr[L * 6 + 2 * d + 1];
     double* F = Ff + ((long long)L * 3 + d) * 5;
@@ -361,7 +386,7 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     double fl[5], fr[5];
     for (int q = 0; q < 5; ++q) { fl[q] = qL[q] + mL[q]; fr[q] = qR[q] - mR[q]; }
     double Fv[5];
-    kfvs(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, Fv);
+    kfvs<ND>(fl[0], fl + 1, fl[4], fr[0], fr + 1, fr[4], nn, Fv);
     for (int q = 0; q < 5; ++q) Fv[q] *= Sabs;
     // viscous + HoT
     const double* wL = Wm + L * 5;
@@ -371,39 +396,88 @@ __device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* 
     const double muf = viscosity(Tf, a.mu0, a.omega);
     const double e[3] = {G[4], G[5], G[6]};
     const double dist = G[7], idist = 1.0 / dist;
-    double guf[9], gTf[3];
-    for (int j = 0; j < 3; ++j) {
-        double gav[3];
-        for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gu[(long long)L * 9 + j * 3 + i] + gu[(long long)Rr * 9 + j * 3 + i]);
-        const double corr = (wR[1 + j] - wL[1 + j]) * idist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
-        for (int i = 0; i < 3; ++i) guf[j * 3 + i] = gav[i] + corr * e[i];
+    // face gradients: cell average corrected along the line of centres, for the
+    // velocity components j and directions i below ND (the rest are zero)
+    double guf[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gTf[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+        double gav[3], ge = 0.0;
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            gav[i] = 0.5 * (gu[(long long)L * 9 + j * 3 + i] + gu[(long long)Rr * 9 + j * 3 + i]);
+            ge = i == 0 ? gav[0] * e[0] : ge + gav[i] * e[i];
+        }
+        const double corr = (wR[1 + j] - wL[1 + j]) * idist - ge;
+#pragma unroll
+        for (int i = 0; i < ND; ++i) guf[j * 3 + i] = gav[i] + corr * e[i];
     }
     {
-        double gav[3];
-        for (int i = 0; i < 3; ++i) gav[i] = 0.5 * (gT[(long long)L * 3 + i] + gT[(long long)Rr * 3 + i]);
-        const double corr = (wR[4] - wL[4]) * idist - (gav[0] * e[0] + gav[1] * e[1] + gav[2] * e[2]);
-        for (int i = 0; i < 3; ++i) gTf[i] = gav[i] + corr * e[i];
+        double gav[3], ge = 0.0;
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            gav[i] = 0.5 * (gT[(long long)L * 3 + i] + gT[(long long)Rr * 3 + i]);
+            ge = i == 0 ? gav[0] * e[0] : ge + gav[i] * e[i];
+        }
+        const double corr = (wR[4] - wL[4]) * idist - ge;
+#pragma unroll
+        for (int i = 0; i < ND; ++i) gTf[i] = gav[i] + corr * e[i];
     }
+    // Eq. NSF_constitutive from the ND x ND block (zero entries not multiplied)
     double sig[6], qf[3];
-    nsf_of(muf, guf, gTf, sig, qf);
+    {
+        double div = guf[0];
+        if (ND > 1) div += guf[4];
+        if (ND > 2) div += guf[8];
+        const double two3 = 2.0 / 3.0, t = two3 * div;
+        sig[0] = -muf * (2.0 * guf[0] - t);
+        sig[1] = ND > 1 ? -muf * (2.0 * guf[4] - t) : -muf * (-t);
+        sig[2] = ND > 2 ? -muf * (2.0 * guf[8] - t) : -muf * (-t);
+        sig[3] = ND > 1 ? -muf * (guf[1] + guf[3]) : 0.0;
+        sig[4] = ND > 2 ? -muf * (guf[2] + guf[6]) : 0.0;
+        sig[5] = ND > 2 ? -muf * (guf[5] + guf[7]) : 0.0;
+        const double kap = 3.75 * muf;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) qf[i] = i < ND ? -kap * gTf[i] : 0.0;
+    }
     const double* hL = hot + (long long)L * HOTN;
     const double* hR = hot + (long long)Rr * HOTN;
     double Sg[6], Q[3];
     for (int q = 0; q < 6; ++q) Sg[q] = sig[q] + 0.5 * (hL[q] + hR[q]);
     for (int q = 0; q < 3; ++q) Q[q] = qf[q] + 0.5 * (hL[6 + q] + hR[6 + q]);
-    const double SigS[3] = {Sg[0] * S[0] + Sg[3] * S[1] + Sg[4] * S[2], Sg[3] * S[0] + Sg[1] * S[1] + Sg[5] * S[2],
-                            Sg[4] * S[0] + Sg[5] * S[1] + Sg[2] * S[2]};
+    // sigma . S and q . S over the normal's components 0..ND-1
+    const double row[3][3] = {{Sg[0], Sg[3], Sg[4]}, {Sg[3], Sg[1], Sg[5]}, {Sg[4], Sg[5], Sg[2]}};
+    double SigS[3], QS = Q[0] * S[0];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        double v = row[r][0] * S[0];
+#pragma unroll
+        for (int k = 1; k < ND; ++k) v += row[r][k] * S[k];
+        SigS[r] = v;
+    }
+#pragma unroll
+    for (int k = 1; k < ND; ++k) QS += Q[k] * S[k];
     F[0] = Fv[0];
     F[1] = Fv[1] + SigS[0];
     F[2] = Fv[2] + SigS[1];
     F[3] = Fv[3] + SigS[2];
-    F[4] = Fv[4] + ((SigS[0] * uf[0] + SigS[1] * uf[1] + SigS[2] * uf[2]) + (Q[0] * S[0] + Q[1] * S[1] + Q[2] * S[2]));
+    F[4] = Fv[4] + ((SigS[0] * uf[0] + SigS[1] * uf[1] + SigS[2] * uf[2]) + QS);
     const double aL = acell[L], aR = acell[Rr];
-    const double lam = fabs(uf[0] * nn[0] + uf[1] * nn[1] + uf[2] * nn[2]) + 0.5 * (aL + aR) +
-                       5.0 * muf / (0.5 * (wL[0] + wR[0]) * dist);
+    double un = uf[0] * nn[0];
+#pragma unroll
+    for (int k = 1; k < ND; ++k) un += uf[k] * nn[k];
+    const double lam = fabs(un) + 0.5 * (aL + aR) + 5.0 * muf / (0.5 * (wL[0] + wR[0]) * dist);
     lamf[(long long)L * 3 + d] = lam * Sabs;
 }
 
+__device__ __forceinline__ void face_flux_one(const MacroArgs& a, const double* Wm, const double* gu,
+                                              const double* gT, const double* hot, const double* acell, int ndir,
+                                              double* Ff, double* lamf, int t) {
+    switch (a.fnd) {
+        case 1: face_flux_nd<1>(a, Wm, gu, gT, hot, acell, ndir, Ff, lamf, t); break;
+        case 2: face_flux_nd<2>(a, Wm, gu, gT, hot, acell, ndir, Ff, lamf, t); break;
+        default: face_flux_nd<3>(a, Wm, gu, gT, hot, acell, ndir, Ff, lamf, t); break;
+    }
+}
 
 // NSF flux through wall side s of cell c at state w (prim) with cell gradients
 // gu, gT: no mass flux, cell pressure, NSF stress and heat flux at u = 0,
