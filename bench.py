@@ -425,18 +425,21 @@ def run_gsis(args):
                        "phase_ms_per_step": {k: v / args.steps for k, v in rep["phase_ms"].items() if v > 0}},
             "roofline": roof, "measured_peaks": peaks, "clocks": ck, "gpu_launches": rep["kernel_launches"]}
     if not args.no_e2e:
-        line["e2e"] = e2e(args, case, stream)
+        line["e2e"] = _arm(lambda: e2e(args, case, stream))
     converged_state = None
     if not args.no_converge and args.config in ("cylinder", "cylinder_full", "shock"):
-        line["time_to_converged"], converged_state = time_to_converged(args, case, stream, args.dtype,
-                                                                       keep_state=True)
+        ttc = _arm(lambda: time_to_converged(args, case, stream, args.dtype, keep_state=True))
+        if isinstance(ttc, tuple):
+            line["time_to_converged"], converged_state = ttc
+        else:
+            line["time_to_converged"] = ttc
     if not args.no_forms and args.config == "cylinder" and args.dtype == "f64" and rank == 0:
-        line["precision_forms"] = precision_forms(args, case, stream, reference_state,
-                                                  line.get("time_to_converged"), t_max / args.steps,
-                                                  converged_state)
-        line["full_kinetic"] = full_kinetic_arm(args, stream, rep, t_max / args.steps)
-        line["reduced_2d"] = reduced_arm(args, stream, rep, reference_state, t_max / args.steps)
-        line["other_workloads"] = other_workloads(stream, local)
+        line["precision_forms"] = _arm(lambda: precision_forms(args, case, stream, reference_state,
+                                                               line.get("time_to_converged"), t_max / args.steps,
+                                                               converged_state))
+        line["full_kinetic"] = _arm(lambda: full_kinetic_arm(args, stream, rep, t_max / args.steps))
+        line["reduced_2d"] = _arm(lambda: reduced_arm(args, stream, rep, reference_state, t_max / args.steps))
+        line["other_workloads"] = _arm(lambda: other_workloads(stream, local))
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, nd, nv, nc, cores, cpu, wall = cpu_baseline(args.config)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu,
@@ -459,6 +462,17 @@ def _error_vs(Wr, qr, W, q):
     return {"rho": rel(W[:, 0], Wr[:, 0]), "T": rel(W[:, 4], Wr[:, 4]), "wall_q": rel(q, qr)}
 
 
+def _arm(fn):
+    """One auxiliary measurement of the JSON line: its result, or the solver's
+    error status (a run that stopped with GSIS_ERR_NONFINITE, say) recorded in
+    its place, so that the headline line is still printed."""
+    from paper_2501_02245_gb300 import GsisError
+    try:
+        return fn()
+    except GsisError as e:
+        return {"error": str(e)}
+
+
 def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_iter, converged_state=None):
     """The cylinder with FP32, BF16 and FP16 VDF storage (FP32 sweep
     arithmetic; FP64 moments, conservation correction and synthetic solve):
@@ -470,7 +484,7 @@ def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_ite
     early in the transient (the benchmark's warm-up + timed iterations, where
     a small shift of the transient dominates the difference)."""
     import torch
-    from paper_2501_02245_gb300 import Solver
+    from paper_2501_02245_gb300 import Solver, GsisError
     Wr, qr, n_ref = reference_state
     out = {"reference": "FP64 GPU run of this benchmark after %d GSIS iterations" % n_ref}
     n_conv = None
@@ -489,9 +503,14 @@ def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_ite
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         n_dvm = vdf = 0
+        stopped = None
         for it in range(max(n_ref, n_conv or 0, 60)):
             e0.record(stream)
-            r = s.iterate(1)
+            try:
+                r = s.iterate(1)
+            except GsisError as e:   # recorded, and the other forms still run
+                stopped = "iteration %d: %s" % (it + 1, e)
+                break
             e1.record(stream)
             torch.cuda.synchronize()
             if it >= 2:
@@ -513,6 +532,8 @@ def precision_forms(args, case, stream, reference_state, f64_ttc, f64_ms_per_ite
         d = {"ms_per_iteration": ms_it, "updates_per_s": n_dvm * case.vgrid.nv / (ms_it * 1e-3) if ms_it else None,
              "vdf_bytes": vdf, "error_vs_f64": err_conv, "error_vs_f64_early": err,
              "time_to_converged": reached, "eps_min": eps_min}
+        if stopped:
+            d["stopped"] = stopped
         if f64_ms_per_iter and ms_it:
             d["speedup_per_iteration_vs_f64"] = f64_ms_per_iter / ms_it
         if f64_ttc:

@@ -342,10 +342,13 @@ __device__ __forceinline__ void prim5(const double* w, double* q) {   // (rho, u
 // (area vector S pointing L -> R).  Writes the total face flux (inviscid +
 // viscous + HoT) F.S to Ff[c][d][5] and lambda |S| to lamf[c][d]; faces that
 // do not exist (boundary) get lamf = -1.
-// ND: on a mesh whose face normals, cell-to-cell vectors and gradients have
-// components 0..ND-1 only (MacroArgs::fnd), the NSF part is formed from those
-// components of the velocity and temperature gradients (the velocity components
-// beyond ND are rounding-level in such a flow and carry no gradient terms).
+// ND: on a mesh whose face normals, cell-to-cell vectors and LSQ weights have
+// components 0..ND-1 only (MacroArgs::fnd), the gradient entries along the
+// other directions are exact zeros and are not formed or multiplied: the same
+// values as the 3D expressions.  (Every velocity component keeps its gradient:
+// the out-of-plane velocity of a 2D flow is zero only up to rounding -- and up
+// to the storage noise of BF16/FP16 VDFs -- and its viscous stress is what
+// damps it.)
 template <int ND>
 __device__ __forceinline__ void face_flux_nd(const MacroArgs& a, const double* Wm, const double* gu,
                                              const double* gT, const double* hot, const double* acell, int ndir,
@@ -396,11 +399,12 @@ __device__ __forceinline__ void face_flux_nd(const MacroArgs& a, const double* W
     const double muf = viscosity(Tf, a.mu0, a.omega);
     const double e[3] = {G[4], G[5], G[6]};
     const double dist = G[7], idist = 1.0 / dist;
-    // face gradients: cell average corrected along the line of centres, for the
-    // velocity components j and directions i below ND (the rest are zero)
+    // face gradients: cell average corrected along the line of centres, for every
+    // velocity component j and the directions i below ND (the others are zero:
+    // the LSQ weights and the line of centres have no such component)
     double guf[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gTf[3] = {0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < ND; ++j) {
+    for (int j = 0; j < 3; ++j) {
         double gav[3], ge = 0.0;
 #pragma unroll
         for (int i = 0; i < ND; ++i) {
@@ -422,7 +426,8 @@ __device__ __forceinline__ void face_flux_nd(const MacroArgs& a, const double* W
 #pragma unroll
         for (int i = 0; i < ND; ++i) gTf[i] = gav[i] + corr * e[i];
     }
-    // Eq. NSF_constitutive from the ND x ND block (zero entries not multiplied)
+    // Eq. NSF_constitutive (nsf_of) with the zero gradient entries (directions
+    // i >= ND) not multiplied: the same values
     double sig[6], qf[3];
     {
         double div = guf[0];
@@ -432,9 +437,9 @@ __device__ __forceinline__ void face_flux_nd(const MacroArgs& a, const double* W
         sig[0] = -muf * (2.0 * guf[0] - t);
         sig[1] = ND > 1 ? -muf * (2.0 * guf[4] - t) : -muf * (-t);
         sig[2] = ND > 2 ? -muf * (2.0 * guf[8] - t) : -muf * (-t);
-        sig[3] = ND > 1 ? -muf * (guf[1] + guf[3]) : 0.0;
-        sig[4] = ND > 2 ? -muf * (guf[2] + guf[6]) : 0.0;
-        sig[5] = ND > 2 ? -muf * (guf[5] + guf[7]) : 0.0;
+        sig[3] = -muf * (ND > 1 ? guf[1] + guf[3] : guf[3]);   // du_x/dy + du_y/dx
+        sig[4] = -muf * (ND > 2 ? guf[2] + guf[6] : guf[6]);   // du_x/dz + du_z/dx
+        sig[5] = ND > 1 ? -muf * (ND > 2 ? guf[5] + guf[7] : guf[7]) : 0.0;   // du_y/dz + du_z/dy
         const double kap = 3.75 * muf;
 #pragma unroll
         for (int i = 0; i < 3; ++i) qf[i] = i < ND ? -kap * gTf[i] : 0.0;

@@ -59,3 +59,23 @@ def moment_scales(direct):
     s3 = s2 ** 1.5 / np.sqrt(s0)
     sw = max(np.abs(direct[:, 13:]).max(), 1e-300)
     return np.array([s0] + [s1] * 3 + [s2] * 6 + [s3] * 3 + [sw] * 6)
+
+
+def compare_derived(s, o, tol):
+    """Wall pressure and shear, the constitutive stress and heat flux of Eq.
+    full_constitutive at the current state, and the pressure."""
+    names = ["wall_p", "wall_tx", "wall_ty", "wall_tz", "sxx", "syy", "szz", "sxy", "sxz", "syz",
+             "qx", "qy", "qz", "p"]
+    g = s.moments(names)
+    L = o.wall_loads()
+    if np.any(L[:, 1] != 0.0):
+        assert rel_err(g["wall_p"], L[:, 1]) < tol
+        tau = np.stack([g["wall_tx"], g["wall_ty"], g["wall_tz"]], axis=1)
+        assert rel_err(tau, L[:, 2:5]) < tol, "wall shear relative error %.3e" % rel_err(tau, L[:, 2:5])
+    sig_o, q_o = o.constitutive()
+    sig = np.stack([g[k] for k in ("sxx", "syy", "szz", "sxy", "sxz", "syz")], axis=1)
+    e = rel_err(sig, sig_o[:, [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]])
+    assert e < tol, "constitutive stress relative error %.3e" % e
+    q = np.stack([g[k] for k in ("qx", "qy", "qz")], axis=1)
+    assert rel_err(q, q_o) < tol, "constitutive heat flux relative error %.3e" % rel_err(q, q_o)
+    assert rel_err(g["p"], o.W[:, 0] * o.W[:, 4]) < 1e-12

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from workloads import shock_1d_case, cylinder_case, sphere_case
-from helpers import RTOL_W, rel_err, w_rel_err, run_oracle, run_gpu, vdf_by_cell
+from helpers import RTOL_W, rel_err, w_rel_err, run_oracle, run_gpu, vdf_by_cell, compare_derived
 
 pytestmark = pytest.mark.gpu
 
@@ -32,29 +32,9 @@ def _compare(case, n_iter, flags=None, f_tol=1e-10, hot_tol=1e-9):
     if np.any(qo != 0.0):
         qg = s.moments(["wall_q"])["wall_q"]
         assert rel_err(qg, qo) < 1e-9, "wall heat flux relative error %.3e" % rel_err(qg, qo)
-    _compare_derived(s, o, hot_tol)
+    compare_derived(s, o, hot_tol)
     s.close()
     return o
-
-
-def _compare_derived(s, o, tol):
-    """Wall pressure and shear, the constitutive stress and heat flux of Eq.
-    full_constitutive at the current state, and the pressure."""
-    names = ["wall_p", "wall_tx", "wall_ty", "wall_tz", "sxx", "syy", "szz", "sxy", "sxz", "syz",
-             "qx", "qy", "qz", "p"]
-    g = s.moments(names)
-    L = o.wall_loads()
-    if np.any(L[:, 1] != 0.0):
-        assert rel_err(g["wall_p"], L[:, 1]) < tol
-        tau = np.stack([g["wall_tx"], g["wall_ty"], g["wall_tz"]], axis=1)
-        assert rel_err(tau, L[:, 2:5]) < tol, "wall shear relative error %.3e" % rel_err(tau, L[:, 2:5])
-    sig_o, q_o = o.constitutive()
-    sig = np.stack([g[k] for k in ("sxx", "syy", "szz", "sxy", "sxz", "syz")], axis=1)
-    e = rel_err(sig, sig_o[:, [0, 1, 2, 0, 0, 1], [0, 1, 2, 1, 2, 2]])
-    assert e < tol, "constitutive stress relative error %.3e" % e
-    q = np.stack([g[k] for k in ("qx", "qy", "qz")], axis=1)
-    assert rel_err(q, q_o) < tol, "constitutive heat flux relative error %.3e" % rel_err(q, q_o)
-    assert rel_err(g["p"], o.W[:, 0] * o.W[:, 4]) < 1e-12
 
 
 def test_shock_small_ragged():

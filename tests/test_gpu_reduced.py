@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from workloads import cylinder_case, sphere_case
-from helpers import RTOL_W, rel_err, w_rel_err, run_oracle, run_gpu, vdf_by_cell, moment_scales
+from helpers import RTOL_W, rel_err, w_rel_err, run_oracle, run_gpu, vdf_by_cell, moment_scales, compare_derived
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +28,7 @@ def _compare(case, n_iter, flags=None, vdf_dtype="f64", w_tol=RTOL_W, f_tol=1e-1
     qo = o.wall_heat_flux()
     qg = s.moments(["wall_q"])["wall_q"]
     assert rel_err(qg, qo) < q_tol, "wall heat flux relative error %.3e" % rel_err(qg, qo)
+    compare_derived(s, o, max(hot_tol, q_tol))   # wall pressure and shear, constitutive stress and heat flux
     return o, s
 
 
