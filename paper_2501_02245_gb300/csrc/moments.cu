@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(256, 3) k_moments(int Nd, const int* __restric
     int wall_mask = 0;
     for (int s = 0; s < 6; ++s)
         if (side_bc[c * 6 + s] == GSIS_BC_WALL) wall_mask |= 1 << s;
-    double acc[MOMN];
+    // this thread's sums live in its row of the reduction buffer (shared memory),
+    // not in registers: they are touched once per plane
+    double* part = sh_raw + (4 * nx * (int)sizeof(T) + 7) / 8;
+    double* acc = part + threadIdx.x * MOMN;
 #pragma unroll
     for (int q = 0; q < MOMN; ++q) acc[q] = 0.0;
     const S* fk = f + (long long)k * vg.Nv;
@@ -134,16 +137,21 @@ __global__ void __launch_bounds__(256, 3) k_moments(int Nd, const int* __restric
     // 16 bytes (the VDF allocation is 256-byte aligned and a cell holds whole rows).
     constexpr int V = Vec16<S>::N;
     const bool vec = nx % V == 0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        const int iy = r % ny, iz = r / ny;
-        const int jy = nx + iy, jz = nx + ny + iz;
-        const double xy = vg.xi[jy], xz = vg.xi[jz];
-        const double cy = xy - uy, cz = xz - uz;
-        // plane weights of c_z^k on the reduced grid
-        double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
-        if (vg.reduced) {
-            z0 = zpow(vg, iz, cz, 0); z1 = zpow(vg, iz, cz, 1); z2 = zpow(vg, iz, cz, 2); z3 = zpow(vg, iz, cz, 3);
-        }
+    // Each thread takes a contiguous run of rows, so that its rows share the
+    // plane iz: per row it folds the row sums d_a with the powers of c_y only
+    // (Y sums), and once per plane with the plane's c_z weights z_k (c_z^k on
+    // the 3D grid, the G/H plane weights on the reduced grid):
+    //   m = sum_planes sum_a,b Y_{a,b} z_k
+    double Y[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // d0 (1, cy, cy^2, cy^3), d1 (1, cy, cy^2), d2 (1, cy), d3
+    const int per = (rows + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * per, r1 = min(rows, r0 + per);
+    for (int rp = r0; rp < r1;) {   // the thread's rows plane by plane
+      const int iz = rp / ny, rend = min(r1, (iz + 1) * ny);
+#pragma unroll
+      for (int q = 0; q < 10; ++q) Y[q] = 0.0;
+      for (int r = rp; r < rend; ++r) {
+        const int iy = r - iz * ny;
+        const double cy = vg.xi[nx + iy] - uy;
         const S* row = fk + (long long)r * nx;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         if (vec) {   // the row as 16-byte loads (same order of the sums)
@@ -171,37 +179,42 @@ __global__ void __launch_bounds__(256, 3) k_moments(int Nd, const int* __restric
             }
         }
         const double d0 = s0, d1 = s1, d2 = s2, d3 = s3;
-        if (!vg.reduced) {
-            const double t = cy * cy + cz * cz;
-            acc[0] += d0;
-            acc[1] += d1;
-            acc[2] += d0 * cy;
-            acc[3] += d0 * cz;
-            acc[4] += d2;
-            acc[5] += d0 * (cy * cy);
-            acc[6] += d0 * (cz * cz);
-            acc[7] += d1 * cy;
-            acc[8] += d1 * cz;
-            acc[9] += d0 * (cy * cz);
-            acc[10] += d3 + d1 * t;
-            acc[11] += cy * (d2 + d0 * t);
-            acc[12] += cz * (d2 + d0 * t);
-        } else {   // each moment c_x^a c_y^b c_z^k: row sum d_a times c_y^b times the plane's c_z^k weight
-            const double cy2 = cy * cy;
-            acc[0] += d0 * z0;
-            acc[1] += d1 * z0;
-            acc[2] += d0 * cy * z0;
-            acc[3] += d0 * z1;
-            acc[4] += d2 * z0;
-            acc[5] += d0 * cy2 * z0;
-            acc[6] += d0 * z2;
-            acc[7] += d1 * cy * z0;
-            acc[8] += d1 * z1;
-            acc[9] += d0 * cy * z1;
-            acc[10] += (d3 + d1 * cy2) * z0 + d1 * z2;                   // c_x c^2
-            acc[11] += cy * (d2 + d0 * cy2) * z0 + cy * d0 * z2;         // c_y c^2
-            acc[12] += (d2 + d0 * cy2) * z1 + d0 * z3;                   // c_z c^2
+        const double cy2 = cy * cy, cy3 = cy2 * cy;
+        Y[0] += d0;
+        Y[1] = fma(d0, cy, Y[1]);
+        Y[2] = fma(d0, cy2, Y[2]);
+        Y[3] = fma(d0, cy3, Y[3]);
+        Y[4] += d1;
+        Y[5] = fma(d1, cy, Y[5]);
+        Y[6] = fma(d1, cy2, Y[6]);
+        Y[7] += d2;
+        Y[8] = fma(d2, cy, Y[8]);
+        Y[9] += d3;
+      }
+      {   // fold the plane's Y sums with its c_z weights
+        double z0, z1, z2, z3;
+        const double cz = vg.xi[nx + ny + iz] - uz;
+        if (vg.reduced) {
+            z0 = zpow(vg, iz, cz, 0); z1 = zpow(vg, iz, cz, 1);
+            z2 = zpow(vg, iz, cz, 2); z3 = zpow(vg, iz, cz, 3);
+        } else {
+            z0 = 1.0; z1 = cz; z2 = cz * cz; z3 = z2 * cz;
         }
+        acc[0] += Y[0] * z0;
+        acc[1] += Y[4] * z0;
+        acc[2] += Y[1] * z0;
+        acc[3] += Y[0] * z1;
+        acc[4] += Y[7] * z0;
+        acc[5] += Y[2] * z0;
+        acc[6] += Y[0] * z2;
+        acc[7] += Y[5] * z0;
+        acc[8] += Y[4] * z1;
+        acc[9] += Y[1] * z1;
+        acc[10] += (Y[9] + Y[6]) * z0 + Y[4] * z2;   // c_x c^2
+        acc[11] += (Y[8] + Y[3]) * z0 + Y[1] * z2;   // c_y c^2
+        acc[12] += (Y[7] + Y[2]) * z1 + Y[0] * z3;   // c_z c^2
+      }
+      rp = rend;
     }
     if (wall_mask) {   // outgoing mass flux through each wall side, row by row (mass rows only)
         double wsum[6] = {0, 0, 0, 0, 0, 0};
@@ -227,11 +240,24 @@ __global__ void __launch_bounds__(256, 3) k_moments(int Nd, const int* __restric
 #pragma unroll
         for (int s = 0; s < 6; ++s) acc[13 + s] = wsum[s];
     }
-    block_sum<MOMN>(acc, red);
-    if (threadIdx.x == 0) {
-        double* m = mom + (long long)k * MOMN;
+    // Block reduction over the rows of the buffer: lane q of each warp adds
+    // moment q over the warp's threads
+    // (31 FP64 additions per warp instead of MOMN five-step shuffle trees), and
+    // thread q adds the warps' totals.
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane < MOMN) {
+        const double* pw = part + w * 32 * MOMN + lane;
+        double t = 0.0;
+        for (int j = 0; j < 32; ++j) t += pw[j * MOMN];
+        red[w * MOMN + lane] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < MOMN) {
+        double t = 0.0;
+        for (int j = 0; j < nw; ++j) t += red[j * MOMN + threadIdx.x];
         const double wv = vg.w / vg.vscale;   // stored values carry the VDF storage scale
-        for (int q = 0; q < MOMN; ++q) m[q] = acc[q] * wv;
+        mom[(long long)k * MOMN + threadIdx.x] = t * wv;
     }
 }
 
@@ -643,13 +669,14 @@ void launch_wall_rho(gsis_ctx* c) {
 template <typename S, typename T>
 static void moments_t(gsis_ctx* c, const double* Wref, double* out) {
     const int Nd = (int)c->Nd;
-    const size_t smem = (size_t)4 * c->vg.nx * sizeof(T);
     // threads own whole x-rows: a block size that divides the rows evenly keeps
     // every warp busy until the final reduction (256 unless 192 or 128 fits better)
     const int rows = c->vg.ny * c->vg.nz;
     int tb = 256;
     for (int b : {256, 192, 128})
         if ((rows + b - 1) / b * b - rows < (rows + tb - 1) / tb * tb - rows) tb = b;
+    // c_x tables, then one row of MOMN sums per thread for the block reduction
+    const size_t smem = ((size_t)4 * c->vg.nx * sizeof(T) + 7) / 8 * 8 + (size_t)tb * MOMN * sizeof(double);
     k_moments<S, T><<<Nd, tb, smem, c->stream>>>(Nd, c->dvm_cell, Wref, c->m.side_bc, c->m.Sout, (const S*)c->f,
                                                   c->vg, out);
     c->launches++;
