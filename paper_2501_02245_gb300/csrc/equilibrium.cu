@@ -15,6 +15,7 @@
 //      sum_v w psi phi^T M a = U - sum_v w psi D,  psi = (1, xi, |xi|^2/2),
 //      phi = (1, xi, |xi|^2),
 //    whose sums are assembled exactly from 1D sums C_d[k] = sum_i e_d c_d^k.
+#include <type_traits>
 #include "gsis_device.cuh"
 
 namespace gsis {
@@ -312,11 +313,42 @@ __global__ void k_cell_eq(int Nd, const int* __restrict__ dvm_cell, const double
 //   y(q)  = E_yz/tau (D + R_yz C2_yz, 1, C2_yz, R_yz ; A)   [gy4 ; gy1]
 // so that g~/tau = sum of the five products x_i y_i.
 template <typename T>
-__global__ void k_build_gtab(int Nd, Records rec, VGridDev vg, const double* __restrict__ itau, T* __restrict__ gx4,
-                             T* __restrict__ gx1, T* __restrict__ gy4, T* __restrict__ gy1) {
+__global__ void k_build_gtab(int Nd, Records rec, VGridDev vg, const double* __restrict__ itau,
+                             const float* __restrict__ itauf, T* __restrict__ gx4, T* __restrict__ gx1,
+                             T* __restrict__ gy4, T* __restrict__ gy1) {
     const int k = blockIdx.x;
     if (k >= Nd) return;
     const int NT = vg.NT, nx = vg.nx, ny = vg.ny, nyz = vg.ny * vg.nz;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 arithmetic for FP32 factor vectors, from the FP32 record copies
+        // (whose E_x carries the storage scale; the FP64 form below puts it on
+        // the y-z part): the same products rounded once to FP32 become a few
+        // rounding steps in FP32, far under the storage rounding, and the FP64
+        // pipe (the bound of the FP64 form) is left alone.
+        const float* tf = rec.tabf + (long long)k * NTAB * NT;
+        const float* sf = rec.scalf + (long long)k * RS;
+        const float p0 = sf[RS_P0], pxy = sf[RS_P2XY], pxz = sf[RS_P2XZ], pyz = sf[RS_P2YZ];
+        const float it = itauf[k];
+        for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+            const float E = tf[ix], B = tf[NT + ix], C = tf[2 * NT + ix], C2 = tf[3 * NT + ix], R = tf[4 * NT + ix];
+            *reinterpret_cast<float4*>(gx4 + ((long long)k * nx + ix) * 4) =
+                make_float4(E, E * (B + R * C2), E * R, E * C2);
+            gx1[(long long)k * nx + ix] = E * C;
+        }
+        for (int q = threadIdx.x; q < nyz; q += blockDim.x) {
+            const int iz = q / ny, jy = nx + q - iz * ny, jz = nx + ny + iz;
+            const float Cy = tf[2 * NT + jy], Cz = tf[2 * NT + jz];
+            const float Eyz = tf[jy] * tf[jz] * it;
+            const float D = p0 + (tf[NT + jy] + tf[NT + jz]) + 2.0f * pyz * Cy * Cz;
+            const float Ryz = tf[4 * NT + jy] + tf[4 * NT + jz];
+            const float C2yz = tf[3 * NT + jy] + tf[3 * NT + jz];
+            const float A = 2.0f * (pxy * Cy + pxz * Cz);
+            *reinterpret_cast<float4*>(gy4 + ((long long)k * nyz + q) * 4) =
+                make_float4(Eyz * (D + Ryz * C2yz), Eyz, Eyz * C2yz, Eyz * Ryz);
+            gy1[(long long)k * nyz + q] = Eyz * A;
+        }
+        return;
+    }
     const double* tab = rec.tab + (long long)k * NTAB * NT;
     const double* sc = rec.scal + (long long)k * RS;
     const double p0 = sc[RS_P0], pxy = sc[RS_P2XY], pxz = sc[RS_P2XZ], pyz = sc[RS_P2YZ];
@@ -356,10 +388,10 @@ void launch_cell_eq(gsis_ctx* c) {
     c->launches++;
     launch_build_records(c, c->recG, Nd, c->specs);
     if (c->p.vdf_dtype == GSIS_F64)
-        k_build_gtab<double><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, (double*)c->gx4,
+        k_build_gtab<double><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, c->itauf, (double*)c->gx4,
                                                         (double*)c->gx1, (double*)c->gy4, (double*)c->gy1);
     else
-        k_build_gtab<float><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, (float*)c->gx4,
+        k_build_gtab<float><<<Nd, 128, 0, c->stream>>>(Nd, c->recG, c->vg, c->itau, c->itauf, (float*)c->gx4,
                                                        (float*)c->gx1, (float*)c->gy4, (float*)c->gy1);
     c->launches++;
 }
