@@ -142,8 +142,9 @@ static const SweepShape kShapesF64[] = {
 static const SweepShape kShapesF32[] = {
     {8, 1, 1, "g8_v1_c1"}, {4, 1, 1, "g4_v1_c1"}, {8, 2, 1, "g8_v2_c1"},
     {4, 4, 1, "g4_v4_c1"}, {8, 4, 1, "g8_v4_c1"}, {4, 2, 2, "g4_v2_c2"},
-    {8, 1, 1, "p8_v1_c1"}, {4, 2, 1, "p4_v2_c1"}, {8, 2, 1, "p8_v2_c1"}, {4, 1, 1, "p4_v1_c1"}};
-constexpr int kFirstPairShape = 6, kPairShapeEnd = 10;
+    {8, 1, 1, "p8_v1_c1"}, {4, 2, 1, "p4_v2_c1"}, {8, 2, 1, "p8_v2_c1"}, {4, 1, 1, "p4_v1_c1"},
+    {5, 2, 1, "p5_v2_c1"}};
+constexpr int kFirstPairShape = 6, kPairShapeEnd = 11;
 static bool pair_shape(int dtype, int shape) {
     return dtype != GSIS_F64 && shape >= kFirstPairShape && shape < kPairShapeEnd;
 }
@@ -179,6 +180,7 @@ static void sweep_f32_shape(gsis_ctx* c, const SweepArgs& a, int pass, int shape
         case 7: sweep2_t<S, 4, 2, 1>(c, a, pass); break;
         case 8: sweep2_t<S, 8, 2, 1>(c, a, pass); break;
         case 9: sweep2_t<S, 4, 1, 1>(c, a, pass); break;
+        case 10: sweep2_t<S, 5, 2, 1>(c, a, pass); break;
         default: sweep_t<S, float, 8, 1, 1>(c, a, pass); break;
     }
 }

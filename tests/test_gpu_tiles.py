@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 TILES = {
     "f64": ["g2_v1_c2", "g1_v1_c2", "g4_v1_c1", "g2_v1_c1", "g8_v1_c1", "g16_v1_c1", "ring_w8_v32", "ring_w4_v32"],
     "f32": ["g8_v1_c1", "g4_v1_c1", "g8_v2_c1", "g4_v4_c1", "g8_v4_c1", "g4_v2_c2",
-            "p8_v1_c1", "p4_v2_c1", "p8_v2_c1", "p4_v1_c1", "ring_w8_v32", "ring_w4_v32", "ring_w8_v64"],
+            "p8_v1_c1", "p4_v2_c1", "p8_v2_c1", "p4_v1_c1", "p5_v2_c1", "ring_w8_v32", "ring_w4_v32",
+            "ring_w8_v64"],
 }
 
 
@@ -50,7 +51,7 @@ def test_every_sweep_tile_matches_the_oracle(dtype):
     for tile, W in results.items():
         assert w_rel_err(W, ref) <= (1e-12 if dtype == "f64" else 1e-5), tile
     if dtype == "f32":   # the packed pair update performs the same roundings as the single-velocity one
-        for tile in ("p8_v1_c1", "p4_v2_c1", "p8_v2_c1", "p4_v1_c1"):
+        for tile in ("p8_v1_c1", "p4_v2_c1", "p8_v2_c1", "p4_v1_c1", "p5_v2_c1"):
             assert np.array_equal(results[tile], ref), tile
 
 
