@@ -395,14 +395,17 @@ __device__ __forceinline__ __half rounded<float, __half>(float v, unsigned key) 
         const unsigned r = mix32(key ^ b) & 0x1fffu;
         return __float2half_rz(__uint_as_float(b + r));
     }
-    const __half lo = __float2half_rz(v);                       // toward zero
-    const unsigned short lb = __half_as_ushort(lo);
-    if ((lb & 0x7c00u) == 0x7c00u) return __float2half_rn(v);  // inf / nan
-    const __half hi = __ushort_as_half((unsigned short)(lb + 1));   // next value away from zero
-    const float flo = __half2float(lo), fhi = __half2float(hi);
-    const float frac = (fabsf(v) - fabsf(flo)) / (fabsf(fhi) - fabsf(flo));   // in [0, 1)
-    const float u = (float)(mix32(key ^ __float_as_uint(v)) >> 8) * (1.0f / 16777216.0f);
-    return u < frac ? hi : lo;
+    if (mag < 0x38800000u) {
+        // below 2^-14: FP16's subnormals, m 2^-24 for m = 0..1023, so |v| 2^24 (exact)
+        // splits into the lower m and the fraction that rounds up (m + 1 = 1024 is
+        // the smallest normal, whose bits follow on)
+        const float r = __uint_as_float(mag) * 16777216.0f;
+        const unsigned m = (unsigned)r;
+        const float frac = r - (float)m;
+        const float u = (float)(mix32(key ^ b) >> 8) * (1.0f / 16777216.0f);
+        return __ushort_as_half((unsigned short)(((b >> 16) & 0x8000u) | (m + (u < frac ? 1u : 0u))));
+    }
+    return __float2half_rn(v);   // beyond the largest finite FP16, inf, nan: nearest
 }
 __device__ __forceinline__ unsigned corr_key(int k, int v) {
     return (unsigned)k * 0x9e3779b9u ^ (unsigned)v * 0x85ebca6bu;
