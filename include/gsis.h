@@ -131,7 +131,9 @@ typedef struct {
  * for a wall.  W0 [ncell][5] is the initial (rho, ux, uy, uz, T).
  * Errors: GSIS_ERR_ARG for non-positive sizes or volumes, a periodic
  * direction with fewer than 3 cells, inconsistent periodic sides, non-finite
- * input or non-positive rho/T; GSIS_ERR_STATE after the first gsis_iterate. */
+ * input or non-positive rho/T; GSIS_ERR_UNSUPPORTED when the velocity grid is
+ * set and the mesh's largest sum_s |S_s|/V times max|xi| exceeds 2^100 (see
+ * gsis_set_velocity_grid); GSIS_ERR_STATE after the first gsis_iterate. */
 typedef struct {
     int ni, nj, nk;
     int dim;                    /* spatial directions carrying gradients (1, 2 or 3) */
@@ -184,7 +186,10 @@ typedef struct gsis_ctx gsis_ctx;
 /* Create a context.  params is copied.  alloc may be NULL (cudaMalloc/cudaFree).
  * cuda_stream is a cudaStream_t (NULL = default stream).
  * Errors: GSIS_ERR_ARG (NULL out/params, Kn <= 0, macro_steps < 0, k_sub < 0,
- * cfl <= 0, dt < 0, unknown vdf_dtype), GSIS_ERR_CUDA (no device). */
+ * cfl <= 0, dt < 0, unknown vdf_dtype), GSIS_ERR_UNSUPPORTED (Kn outside
+ * [1e-15, 1e15]: the kinetic update's quotient needs 1/tau + sum xi.S/V inside
+ * the FP32 exponent range, see gsis_set_velocity_grid; d_r > 0),
+ * GSIS_ERR_CUDA (no device). */
 gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, void* cuda_stream,
                       gsis_ctx** out);
 
@@ -192,7 +197,11 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
 gsis_status gsis_set_mesh(gsis_ctx* ctx, const gsis_mesh_desc* mesh);
 
 /* Set the velocity grid. Must precede gsis_iterate; GSIS_ERR_STATE afterwards.
- * Errors: GSIS_ERR_ARG for n[d] < 1 or hi[d] <= lo[d]. */
+ * Errors: GSIS_ERR_ARG for n[d] < 1 or hi[d] <= lo[d]; GSIS_ERR_UNSUPPORTED
+ * when max|xi| times the mesh's largest sum_s |S_s|/V exceeds 2^100 (the
+ * kinetic update divides by 1/tau + sum_s max(xi.S_s, 0)/V with an FP32
+ * reciprocal seed, which needs that denominator inside the FP32 exponent
+ * range; gsis_set_mesh refuses a mesh the same way once the grid is set). */
 gsis_status gsis_set_velocity_grid(gsis_ctx* ctx, const gsis_vgrid_desc* vgrid);
 
 /* Run up to max_iter GSIS iterations (Sec. 3.1 steps; Sec. 3.4 drives the

@@ -663,6 +663,24 @@ void drop_plans_with(gsis_ctx* c) {
 
 }  // namespace
 
+namespace {
+// The kinetic update divides by 1/tau + sum_s max(xi.S_s, 0)/V.  The FP64
+// sweep seeds that quotient with an FP32 reciprocal of the denominator moved
+// into the FP32 exponent range by an integer rebias, and the FP32 sweep uses
+// the fast FP32 quotient: both need the denominator inside the normal FP32
+// range (2^-126 .. 2^127).  The host keeps it far inside: the outflow part is
+// at most max|xi| * max_c sum_s |S_s|/V_c <= 2^100, and 1/tau = rho T^(1-omega)
+// / mu(T0) with mu(T0) = Kn sqrt(2/pi) stays above 2^-100 for Kn <= 1e15 and
+// rho T^(1-omega) >= 1e-15 (below 2^100 for Kn >= 1e-15 and rho T^(1-omega)
+// <= 1e15).
+constexpr double KN_MIN = 1e-15, KN_MAX = 1e15;
+constexpr double QUOTIENT_OUTFLOW_MAX = 1.2676506002282294e30;   // 2^100
+constexpr const char* quotient_range_msg =
+    "max|xi| * max over cells of sum |S|/V exceeds 2^100: the sweep's quotient needs its denominator "
+    "inside the FP32 exponent range";
+bool quotient_range_ok(double max_sv, double max_xi) { return max_sv * max_xi <= QUOTIENT_OUTFLOW_MAX; }
+}  // namespace
+
 // ============================================================================ C ABI
 extern "C" {
 
@@ -677,6 +695,7 @@ gsis_status gsis_init(const gsis_params* params, const gsis_allocator* alloc, vo
         p.presolve_max_blocks < 0 || p.wall_layers < 0 || p.adapt_every < 0 || !(p.tol >= 0.0) ||
         !(p.relax >= 0.0 && p.relax <= 1.0))
         return GSIS_ERR_ARG;
+    if (!(p.Kn >= KN_MIN && p.Kn <= KN_MAX)) return GSIS_ERR_UNSUPPORTED;   // see quotient_range_ok
     if (p.d_r < 0) return GSIS_ERR_ARG;
     if (p.d_r > 0) return GSIS_ERR_UNSUPPORTED;   // the two-VDF model of Eq. general_model is not built
     if (alloc && (!alloc->alloc || !alloc->free)) return GSIS_ERR_ARG;
@@ -791,6 +810,19 @@ gsis_status gsis_set_mesh(gsis_ctx* c, const gsis_mesh_desc* md) {
                         side_bc[(size_t)cc * 6 + s] = nb >= 0 ? -1 : md->bc_type[s];
                     }
             }
+    // largest outflow factor sum_s |S_s| / V of a cell (bound on the sweep's denominator, see quotient_range)
+    double max_sv = 0.0;
+    for (int cc = 0; cc < N; ++cc) {
+        double sv = 0.0;
+        for (int s = 0; s < 6; ++s) {
+            const double* v = &Sout[((size_t)cc * 6 + s) * 3];
+            sv += std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        }
+        max_sv = std::max(max_sv, sv / md->volumes[cc]);
+    }
+    if (c->vgrid_set && !quotient_range_ok(max_sv, c->max_xi))
+        return set_err(c, GSIS_ERR_UNSUPPORTED, quotient_range_msg);
+    c->max_sv = max_sv;
     // face-normal components that are nonzero on some flux-carrying face
     {
         bool any_y = false, any_z = false;
@@ -964,6 +996,11 @@ gsis_status gsis_set_velocity_grid(gsis_ctx* c, const gsis_vgrid_desc* vd) {
     const int n3[3] = {vd->n[0], vd->n[1], red ? 2 : vd->n[2]};
     const long long Nv = (long long)n3[0] * n3[1] * n3[2];
     if (Nv > (1ll << 31)) return set_err(c, GSIS_ERR_ARG, "too many velocities");
+    double max_xi = 0.0;
+    for (int d = 0; d < naxes; ++d) max_xi = std::max(max_xi, std::max(std::fabs(vd->lo[d]), std::fabs(vd->hi[d])));
+    if (c->mesh_set && !quotient_range_ok(c->max_sv, max_xi))
+        return set_err(c, GSIS_ERR_UNSUPPORTED, quotient_range_msg);
+    c->max_xi = max_xi;
     std::vector<double> xi;
     double w = 1.0;
     for (int d = 0; d < 3; ++d) {

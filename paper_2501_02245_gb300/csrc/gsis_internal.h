@@ -164,6 +164,8 @@ struct gsis_ctx {
     int face_nd = 3;               // normal_components when the LSQ gradients and the cell-to-cell vectors
                                    // have no other components either (mesh dim and cell centres), else 3
     bool has_wall = false;         // some boundary side is a diffuse wall
+    double max_sv = 0.0;           // max over cells of sum_s |S_s| / V (set_mesh)
+    double max_xi = 0.0;           // largest |velocity node| (set_velocity_grid)
     int* d_bc_type = nullptr;      // [6]
     double* d_bc_state = nullptr;  // [6][5]
     std::vector<double> host_W0;

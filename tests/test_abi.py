@@ -65,6 +65,22 @@ def test_init_refuses_internal_degrees_of_freedom(lib):
         assert lib.gsis_init(ctypes.byref(p), None, None, ctypes.byref(ctx)) == want
 
 
+def test_init_refuses_knudsen_numbers_outside_the_quotient_range(lib):
+    """The kinetic update's quotient needs 1/tau = rho T^(1-omega)/mu(T0) inside
+    the FP32 exponent range: Kn outside [1e-15, 1e15] is refused before any
+    device call; the ends of the range are accepted by the parameter checks."""
+    from paper_2501_02245_gb300.gsis import Params, GSIS_ERR_UNSUPPORTED
+    ctx = ctypes.c_void_p()
+    base = dict(omega=0.74, adaptive=0, Kn_ref=0.0, adapt_every=5, wall_layers=2, vdf_dtype=0,
+                macro_steps=10, cfl=5.0, k_sub=2, dt=0.0, tol=1e-6, presolve_max_blocks=0, spin_limit=0)
+    for Kn in (1e-16, 2e15, 1e300):
+        p = Params(**base, Kn=Kn)
+        assert lib.gsis_init(ctypes.byref(p), None, None, ctypes.byref(ctx)) == GSIS_ERR_UNSUPPORTED
+    for Kn in (1e-15, 1e15):
+        p = Params(**base, Kn=Kn)
+        assert lib.gsis_init(ctypes.byref(p), None, None, ctypes.byref(ctx)) != GSIS_ERR_UNSUPPORTED
+
+
 def test_null_safety(lib):
     lib.gsis_free(None)
     assert lib.gsis_last_error(None) == b"NULL context"

@@ -274,6 +274,38 @@ def test_non_finite_input_is_rejected_unchanged():
     lib.gsis_free(ctx)
 
 
+def test_mesh_and_grid_beyond_the_quotient_range_are_refused():
+    """The kinetic update divides by 1/tau + sum_s max(xi.S_s, 0)/V with an
+    FP32 reciprocal seed: a velocity grid whose largest |xi| times the mesh's
+    largest sum |S|/V exceeds 2^100 is refused (GSIS_ERR_UNSUPPORTED, host
+    checks only, no launch), in either order of the two calls, and the
+    context keeps its previous mesh and grid and still iterates."""
+    from paper_2501_02245_gb300 import gsis
+    lib = gsis.load()
+    case = shock_1d_case(n_cells=24, half_width=6.0, nv=(20, 10, 9), vmax=8.0, macro_steps=20)
+    ctx = _raw_ctx(lib, gsis, case)
+    keep = []
+    assert lib.gsis_set_mesh(ctx, ctypes.byref(_mesh_desc(gsis, case.mesh, case.W0, keep))) == gsis.GSIS_OK
+    vg = gsis.VGridDesc()
+    for d in range(3):
+        vg.n[d], vg.lo[d], vg.hi[d] = case.vgrid.n[d], case.vgrid.lo[d], case.vgrid.hi[d]
+    wide = gsis.VGridDesc()
+    for d in range(3):
+        wide.n[d], wide.lo[d], wide.hi[d] = case.vgrid.n[d], -1e30, 1e30
+    assert lib.gsis_set_velocity_grid(ctx, ctypes.byref(wide)) == gsis.GSIS_ERR_UNSUPPORTED
+    assert b"FP32 exponent range" in lib.gsis_last_error(ctx)
+    assert lib.gsis_set_velocity_grid(ctx, ctypes.byref(vg)) == gsis.GSIS_OK
+    # the same faces around cells of volume 1e-60 (sum |S|/V near 1e60) against the set grid
+    tiny = _mesh_desc(gsis, case.mesh, case.W0, keep)
+    vols = np.full(case.mesh.ncell, 1e-60)
+    keep.append(vols)
+    tiny.volumes = vols.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.gsis_set_mesh(ctx, ctypes.byref(tiny)) == gsis.GSIS_ERR_UNSUPPORTED
+    rep = gsis.Report()
+    assert lib.gsis_iterate(ctx, 1, ctypes.byref(rep)) == gsis.GSIS_OK and np.isfinite(rep.eps)
+    lib.gsis_free(ctx)
+
+
 def test_diverging_run_reports_nonfinite():
     """An all-kinetic O-grid run started from the uniform stream without the
     NS presolve and without the time term diverges (its state leaves the
