@@ -385,27 +385,29 @@ __device__ __forceinline__ __nv_bfloat16 rounded<float, __nv_bfloat16>(float v, 
 }
 template <>
 __device__ __forceinline__ __half rounded<float, __half>(float v, unsigned key) {
+    // Both roundings are formed and one is selected (Maxwellian tails put
+    // normal and subnormal results in most warps, where a branch runs both
+    // anyway); one hash serves both.
     const unsigned b = __float_as_uint(v);
     const unsigned mag = b & 0x7fffffffu;
-    if (mag >= 0x38800000u && mag < 0x477fe000u) {
-        // |v| in FP16's normal range (2^-14 up to the last binade below 65504): FP16
-        // keeps the top 10 of FP32's 23 fraction bits, so adding 13 uniform random
-        // bits below them and truncating toward zero rounds up with probability
-        // equal to the dropped fraction (as for BF16)
-        const unsigned r = mix32(key ^ b) & 0x1fffu;
-        return __float2half_rz(__uint_as_float(b + r));
-    }
-    if (mag < 0x38800000u) {
-        // below 2^-14: FP16's subnormals, m 2^-24 for m = 0..1023, so |v| 2^24 (exact)
-        // splits into the lower m and the fraction that rounds up (m + 1 = 1024 is
-        // the smallest normal, whose bits follow on)
-        const float r = __uint_as_float(mag) * 16777216.0f;
-        const unsigned m = (unsigned)r;
-        const float frac = r - (float)m;
-        const float u = (float)(mix32(key ^ b) >> 8) * (1.0f / 16777216.0f);
-        return __ushort_as_half((unsigned short)(((b >> 16) & 0x8000u) | (m + (u < frac ? 1u : 0u))));
-    }
-    return __float2half_rn(v);   // beyond the largest finite FP16, inf, nan: nearest
+    const unsigned h = mix32(key ^ b);
+    // |v| in FP16's normal range (2^-14 up to the last binade below 65504): FP16
+    // keeps the top 10 of FP32's 23 fraction bits, so adding 13 uniform random
+    // bits below them and truncating toward zero rounds up with probability
+    // equal to the dropped fraction (as for BF16)
+    const __half hn = __float2half_rz(__uint_as_float(b + (h & 0x1fffu)));
+    // below 2^-14: FP16's subnormals, m 2^-24 for m = 0..1023, so |v| 2^24 (exact)
+    // splits into the lower m and the fraction that rounds up (m + 1 = 1024 is
+    // the smallest normal, whose bits follow on); clamped so that the
+    // conversion stays in range where this result is not the one selected
+    const float r = fminf(__uint_as_float(mag) * 16777216.0f, 2048.0f);
+    const unsigned m = (unsigned)r;
+    const float frac = r - (float)m;
+    const float u = (float)(h >> 8) * (1.0f / 16777216.0f);
+    const __half hs = __ushort_as_half((unsigned short)(((b >> 16) & 0x8000u) | (m + (u < frac ? 1u : 0u))));
+    // beyond the largest finite FP16, inf, nan: nearest
+    const __half ho = __float2half_rn(v);
+    return mag < 0x38800000u ? hs : (mag < 0x477fe000u ? hn : ho);
 }
 __device__ __forceinline__ unsigned corr_key(int k, int v) {
     return (unsigned)k * 0x9e3779b9u ^ (unsigned)v * 0x85ebca6bu;
