@@ -53,7 +53,8 @@ __device__ __forceinline__ float2 hmm2(float2 a, float2 b) {
 template <typename S> __device__ __forceinline__ float2 ld2(const S* p);
 template <> __device__ __forceinline__ float2 ld2<float>(const float* p) { return *reinterpret_cast<const float2*>(p); }
 template <> __device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    const unsigned w = *reinterpret_cast<const unsigned*>(p);   // element 0 in the low half
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 template <> __device__ __forceinline__ float2 ld2<__half>(const __half* p) {
     return __half22float2(*reinterpret_cast<const __half2*>(p));
