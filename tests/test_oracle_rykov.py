@@ -15,7 +15,8 @@ What fixes each function, other than its own formula:
 * Eq. updatef leaves every kinetic cell with the conserved moments of the new
   macroscopic state, a uniform equilibrium stream is a fixed point, and a
   nitrogen shock relaxes its internal temperature behind the translational
-  one.
+  one;
+* on a 2D flow the reduced-grid iteration is the xi_z integral of the 3D one.
 """
 import os
 
