@@ -344,6 +344,36 @@ const char* gsis_tuning_info(gsis_ctx* ctx);
  * next call from the same thread. */
 const char* gsis_batch_info(gsis_ctx** ctxs, int n);
 
+/* Reference distribution pair of the two-VDF model of a gas with d_r internal
+ * degrees of freedom (Sec. 2, Eq. general_model): for each state, on the
+ * context's velocity grid,
+ *   g0 = (1 - 1/Z_r) g_0t + g_0r / Z_r,   g1 = (1 - 1/Z_r) g_1t + g_1r / Z_r,
+ * with g_0t the Shakhov form at (T_t, q_t), g_0r the one at the equilibrium
+ * temperature T = (3 T_t + d_r T_r)/(3 + d_r) and q0, g_1t = (d_r/2) T_r g_0t +
+ * M_t (q_r.c)/(rho T_t), g_1r = (d_r/2) T g_0r + M_T (q1.c)/(rho T) (R = 1),
+ * (q0, q1) the mixing of (q_t, q_r) by the A matrix.  g_0t and g_0r are
+ * conservation-corrected (their discrete mass, momentum and translational
+ * energy are exact), and so are the Maxwellians M_t, M_T of the q terms, so
+ * that the pair conserves mass, momentum and total energy on the grid.  This
+ * is the reference pair of the two-VDF kinetic step, which gsis_iterate does
+ * not run (gsis_init refuses d_r > 0); it is evaluated here on its own.
+ *
+ * ctx:    a context whose velocity grid is set (full 3D grids only); its
+ *         allocator and stream are used, and the call synchronises the stream.
+ * S:      device pointer, [n][12] states: rho, u_x, u_y, u_z, T_t, T_r,
+ *         q_t (3), q_r (3); rho, T_t > 0 and (d_r > 0) T_r > 0; 0 <= n <= 65535.
+ * d_r, Z_r, A: the gas (A = A_tt, A_tr, A_rt, A_rr; host pointer); Z_r >= 1.
+ * g_out:  device pointer, [n][2][Nv] doubles (x fastest): g0 then g1 of each
+ *         state; written in full, owned by the caller.
+ * Allocates scratch of 4 n (16 + 5 (nx + ny + nz)) doubles through the
+ * context's allocator for the duration of the call.
+ * Errors: GSIS_ERR_ARG (NULL, n out of range, bad gas, non-finite or
+ * non-positive states; checked before any launch), GSIS_ERR_STATE (no
+ * velocity grid), GSIS_ERR_UNSUPPORTED (reduced grid), GSIS_ERR_OOM,
+ * GSIS_ERR_CUDA. */
+gsis_status gsis_two_vdf_reference(gsis_ctx* ctx, const double* S, int n, int d_r, double Z_r, const double* A,
+                                   double* g_out);
+
 /* Human-readable description of the last error on this context (never NULL). */
 const char* gsis_last_error(const gsis_ctx* ctx);
 

@@ -15,6 +15,7 @@
 //      sum_v w psi phi^T M a = U - sum_v w psi D,  psi = (1, xi, |xi|^2/2),
 //      phi = (1, xi, |xi|^2),
 //    whose sums are assembled exactly from 1D sums C_d[k] = sum_i e_d c_d^k.
+#include <algorithm>
 #include <type_traits>
 #include "gsis_device.cuh"
 
@@ -549,6 +550,98 @@ void launch_seed_records(gsis_ctx* c, int ne, int grad13) {
                                                            c->specs);
     c->launches++;
     launch_build_records(c, c->recNew, ne, c->specs);
+}
+
+
+// ---------------------------------------------------------------------------- two-VDF reference pair
+// Reference pair of Eq. general_model, g = (1 - 1/Z_r) g_t + g_r / Z_r for
+// f0 and f1, for states S[n][12] = (rho, u (3), T_t, T_r, q_t (3), q_r (3)) on
+// a full 3D grid.  Four conservation-corrected records per state: the
+// Shakhov forms g_0t at (T_t, q_t) and g_0r at (T, q0), each corrected to its
+// own translational energy, and the Maxwellians M~ at T_t and at T; per node
+//   g0 = a g_0t + b g_0r,
+//   g1 = a [(d_r/2) T_r g_0t + M~_t (q_r.c)/(rho T_t)] + b [(d_r/2) T g_0r + M~_T (q1.c)/(rho T)],
+// a = 1 - 1/Z_r, b = 1/Z_r, T = (3 T_t + d_r T_r)/(3 + d_r) and (q0, q1) the
+// mixing of (q_t, q_r) of Sec. 2 (g_1t and g_1r with R = 1: their
+// Maxwellian factor is rho^-1 times that of g_0t, g_0r).
+__device__ static void two_vdf_mix(const TwoVdfGas& g, const double* qt, const double* qr, double* q0, double* q1) {
+    const double m00 = (2.0 - 3.0 * g.A[0]) * g.Zr + 1.0, m01 = -3.0 * g.A[1] * g.Zr;
+    const double m10 = -g.A[2] * g.Zr, m11 = -g.A[3] * g.Zr + 1.0;
+    for (int d = 0; d < 3; ++d) {
+        q0[d] = m00 * qt[d] + m01 * qr[d];
+        q1[d] = m10 * qt[d] + m11 * qr[d];
+    }
+}
+
+__device__ static RecSpec spec_shakhov(double rho, const double* u, double T, const double* q) {
+    RecSpec s;
+    spec_maxwellian(s, rho, u, T, 1);
+    const double sc = 1.0 / (15.0 * rho * T * T * T);   // 1/(15 p T^2), p = rho T
+    for (int d = 0; d < 3; ++d) { s.p[d] = -5.0 * T * sc * q[d]; s.r[d] = sc * q[d]; }
+    return s;
+}
+
+__global__ void k_two_vdf_specs(int n, const double* __restrict__ S, TwoVdfGas g, RecSpec* __restrict__ specs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double* s = S + (long long)k * 12;
+    const double rho = s[0], Tt = s[4], Tr = s[5];
+    const double T = (3.0 * Tt + g.d_r * Tr) / (3.0 + g.d_r);
+    double q0[3], q1[3];
+    two_vdf_mix(g, s + 6, s + 9, q0, q1);
+    RecSpec m;
+    specs[4 * k + 0] = spec_shakhov(rho, s + 1, Tt, s + 6);
+    specs[4 * k + 1] = spec_shakhov(rho, s + 1, T, q0);
+    spec_maxwellian(m, rho, s + 1, Tt, 1);
+    specs[4 * k + 2] = m;
+    spec_maxwellian(m, rho, s + 1, T, 1);
+    specs[4 * k + 3] = m;
+}
+
+// grid (x: velocity blocks, y: state); out[k][0][v] = g0, out[k][1][v] = g1
+__global__ void k_two_vdf_eval(int n, const double* __restrict__ S, TwoVdfGas g, Records rec, VGridDev vg,
+                               double* __restrict__ out) {
+    const int k = blockIdx.y;
+    if (k >= n) return;
+    const long long Nv = vg.Nv;
+    const int nx = vg.nx, ny = vg.ny, NT = vg.NT;
+    const double* s = S + (long long)k * 12;
+    const double rho = s[0], Tt = s[4], Tr = s[5];
+    const double T = (3.0 * Tt + g.d_r * Tr) / (3.0 + g.d_r);
+    double q0[3], q1[3];
+    two_vdf_mix(g, s + 6, s + 9, q0, q1);
+    const double a = 1.0 - 1.0 / g.Zr, b = 1.0 / g.Zr;
+    const double* sc = rec.scal + (long long)4 * k * RS;
+    const double* tb = rec.tab + (long long)4 * k * NTAB * NT;
+    const long long TS = (long long)NTAB * NT;
+    double* o0 = out + (long long)k * 2 * Nv;
+    double* o1 = o0 + Nv;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Nv; v += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(v % nx);
+        const long long rr = v / nx;
+        const int iy = (int)(rr % ny), iz = (int)(rr / ny);
+        const double c0 = vg.xi[ix] - s[1], c1 = vg.xi[nx + iy] - s[2], c2 = vg.xi[nx + ny + iz] - s[3];
+        const double G0t = eval_rec(sc, tb, NT, nx, ny, ix, iy, iz);
+        const double G0r = eval_rec(sc + RS, tb + TS, NT, nx, ny, ix, iy, iz);
+        const double Mt = eval_rec(sc + 2 * RS, tb + 2 * TS, NT, nx, ny, ix, iy, iz);
+        const double Mr = eval_rec(sc + 3 * RS, tb + 3 * TS, NT, nx, ny, ix, iy, iz);
+        const double qrc = s[9] * c0 + s[10] * c1 + s[11] * c2;
+        const double q1c = q1[0] * c0 + q1[1] * c1 + q1[2] * c2;
+        o0[v] = a * G0t + b * G0r;
+        o1[v] = a * (0.5 * g.d_r * Tr * G0t + Mt * qrc / (rho * Tt)) + b * (0.5 * g.d_r * T * G0r + Mr * q1c / (rho * T));
+    }
+}
+
+void launch_two_vdf_reference(gsis_ctx* c, const double* S, int n, const TwoVdfGas& g, RecSpec* specs,
+                              const Records& rec, double* out) {
+    if (n <= 0) return;
+    k_two_vdf_specs<<<(n + 127) / 128, 128, 0, c->stream>>>(n, S, g, specs);
+    c->launches++;
+    launch_build_records(c, rec, 4 * n, specs);
+    const long long Nv = c->vg.Nv;
+    const int bx = (int)std::min<long long>((Nv + 255) / 256, 64);
+    k_two_vdf_eval<<<dim3(bx, n), 256, 0, c->stream>>>(n, S, g, rec, c->vg, out);
+    c->launches++;
 }
 
 }  // namespace gsis

@@ -1184,6 +1184,50 @@ gsis_status gsis_get_vdf(gsis_ctx* c, double* dst, int* cells, long long capacit
     return GSIS_OK;
 }
 
+gsis_status gsis_two_vdf_reference(gsis_ctx* c, const double* S, int n, int d_r, double Z_r, const double* A,
+                                   double* g_out) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!S || !A || !g_out || n < 0) return set_err(c, GSIS_ERR_ARG, "NULL argument or n < 0");
+    if (n > 65535) return set_err(c, GSIS_ERR_ARG, "at most 65535 states per call");
+    if (d_r < 0 || !(Z_r >= 1.0) || !std::isfinite(Z_r) || !finite_all(A, 4))
+        return set_err(c, GSIS_ERR_ARG, "need d_r >= 0, finite Z_r >= 1 and a finite A matrix");
+    if (!c->vgrid_set) return set_err(c, GSIS_ERR_STATE, "velocity grid not set");
+    if (c->vg.reduced) return set_err(c, GSIS_ERR_UNSUPPORTED, "two-VDF reference pair: full 3D velocity grids only");
+    if (n == 0) return GSIS_OK;
+    // the states are few: check them on the host before any launch
+    std::vector<double> h((size_t)n * 12);
+    if (!cuda_ok(c, cudaMemcpyAsync(h.data(), S, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                 "gsis_two_vdf_reference") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "gsis_two_vdf_reference"))
+        return GSIS_ERR_CUDA;
+    if (!finite_all(h.data(), h.size())) return set_err(c, GSIS_ERR_ARG, "non-finite state");
+    for (int k = 0; k < n; ++k) {
+        const double* s = &h[(size_t)k * 12];
+        if (!(s[0] > 0.0) || !(s[4] > 0.0) || (d_r > 0 && !(s[5] > 0.0)))
+            return set_err(c, GSIS_ERR_ARG, "states need rho > 0, T_t > 0 and (d_r > 0) T_r > 0");
+    }
+    const int NT = c->vg.NT;
+    RecSpec* specs = (RecSpec*)dev_alloc(c, (size_t)4 * n * sizeof(RecSpec));
+    Records rec{};
+    rec.scal = (double*)dev_alloc(c, (size_t)4 * n * RS * sizeof(double));
+    rec.tab = (double*)dev_alloc(c, (size_t)4 * n * NTAB * NT * sizeof(double));
+    gsis_status out = GSIS_OK;
+    if (!specs || !rec.scal || !rec.tab) {
+        out = set_err(c, GSIS_ERR_OOM, "device allocation failed in gsis_two_vdf_reference");
+    } else {
+        TwoVdfGas g{d_r, Z_r, {A[0], A[1], A[2], A[3]}};
+        launch_two_vdf_reference(c, S, n, g, specs, rec, g_out);
+        if (!cuda_ok(c, cudaGetLastError(), "gsis_two_vdf_reference launch") ||
+            !cuda_ok(c, cudaStreamSynchronize(c->stream), "gsis_two_vdf_reference"))
+            out = GSIS_ERR_CUDA;
+    }
+    dev_free(c, specs);
+    dev_free(c, rec.scal);
+    dev_free(c, rec.tab);
+    return out;
+}
+
 const char* gsis_last_error(const gsis_ctx* c) {
     if (!c) return "NULL context";
     return c->err.c_str();

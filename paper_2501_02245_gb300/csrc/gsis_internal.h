@@ -250,6 +250,12 @@ void launch_wall_den(gsis_ctx* c);
 void launch_ghost_records(gsis_ctx* c);
 void launch_correction_records(gsis_ctx* c);
 void launch_seed_records(gsis_ctx* c, int n_enter, int grad13);
+// Reference pair (g0, g1) of the two-VDF model for n states [n][12] (rho, u,
+// T_t, T_r, q_t, q_r) into out[n][2][Nv]; specs [4n] and rec (4n records)
+// are scratch of the caller.
+struct TwoVdfGas { int d_r; double Zr; double A[4]; };
+void launch_two_vdf_reference(gsis_ctx* c, const double* S, int n, const TwoVdfGas& g, RecSpec* specs,
+                              const Records& rec, double* out);
 // sweep.cu
 void launch_sweep(gsis_ctx* c, int pass);
 gsis_status tune_sweep(gsis_ctx* c);

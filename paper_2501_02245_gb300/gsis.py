@@ -28,7 +28,7 @@ EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterat
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
             "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
             "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments", "gsis_debug_set_macro_path",
-            "gsis_probe_fma_peak", "gsis_debug_set_batch_tile"]
+            "gsis_probe_fma_peak", "gsis_debug_set_batch_tile", "gsis_two_vdf_reference"]
 MACRO_PATHS = {"auto": 0, "fused": 1, "multi": 2, "persistent": 3, "persistent_stall": 4}
 
 
@@ -115,6 +115,8 @@ def load():
     lib.gsis_debug_set_batch_tile.restype = c_int
     lib.gsis_probe_fma_peak.argtypes = [c_int, vp, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]
     lib.gsis_probe_fma_peak.restype = c_int
+    lib.gsis_two_vdf_reference.argtypes = [vp, vp, c_int, c_int, c_double, ctypes.POINTER(c_double), vp]
+    lib.gsis_two_vdf_reference.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
     lib.gsis_tuning_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
@@ -296,6 +298,21 @@ class Solver:
         names = ["hot_sxx", "hot_syy", "hot_szz", "hot_sxy", "hot_sxz", "hot_syz", "hot_qx", "hot_qy", "hot_qz"]
         m = self.moments(names)
         return np.stack([m[n] for n in names], axis=1)
+
+    def two_vdf_reference(self, S, d_r, Z_r, A):
+        """Reference pair (g0, g1) of the two-VDF model (gsis_two_vdf_reference)
+        for states S [n, 12] (rho, u (3), T_t, T_r, q_t (3), q_r (3)) on this
+        solver's velocity grid; returns [n, 2, Nv] on the host."""
+        import torch
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(-1, 12))
+        n = S.shape[0]
+        dS = torch.from_numpy(S).to("cuda")
+        out = torch.empty((n, 2, self.nv), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()   # the library works on its own stream
+        Ah = (ctypes.c_double * 4)(*[float(a) for a in A])
+        self._check(self.lib.gsis_two_vdf_reference(self.ctx, ctypes.c_void_p(dS.data_ptr()), n, int(d_r),
+                                                    float(Z_r), Ah, ctypes.c_void_p(out.data_ptr())))
+        return out.cpu().numpy()
 
     def dvm_flags(self):
         return self.moments(("dvm",))["dvm"] > 0.5
