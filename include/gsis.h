@@ -374,6 +374,24 @@ const char* gsis_batch_info(gsis_ctx** ctxs, int n);
 gsis_status gsis_two_vdf_reference(gsis_ctx* ctx, const double* S, int n, int d_r, double Z_r, const double* A,
                                    double* g_out);
 
+/* Moments of two-VDF distribution pairs (Sec. 2, Eq. getmoment) on the
+ * context's velocity grid, the reduction of the two-VDF kinetic step
+ * (evaluated on its own, as gsis_two_vdf_reference): rho and u from f0; about
+ * u the traceless stress sigma = P - tr P/3 I and the heat flux
+ * q_t = 1/2 sum w c |c|^2 f0 of f0, T_t = tr P/(3 rho); from f1
+ * d_r/2 rho T_r = sum w f1 and q_r = sum w c f1 (T_r = T_t when d_r = 0).
+ * FP64 sums.
+ *
+ * ctx:  a context whose velocity grid is set (full 3D grids only); its stream
+ *       is used and synchronised.
+ * F:    device pointer, [n][2][Nv] doubles (x fastest): f0 then f1 of each
+ *       pair (as gsis_two_vdf_reference writes them); 0 <= n <= 65535.
+ * out:  device pointer, [n][18] doubles: rho, u (3), T_t, T_r, sigma (xx, yy,
+ *       zz, xy, xz, yz), q_t (3), q_r (3); owned by the caller.
+ * Errors: GSIS_ERR_ARG (NULL, n or d_r out of range), GSIS_ERR_STATE (no
+ * velocity grid), GSIS_ERR_UNSUPPORTED (reduced grid), GSIS_ERR_CUDA. */
+gsis_status gsis_two_vdf_moments(gsis_ctx* ctx, const double* F, int n, int d_r, double* out);
+
 /* Human-readable description of the last error on this context (never NULL). */
 const char* gsis_last_error(const gsis_ctx* ctx);
 

@@ -1228,6 +1228,21 @@ gsis_status gsis_two_vdf_reference(gsis_ctx* c, const double* S, int n, int d_r,
     return out;
 }
 
+gsis_status gsis_two_vdf_moments(gsis_ctx* c, const double* F, int n, int d_r, double* out) {
+    gsis_status st = check_ctx(c);
+    if (st != GSIS_OK) return st;
+    if (!F || !out || n < 0 || d_r < 0) return set_err(c, GSIS_ERR_ARG, "NULL argument, n < 0 or d_r < 0");
+    if (n > 65535) return set_err(c, GSIS_ERR_ARG, "at most 65535 pairs per call");
+    if (!c->vgrid_set) return set_err(c, GSIS_ERR_STATE, "velocity grid not set");
+    if (c->vg.reduced) return set_err(c, GSIS_ERR_UNSUPPORTED, "two-VDF moments: full 3D velocity grids only");
+    if (n == 0) return GSIS_OK;
+    launch_two_vdf_moments(c, F, n, d_r, out);
+    if (!cuda_ok(c, cudaGetLastError(), "gsis_two_vdf_moments launch") ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream), "gsis_two_vdf_moments"))
+        return GSIS_ERR_CUDA;
+    return GSIS_OK;
+}
+
 const char* gsis_last_error(const gsis_ctx* c) {
     if (!c) return "NULL context";
     return c->err.c_str();

@@ -256,6 +256,8 @@ void launch_seed_records(gsis_ctx* c, int n_enter, int grad13);
 struct TwoVdfGas { int d_r; double Zr; double A[4]; };
 void launch_two_vdf_reference(gsis_ctx* c, const double* S, int n, const TwoVdfGas& g, RecSpec* specs,
                               const Records& rec, double* out);
+// moments.cu: Eq. getmoment of n pairs F[n][2][Nv] into out[n][18]
+void launch_two_vdf_moments(gsis_ctx* c, const double* F, int n, int d_r, double* out);
 // sweep.cu
 void launch_sweep(gsis_ctx* c, int pass);
 gsis_status tune_sweep(gsis_ctx* c);

@@ -854,4 +854,87 @@ void launch_hot(gsis_ctx* c) {
     c->launches++;
 }
 
+// ---------------------------------------------------------------------------- two-VDF moments
+// Eq. getmoment for the two-VDF model, one block per state of F[n][2][Nv]
+// (f0 then f1 on a full 3D grid): rho, u from f0; then, about u, the
+// pressure tensor P and heat flux q_t = 1/2 sum w c |c|^2 f0, and
+// q_r = sum w c f1, d_r/2 rho T_r = sum w f1.  out[k][18] = rho, u (3), T_t,
+// T_r, sigma (xx, yy, zz, xy, xz, yz), q_t (3), q_r (3); T_t = tr P/(3 rho),
+// sigma = P - tr P/3 I, T_r = T_t when d_r = 0.  FP64 sums in a fixed order
+// (block reduction through shared memory).
+constexpr int TWO_VDF_THREADS = 256;
+
+__device__ static void block_sum(double* v, int m, double* sh) {
+    // sums v[0..m) over the block into sh[0..m) (m <= 16); every thread gets the result in v
+    for (int i = 0; i < m; ++i) sh[i * TWO_VDF_THREADS + threadIdx.x] = v[i];
+    __syncthreads();
+    for (int stride = TWO_VDF_THREADS / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride)
+            for (int i = 0; i < m; ++i)
+                sh[i * TWO_VDF_THREADS + threadIdx.x] += sh[i * TWO_VDF_THREADS + threadIdx.x + stride];
+        __syncthreads();
+    }
+    for (int i = 0; i < m; ++i) v[i] = sh[i * TWO_VDF_THREADS];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(TWO_VDF_THREADS) k_two_vdf_moments(int n, const double* __restrict__ F, int d_r,
+                                                                     VGridDev vg, double* __restrict__ out) {
+    __shared__ double sh[16 * TWO_VDF_THREADS];
+    const int k = blockIdx.x;
+    if (k >= n) return;
+    const long long Nv = vg.Nv;
+    const int nx = vg.nx, ny = vg.ny;
+    const double* f0 = F + (long long)k * 2 * Nv;
+    const double* f1 = f0 + Nv;
+    double a[16];
+    for (int i = 0; i < 4; ++i) a[i] = 0.0;
+    for (long long v = threadIdx.x; v < Nv; v += TWO_VDF_THREADS) {
+        const int ix = (int)(v % nx);
+        const long long rr = v / nx;
+        const int iy = (int)(rr % ny), iz = (int)(rr / ny);
+        const double f = f0[v];
+        a[0] += f;
+        a[1] += vg.xi[ix] * f;
+        a[2] += vg.xi[nx + iy] * f;
+        a[3] += vg.xi[nx + ny + iz] * f;
+    }
+    block_sum(a, 4, sh);
+    const double rho = vg.w * a[0];
+    const double u[3] = {vg.w * a[1] / rho, vg.w * a[2] / rho, vg.w * a[3] / rho};
+    for (int i = 0; i < 14; ++i) a[i] = 0.0;
+    for (long long v = threadIdx.x; v < Nv; v += TWO_VDF_THREADS) {
+        const int ix = (int)(v % nx);
+        const long long rr = v / nx;
+        const int iy = (int)(rr % ny), iz = (int)(rr / ny);
+        const double c0 = vg.xi[ix] - u[0], c1 = vg.xi[nx + iy] - u[1], c2 = vg.xi[nx + ny + iz] - u[2];
+        const double f = f0[v], g = f1[v];
+        const double c2f = (c0 * c0 + c1 * c1 + c2 * c2) * f;
+        a[0] += c0 * c0 * f; a[1] += c1 * c1 * f; a[2] += c2 * c2 * f;
+        a[3] += c0 * c1 * f; a[4] += c0 * c2 * f; a[5] += c1 * c2 * f;
+        a[6] += c0 * c2f; a[7] += c1 * c2f; a[8] += c2 * c2f;
+        a[9] += g; a[10] += c0 * g; a[11] += c1 * g; a[12] += c2 * g;
+    }
+    block_sum(a, 13, sh);
+    if (threadIdx.x != 0) return;
+    const double w = vg.w;
+    const double P[6] = {w * a[0], w * a[1], w * a[2], w * a[3], w * a[4], w * a[5]};
+    const double tr = P[0] + P[1] + P[2];
+    const double Tt = tr / (3.0 * rho);
+    double* o = out + (long long)k * 18;
+    o[0] = rho; o[1] = u[0]; o[2] = u[1]; o[3] = u[2];
+    o[4] = Tt;
+    o[5] = d_r > 0 ? 2.0 * w * a[9] / (d_r * rho) : Tt;
+    o[6] = P[0] - tr / 3.0; o[7] = P[1] - tr / 3.0; o[8] = P[2] - tr / 3.0;
+    o[9] = P[3]; o[10] = P[4]; o[11] = P[5];
+    o[12] = 0.5 * w * a[6]; o[13] = 0.5 * w * a[7]; o[14] = 0.5 * w * a[8];
+    o[15] = w * a[10]; o[16] = w * a[11]; o[17] = w * a[12];
+}
+
+void launch_two_vdf_moments(gsis_ctx* c, const double* F, int n, int d_r, double* out) {
+    if (n <= 0) return;
+    k_two_vdf_moments<<<n, TWO_VDF_THREADS, 0, c->stream>>>(n, F, d_r, c->vg, out);
+    c->launches++;
+}
+
 }  // namespace gsis

@@ -28,7 +28,8 @@ EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterat
             "gsis_get_vdf", "gsis_debug_set_region", "gsis_last_error", "gsis_free", "gsis_version",
             "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
             "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments", "gsis_debug_set_macro_path",
-            "gsis_probe_fma_peak", "gsis_debug_set_batch_tile", "gsis_two_vdf_reference"]
+            "gsis_probe_fma_peak", "gsis_debug_set_batch_tile", "gsis_two_vdf_reference",
+            "gsis_two_vdf_moments"]
 MACRO_PATHS = {"auto": 0, "fused": 1, "multi": 2, "persistent": 3, "persistent_stall": 4}
 
 
@@ -117,6 +118,8 @@ def load():
     lib.gsis_probe_fma_peak.restype = c_int
     lib.gsis_two_vdf_reference.argtypes = [vp, vp, c_int, c_int, c_double, ctypes.POINTER(c_double), vp]
     lib.gsis_two_vdf_reference.restype = c_int
+    lib.gsis_two_vdf_moments.argtypes = [vp, vp, c_int, c_int, vp]
+    lib.gsis_two_vdf_moments.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
     lib.gsis_tuning_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
@@ -312,6 +315,20 @@ class Solver:
         Ah = (ctypes.c_double * 4)(*[float(a) for a in A])
         self._check(self.lib.gsis_two_vdf_reference(self.ctx, ctypes.c_void_p(dS.data_ptr()), n, int(d_r),
                                                     float(Z_r), Ah, ctypes.c_void_p(out.data_ptr())))
+        return out.cpu().numpy()
+
+    def two_vdf_moments(self, F, d_r):
+        """Moments of two-VDF pairs F [n, 2, Nv] on this solver's velocity grid
+        (gsis_two_vdf_moments): [n, 18] = rho, u (3), T_t, T_r, sigma (6), q_t
+        (3), q_r (3), on the host."""
+        import torch
+        F = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(-1, 2, self.nv))
+        n = F.shape[0]
+        dF = torch.from_numpy(F).to("cuda")
+        out = torch.empty((n, 18), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()   # the library works on its own stream
+        self._check(self.lib.gsis_two_vdf_moments(self.ctx, ctypes.c_void_p(dF.data_ptr()), n, int(d_r),
+                                                  ctypes.c_void_p(out.data_ptr())))
         return out.cpu().numpy()
 
     def dvm_flags(self):

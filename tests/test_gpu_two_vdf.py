@@ -1,6 +1,7 @@
-"""GPU parity of the two-VDF reference pair (gsis_two_vdf_reference) with the
-pinned oracle (oracle.rykov.RykovGrid.reference), element by element on a
-full 3D velocity grid: the paper's nitrogen gas, a made-up A matrix (so that
+"""GPU parity of the two-VDF reference pair (gsis_two_vdf_reference) and of
+the two-VDF moments (gsis_two_vdf_moments) with the pinned oracle
+(oracle.rykov.RykovGrid.reference, .moments), element by element on a full
+3D velocity grid.  The reference pair: the paper's nitrogen gas, a made-up A matrix (so that
 no mixing coefficient can be swapped unnoticed), and the monatomic case,
 where the pair must reduce to the oracle's conservation-corrected Shakhov
 form and g1 = 0.  The refusals of the entry point are host-side checks made
@@ -94,3 +95,30 @@ def test_two_vdf_reference_refusals():
     assert lib.gsis_two_vdf_reference(r.ctx, vp(good.data_ptr()), 2, 2, 2.667, A,
                                       vp(out.data_ptr())) == gsis.GSIS_ERR_UNSUPPORTED
     r.close()
+
+
+@pytest.mark.parametrize("d_r", [2, 0])
+def test_two_vdf_moments_match_the_oracle(d_r):
+    """gsis_two_vdf_moments against the oracle's Eq. getmoment
+    (RykovGrid.moments) on pairs far from equilibrium: the Grad-13 pair of a
+    stressed, heat-conducting state plus a second population, so that every
+    moment (stress, both heat fluxes, T_t != T_r) is nonzero."""
+    case, s = _solver()
+    vg = RykovGrid(M.VelocityGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi), d_r)
+    sig = np.array([[0.05, -0.02, 0.01], [-0.02, -0.03, 0.0], [0.01, 0.0, -0.02]])
+    F = []
+    for st in STATES[1:]:
+        f = (vg.grad13(st[0], st[1:4], st[4], st[5], sig, st[6:9], st[9:12])
+             + vg.equilibrium(0.3, np.array([-0.5, 0.2, 0.1]), 1.9, 0.7))
+        F.append(np.stack(vg.split(f)))
+    F = np.array(F)
+    m = s.two_vdf_moments(F, d_r)
+    assert m.shape == (len(F), 18)
+    for k in range(len(F)):
+        rho, u, Tt, Tr, sg, qt, qr = vg.moments(vg.join(F[k, 0], F[k, 1]))
+        ref = np.concatenate([[rho], u, [Tt, Tr], [sg[0, 0], sg[1, 1], sg[2, 2], sg[0, 1], sg[0, 2], sg[1, 2]],
+                              qt, qr])
+        assert np.max(np.abs(m[k] - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref))), k
+        assert min(np.linalg.norm(ref[6:12]), np.linalg.norm(ref[12:15]), np.linalg.norm(ref[15:18])) > 1e-3
+        assert d_r == 0 or abs(Tt - Tr) > 1e-2
+    s.close()
