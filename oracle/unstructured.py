@@ -1,0 +1,189 @@
+"""Unstructured two-dimensional meshes for the oracle (test infrastructure only).
+
+The paper's three-dimensional runs (Secs. 4.3, 4.4) use unstructured spatial
+meshes; it describes neither their data structures nor their reconstruction.
+This module gives the oracle polygon meshes (unit depth in z, like the
+structured 2D meshes) with the interface the transport sweep of
+oracle.kinetic and the synthetic solve of oracle.macro use, so that the
+whole GSIS iteration of oracle.gsis runs on them unchanged.  Readings:
+
+* face values are first order (the upwind cell value): index-space slopes do
+  not exist on such a mesh, and the paper does not state the unstructured
+  reconstruction; the synthetic solve's splitting is first order too;
+* the Gauss-Seidel order is by a per-cell key (default x + y of the centroid,
+  i.e. the diagonal hyperplanes of a square structured grid); cells with
+  nearly equal keys are not face neighbours on the meshes used here, so the
+  order inside such a group does not change the result;
+* the wall layers of the region rule (Sec. 4.4) are the cells within
+  `wall_layers` face-neighbour steps of a wall face.
+
+Boundary faces carry a tag 0..5 that indexes bc_type / bc_state, as the six
+sides of a structured block do.
+"""
+from dataclasses import dataclass
+import numpy as np
+
+from .mesh import Side, BC_NONE, BC_FARFIELD, BC_WALL
+from .macro import MacroGeometry
+from .gsis import OracleSolver
+from .reduced import ReducedGrid
+from .hybrid import HybridGrid
+from . import model as M
+
+
+@dataclass
+class PolygonMesh:
+    """vertices [nV, 2]; cells: vertex-index lists in counter-clockwise order
+    (3 to 6 vertices); boundary: {(a, b) with a < b: tag} for every edge that
+    belongs to one cell only; bc_type [6], bc_state [6][5] per tag; W0 [N, 5];
+    key: optional per-cell sweep-order key."""
+    vertices: np.ndarray
+    cells: list
+    boundary: dict
+    bc_type: list
+    bc_state: np.ndarray
+    W0: np.ndarray = None
+    key: np.ndarray = None
+    dim: int = 2
+
+    @property
+    def ncell(self):
+        return len(self.cells)
+
+
+def polygon_geometry(P):
+    """Area and centroid of a simple polygon with counter-clockwise vertices P [m, 2]."""
+    x, y = P[:, 0], P[:, 1]
+    xn, yn = np.roll(x, -1), np.roll(y, -1)
+    cr = x * yn - xn * y
+    A = 0.5 * np.sum(cr)
+    cx = np.sum((x + xn) * cr) / (6.0 * A)
+    cy = np.sum((y + yn) * cr) / (6.0 * A)
+    return A, np.array([cx, cy])
+
+
+class UnstructuredTopology:
+    """The interface of oracle.mesh.Topology for a PolygonMesh: sides with
+    outward area vectors (dy, -dx, 0) of each counter-clockwise edge (unit
+    depth), edge midpoints, neighbours across shared edges; no index-space
+    steps (step() is always -1, so face values are first order)."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        self.ncell = mesh.ncell
+        self.dim = 2
+        self.n = (self.ncell, 1, 1)
+        V = np.asarray(mesh.vertices, dtype=np.float64)
+        self.vol = np.zeros(self.ncell)
+        self.centers = np.zeros((self.ncell, 3))
+        owner = {}
+        for c, cell in enumerate(mesh.cells):
+            assert 3 <= len(cell) <= 6
+            A, ctr = polygon_geometry(V[cell])
+            assert A > 0.0, "cell %d is not counter-clockwise" % c
+            self.vol[c] = A
+            self.centers[c] = [ctr[0], ctr[1], 0.5]
+            for a, b in zip(cell, cell[1:] + cell[:1]):
+                owner.setdefault((min(a, b), max(a, b)), []).append(c)
+        self.sides = []
+        for c, cell in enumerate(mesh.cells):
+            sides = []
+            for a, b in zip(cell, cell[1:] + cell[:1]):
+                e = (min(a, b), max(a, b))
+                own = owner[e]
+                nb = [o for o in own if o != c]
+                d = V[b] - V[a]
+                S = np.array([d[1], -d[0], 0.0])
+                xf = np.array([0.5 * (V[a, 0] + V[b, 0]), 0.5 * (V[a, 1] + V[b, 1]), 0.5])
+                if nb:
+                    assert len(own) == 2
+                    n = nb[0]
+                    sides.append(Side(0, 1 if n > c else -1, S, xf, n, -1, -1))
+                else:
+                    tag = int(mesh.boundary[e])
+                    sides.append(Side(0, 1, S, xf, -1, int(mesh.bc_type[tag]), tag))
+            self.sides.append(sides)
+        self.key = (np.asarray(mesh.key, dtype=np.float64) if mesh.key is not None
+                    else self.centers[:, 0] + self.centers[:, 1])
+
+    def step(self, c, d, s):
+        return -1
+
+    def hyperplane(self, c):
+        return self.key[c]
+
+    def interior_faces(self):
+        L, R, S = [], [], []
+        for c in range(self.ncell):
+            for sd in self.sides[c]:
+                if sd.s > 0 and sd.nbr >= 0:
+                    L.append(c); R.append(sd.nbr); S.append(sd.S_out)
+        return np.array(L, dtype=np.int64), np.array(R, dtype=np.int64), np.array(S)
+
+    def boundary_faces(self):
+        C, S, X, B, T = [], [], [], [], []
+        for c in range(self.ncell):
+            for sd in self.sides[c]:
+                if sd.nbr < 0 and sd.bc in (BC_FARFIELD, BC_WALL):
+                    C.append(c); S.append(sd.S_out); X.append(sd.xf); B.append(sd.bc_side); T.append(sd.bc)
+        return (np.array(C, dtype=np.int64), np.array(S).reshape(-1, 3), np.array(X).reshape(-1, 3),
+                np.array(B, dtype=np.int64), np.array(T, dtype=np.int64))
+
+
+class UnstructuredGeometry(MacroGeometry):
+    """oracle.macro.MacroGeometry on an UnstructuredTopology, without the
+    index-space neighbour table (first-order face states)."""
+
+    def __init__(self, topo):
+        super().__init__(topo)
+        self.nb[:] = -1
+
+
+class UnstructuredSolver(OracleSolver):
+    """oracle.gsis.OracleSolver on a PolygonMesh (case.mesh) with a uniform,
+    reduced or hybrid velocity grid (case.vgrid may be a HybridGrid)."""
+
+    def __init__(self, case, flags_override=None):
+        self.case = case
+        self.topo = UnstructuredTopology(case.mesh)
+        self.geo = UnstructuredGeometry(self.topo)
+        if isinstance(case.vgrid, HybridGrid):
+            self.vg = case.vgrid
+        elif getattr(case.vgrid, "reduced", False):
+            self.vg = ReducedGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
+        else:
+            self.vg = M.VelocityGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
+        self.mu0 = M.mu0_from_kn(case.Kn)
+        self.omega = case.omega
+        self.bc_state = np.array(case.mesh.bc_state, dtype=np.float64)
+        self.W = np.array(case.W0, dtype=np.float64)
+        self.N = self.topo.ncell
+        self.f = np.zeros((self.N, self.vg.nv))
+        self.dvm = np.zeros(self.N, dtype=bool)
+        self.flags_override = flags_override
+        self.eps_history = []
+        self.W_history = []
+        self.kn_gll = np.zeros(self.N)
+        self.hot_sigma = np.zeros((self.N, 3, 3))
+        self.hot_q = np.zeros((self.N, 3))
+        self.iteration = 0
+        self.presolve_blocks = 0
+
+    def region(self, W):
+        """Kn_Gll >= Kn_ref, plus the cells within wall_layers face-neighbour
+        steps of a wall face."""
+        if self.flags_override is not None:
+            return np.array(self.flags_override, dtype=bool)
+        self.kn_gll = self.kn_gll_field(W)
+        flag = self.kn_gll >= self.case.Kn_ref
+        front = [c for c in range(self.N) if any(sd.bc == BC_WALL for sd in self.topo.sides[c])]
+        seen = set(front)
+        for _ in range(self.case.wall_layers):
+            nxt = []
+            for c in front:
+                flag[c] = True
+                for sd in self.topo.sides[c]:
+                    if sd.nbr >= 0 and sd.nbr not in seen:
+                        seen.add(sd.nbr); nxt.append(sd.nbr)
+            front = nxt
+        return flag
