@@ -85,3 +85,6 @@ def test_null_safety(lib):
     lib.gsis_free(None)
     assert lib.gsis_last_error(None) == b"NULL context"
     assert lib.gsis_iterate(None, 1, None) == 1
+    A = (ctypes.c_double * 4)(0.786, -0.201, -0.059, 0.842)
+    assert lib.gsis_two_vdf_reference(None, None, 1, 2, 2.667, A, None) == 1
+    assert lib.gsis_two_vdf_moments(None, None, 1, 2, None) == 1
