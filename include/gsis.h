@@ -392,6 +392,28 @@ gsis_status gsis_two_vdf_reference(gsis_ctx* ctx, const double* S, int n, int d_
  * velocity grid), GSIS_ERR_UNSUPPORTED (reduced grid), GSIS_ERR_CUDA. */
 gsis_status gsis_two_vdf_moments(gsis_ctx* ctx, const double* F, int n, int d_r, double* out);
 
+/* Sweep levels of an unstructured mesh (host computation; no context, no
+ * device work): the schedule under which a level-parallel kinetic sweep gives
+ * the values of the sequential Gauss-Seidel sweep in the order (key, index).
+ * In that order each cell's level is one more than the highest level of its
+ * face neighbours that come before it (0 if none): face neighbours never
+ * share a level, and every neighbour that precedes a cell lies on a lower
+ * level (sweeping the levels downwards reproduces the reverse sweep).  On a
+ * structured grid with key i + j + k the levels are its hyperplanes.
+ *
+ * ncell:      number of cells (>= 0).
+ * offsets:    host, [ncell + 1], offsets[0] = 0, non-decreasing: the face
+ *             neighbours of cell c are neighbours[offsets[c] .. offsets[c+1]).
+ * neighbours: host, cell indices in [0, ncell), none equal to its own cell;
+ *             the relation must be symmetric.
+ * key:        host, [ncell] finite sweep-order keys.
+ * level:      host, [ncell], written.  nlevels: host, number of levels.
+ * Errors: GSIS_ERR_ARG (NULL where data are needed, bad offsets, an index
+ * out of range or a self-neighbour, an asymmetric relation, a non-finite
+ * key); nothing is written to level then. */
+gsis_status gsis_sweep_levels(int ncell, const int* offsets, const int* neighbours, const double* key, int* level,
+                              int* nlevels);
+
 /* Human-readable description of the last error on this context (never NULL). */
 const char* gsis_last_error(const gsis_ctx* ctx);
 

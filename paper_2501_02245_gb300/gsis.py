@@ -29,7 +29,7 @@ EXPORTED = ["gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterat
             "gsis_corrected_maxwellian_noalloc", "gsis_iterate_batch", "gsis_batch_info", "gsis_tuning_info",
             "gsis_debug_set_sweep_tile", "gsis_debug_vdf_moments", "gsis_debug_set_macro_path",
             "gsis_probe_fma_peak", "gsis_debug_set_batch_tile", "gsis_two_vdf_reference",
-            "gsis_two_vdf_moments"]
+            "gsis_two_vdf_moments", "gsis_sweep_levels"]
 MACRO_PATHS = {"auto": 0, "fused": 1, "multi": 2, "persistent": 3, "persistent_stall": 4}
 
 
@@ -120,6 +120,9 @@ def load():
     lib.gsis_two_vdf_reference.restype = c_int
     lib.gsis_two_vdf_moments.argtypes = [vp, vp, c_int, c_int, vp]
     lib.gsis_two_vdf_moments.restype = c_int
+    ip = ctypes.POINTER(c_int)
+    lib.gsis_sweep_levels.argtypes = [c_int, ip, ip, ctypes.POINTER(c_double), ip, ip]
+    lib.gsis_sweep_levels.restype = c_int
     lib.gsis_tuning_info.argtypes = [vp]
     lib.gsis_tuning_info.restype = ctypes.c_char_p
     for name in ("gsis_init", "gsis_set_mesh", "gsis_set_velocity_grid", "gsis_iterate", "gsis_moments",
@@ -405,6 +408,27 @@ def fma_peak(fp64, stream=None):
     if st != GSIS_OK:
         raise GsisError(st, "FMA peak probe failed")
     return r.value, ms.value
+
+
+def sweep_levels(neighbour_lists, key):
+    """Sweep levels of an unstructured mesh (gsis_sweep_levels): neighbour_lists
+    [ncell] of face-neighbour index lists, key [ncell]; returns (level [ncell],
+    number of levels)."""
+    lib = load()
+    n = len(neighbour_lists)
+    off = np.zeros(n + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(l) for l in neighbour_lists])
+    nb = np.array([x for l in neighbour_lists for x in l] or [0], dtype=np.int32)
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.float64))
+    lv = np.zeros(max(n, 1), dtype=np.int32)
+    nl = ctypes.c_int(0)
+    ip = ctypes.POINTER(ctypes.c_int)
+    st = lib.gsis_sweep_levels(n, off.ctypes.data_as(ip), nb.ctypes.data_as(ip),
+                               k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), lv.ctypes.data_as(ip),
+                               ctypes.byref(nl))
+    if st != GSIS_OK:
+        raise GsisError(st, "invalid mesh adjacency or keys")
+    return lv[:n].copy(), nl.value
 
 
 def version():
