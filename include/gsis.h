@@ -126,6 +126,11 @@ typedef struct {
  * S[d] and xf[d] of shape [nk'][nj'][ni'][3] with one extra face along d
  * (area vector pointing along +d, magnitude = area; face centre).  In a
  * periodic direction the face between the last and the first cell is face 0.
+ * A periodic direction is taken as geometrically continuous (the angular
+ * direction of an O-grid): the line of centres and the least-squares vectors
+ * across its wrap are the plain differences of the given cell centres, so a
+ * direction whose wrap is a translation (a periodic box) gets the distance
+ * across the whole domain there.
  * bc_type/bc_state per side (i-lo, i-hi, j-lo, j-hi, k-lo, k-hi); bc_state is
  * (rho, ux, uy, uz, T) for a far field, T at index 4 is the wall temperature
  * for a wall.  W0 [ncell][5] is the initial (rho, ux, uy, uz, T).
