@@ -8,11 +8,14 @@
   (1 - Pr) q and a Grad-13 distribution carries its stress and heat flux.
 * Polygon geometry: areas and centroids in closed form, closed cells, least
   squares exact for linear fields on triangles.
-* A square structured grid given as polygons runs the GSIS iteration of the
-  structured oracle with first-order faces (same values); a uniform stream is
-  a fixed point of the iteration on a triangle mesh (with a hybrid grid it
-  moves by the second-order quadrature error); a heated channel on triangles
-  with a hybrid grid and an adaptive region keeps Eq. updatef's conservation.
+* Polyhedra: tetrahedron and box closed forms; a conforming tetrahedral split
+  of a box gives closed, outward cells and exact least squares.
+* A square structured grid given as polygons, and a cubic one given as
+  hexahedra, run the GSIS iteration of the structured oracle with first-order
+  faces (same values); a uniform stream is a fixed point of the iteration on
+  triangles and on tetrahedra (with a hybrid grid it moves by the
+  second-order quadrature error); a heated channel on triangles with a
+  hybrid grid and an adaptive region keeps Eq. updatef's conservation.
 """
 import numpy as np
 import pytest
@@ -235,3 +238,130 @@ def test_heated_channel_on_triangles_with_a_hybrid_grid_converges():
             assert np.max(np.abs(Uf - Uw)) < 1e-12 * np.max(np.abs(Uw))
     e = s.eps_history
     assert e[-1] < e[0] and np.max(s.W[:, 4]) > 1.0 + 1e-3
+
+
+# ----------------------------------------------------------------------------- 3D polyhedra
+from oracle.unstructured import PolyhedralMesh, PolyhedralTopology, face_vector_area, polyhedron_geometry  # noqa: E402
+from workloads.meshes import _hexa_block, _tensor_vertices  # noqa: E402
+
+
+def _box_mesh(n, lo, hi, bc_type, bc_state, tets=False):
+    """A box of n = (ni, nj, nk) cells as hexahedra (flat order c = i + ni (j +
+    nj k), faces in the order x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) or as six
+    tetrahedra each (the split along each cube's main diagonal, conforming
+    between neighbouring cubes); boundary tags 0..5 = x-lo .. z-hi."""
+    ax = [np.linspace(lo[d], hi[d], n[d] + 1) for d in range(3)]
+    V = np.array([[x, y, z] for z in ax[2] for y in ax[1] for x in ax[0]])
+    vid = lambda i, j, k: i + (n[0] + 1) * (j + (n[1] + 1) * k)
+    cells = []
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                v = {(a, b, c): vid(i + a, j + b, k + c) for a in (0, 1) for b in (0, 1) for c in (0, 1)}
+                if tets:
+                    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+                        path = [(0, 0, 0)]
+                        for d in perm:
+                            q = list(path[-1]); q[d] = 1; path.append(tuple(q))
+                        t = [v[q] for q in path]
+                        cells.append([[t[0], t[1], t[2]], [t[0], t[1], t[3]], [t[0], t[2], t[3]], [t[1], t[2], t[3]]])
+                else:
+                    cells.append([[v[0, 0, 0], v[0, 1, 0], v[0, 1, 1], v[0, 0, 1]],
+                                  [v[1, 0, 0], v[1, 1, 0], v[1, 1, 1], v[1, 0, 1]],
+                                  [v[0, 0, 0], v[1, 0, 0], v[1, 0, 1], v[0, 0, 1]],
+                                  [v[0, 1, 0], v[1, 1, 0], v[1, 1, 1], v[0, 1, 1]],
+                                  [v[0, 0, 0], v[1, 0, 0], v[1, 1, 0], v[0, 1, 0]],
+                                  [v[0, 0, 1], v[1, 0, 1], v[1, 1, 1], v[0, 1, 1]]])
+    count = {}
+    for cell in cells:
+        for f in cell:
+            count[tuple(sorted(f))] = count.get(tuple(sorted(f)), 0) + 1
+    bnd = {}
+    for fid, m in count.items():
+        if m == 1:
+            P = V[list(fid)]
+            for d in range(3):
+                if np.all(np.abs(P[:, d] - lo[d]) < 1e-12):
+                    bnd[fid] = 2 * d
+                elif np.all(np.abs(P[:, d] - hi[d]) < 1e-12):
+                    bnd[fid] = 2 * d + 1
+    return PolyhedralMesh(V, cells, bnd, list(bc_type), np.asarray(bc_state, dtype=np.float64))
+
+
+FF3 = [[1.0, 0.3, 0.1, -0.2, 1.0]] * 6
+
+
+def test_polyhedron_geometry_closed_forms():
+    V = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    vol, c = polyhedron_geometry(V, [[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]])
+    assert abs(vol - 1.0 / 6.0) < 1e-15 and np.allclose(c, 0.25)
+    S, xf = face_vector_area(np.array([[0.0, 0, 0], [2, 0, 0], [2, 3, 0], [0, 3, 0]]))
+    assert np.allclose(S, [0, 0, 6.0]) and np.allclose(xf, [1.0, 1.5, 0.0])
+    for tets in (False, True):
+        m = _box_mesh((3, 2, 2), (0.0, -0.5, 0.2), (1.2, 0.3, 1.0), [BC_FARFIELD] * 6, FF3, tets=tets)
+        t = PolyhedralTopology(m)
+        assert t.ncell == 12 * (6 if tets else 1)
+        assert abs(np.sum(t.vol) - 1.2 * 0.8 * 0.8) < 1e-13
+        for c in range(t.ncell):
+            assert np.max(np.abs(sum(sd.S_out for sd in t.sides[c]))) < 1e-15
+            for sd in t.sides[c]:
+                assert np.dot(sd.S_out, sd.xf - t.centers[c]) > 0
+        assert len(m.boundary) == (2 * (6 + 6 + 4) if not tets else 2 * 2 * (6 + 6 + 4))
+
+
+def test_least_squares_gradient_exact_for_linear_fields_on_tetrahedra():
+    m = _box_mesh((3, 2, 2), (0.0, -0.5, 0.2), (1.2, 0.3, 1.0), [BC_FARFIELD] * 6, FF3, tets=True)
+    t = PolyhedralTopology(m)
+    geo = UnstructuredGeometry(t)
+    lin = lambda p: 0.7 - 1.3 * p[..., 0] + 2.1 * p[..., 1] + 0.4 * p[..., 2]
+    bv = np.zeros((t.ncell, 6))
+    for c in range(t.ncell):
+        for si, sd in enumerate(t.sides[c]):
+            bv[c, si] = lin(sd.xf)
+    g = lsq_grad(geo, lin(t.centers), bv)
+    assert np.allclose(g, [-1.3, 2.1, 0.4], atol=1e-12)
+
+
+def _box_case(poly, tets=False, vgrid=None):
+    """Gas entering a box of cubic cells through the x ends, heated by
+    diffuse walls at y = 0, 0.75 (T_w = 1.5); no flux through the z sides."""
+    W_in = [1.0, 0.6, 0.0, 0.1, 1.0]
+    wall = [1.0, 0.0, 0.0, 0.0, 1.5]
+    bc_type = [BC_FARFIELD, BC_FARFIELD, BC_WALL, BC_WALL, BC_NONE, BC_NONE]
+    bc_state = [W_in, W_in, wall, wall, [0.0] * 5, [0.0] * 5]
+    n, lo, hi = (4, 3, 2), (0.0, 0.0, 0.0), (1.0, 0.75, 0.5)
+    if poly:
+        mesh = _box_mesh(n, lo, hi, bc_type, bc_state, tets=tets)
+    else:
+        ax = [np.linspace(lo[d], hi[d], n[d] + 1) for d in range(3)]
+        mesh = _hexa_block(_tensor_vertices(*ax), 3, bc_type, bc_state, "box")
+    vg = vgrid or VGrid((8, 8, 6), (-7.0, -7.0, -6.0), (8.0, 7.0, 6.0))
+    return Case("box", mesh, vg, np.tile(W_in, (mesh.ncell, 1)), Kn=0.1, adaptive=False, macro_steps=8,
+                cfl=5.0, k_sub=2, iterations=2, presolve_max_blocks=0, dt=0.5)
+
+
+def test_hexahedra_run_the_structured_3d_iteration(monkeypatch):
+    """A box of cubic cells given as hexahedra and as a structured block, both
+    with first-order faces: two GSIS iterations give the same states and
+    VDFs."""
+    from oracle import kinetic as K, macro as Mac
+    monkeypatch.setattr(K, "slope", lambda *a: 0.0)
+    monkeypatch.setattr(Mac, "minmod", lambda a, b: np.zeros_like(a))
+    o = OracleSolver(_box_case(False)).run(2)
+    u = UnstructuredSolver(_box_case(True)).run(2)
+    assert np.max(np.abs(o.W - o.W_history[0])) > 1e-3
+    assert np.max(np.abs(u.W - o.W)) < 1e-12 * np.max(np.abs(o.W))
+    assert np.max(np.abs(u.f - o.f)) < 1e-12 * np.max(np.abs(o.f))
+    assert np.allclose(u.eps_history, o.eps_history, rtol=1e-10)
+
+
+def test_uniform_stream_is_a_fixed_point_on_tetrahedra():
+    """Far field on every side: a uniform stream (with all three velocity
+    components) stays uniform on the tetrahedral split of a box, with a
+    velocity grid that resolves its Maxwellian."""
+    W = [1.0, 0.4, -0.2, 0.15, 1.2]
+    mesh = _box_mesh((3, 2, 2), (0.0, -0.5, 0.2), (1.2, 0.3, 1.0), [BC_FARFIELD] * 6, [W] * 6, tets=True)
+    case = Case("uniform3", mesh, VGrid((28, 28, 28), (-11.0,) * 3, (11.0,) * 3), np.tile(W, (mesh.ncell, 1)),
+                Kn=0.1, adaptive=False, macro_steps=8, iterations=2, presolve_max_blocks=0)
+    s = UnstructuredSolver(case).run(2)
+    assert np.max(np.abs(s.W - case.W0)) < 1e-12 and max(s.eps_history) < 1e-12
