@@ -82,3 +82,21 @@ def test_refusals():
         with pytest.raises(gsis.GsisError):
             gsis.sweep_levels(nb, key)
     assert list(gsis.sweep_levels(ok, [1.0, 0.0])[0]) == [1, 0]
+
+
+def test_levels_on_tetrahedra_reproduce_the_sequential_sweep():
+    """The same two properties, and the level-by-level sweep equal bit for bit
+    to the sequential one, on the tetrahedral split of a heated box."""
+    from test_oracle_unstructured import _box_case
+    seq = UnstructuredSolver(_box_case(True, tets=True)).run(2)
+    lev = UnstructuredSolver(_box_case(True, tets=True))
+    adj = _adjacency(lev.topo)
+    lv, n = gsis.sweep_levels(adj, lev.topo.key)
+    rank = {c: r for r, c in enumerate(sorted(range(lev.N), key=lambda c: (lev.topo.key[c], c)))}
+    for c in range(lev.N):
+        for nbr in adj[c]:
+            assert lv[nbr] != lv[c] and (lv[nbr] < lv[c]) == (rank[nbr] < rank[c])
+    assert 1 < n < lev.N
+    lev.topo.hyperplane = lambda c: int(lv[c])
+    lev.run(2)
+    assert np.array_equal(lev.f, seq.f) and np.array_equal(lev.W, seq.W)
