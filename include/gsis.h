@@ -392,7 +392,8 @@ gsis_status gsis_two_vdf_reference(gsis_ctx* ctx, const double* S, int n, int d_
  * F:    device pointer, [n][2][Nv] doubles (x fastest): f0 then f1 of each
  *       pair (as gsis_two_vdf_reference writes them); 0 <= n <= 65535.
  * out:  device pointer, [n][18] doubles: rho, u (3), T_t, T_r, sigma (xx, yy,
- *       zz, xy, xz, yz), q_t (3), q_r (3); owned by the caller.
+ *       zz, xy, xz, yz), q_t (3), q_r (3); owned by the caller.  The pairs
+ *       are not inspected: a pair with zero mass gives non-finite moments.
  * Errors: GSIS_ERR_ARG (NULL, n or d_r out of range), GSIS_ERR_STATE (no
  * velocity grid), GSIS_ERR_UNSUPPORTED (reduced grid), GSIS_ERR_CUDA. */
 gsis_status gsis_two_vdf_moments(gsis_ctx* ctx, const double* F, int n, int d_r, double* out);
