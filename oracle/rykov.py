@@ -53,6 +53,8 @@ from .reduced import ReducedGrid
 from .mesh import Topology, BC_FARFIELD, BC_WALL
 from .kinetic import KineticInputs, sweep, wall_kinetic_flux
 from .macro import MacroGeometry, lsq_grad, minmod, _half_range
+from .hybrid import HybridGrid
+from .unstructured import PolygonMesh, PolyhedralMesh, topology_of, UnstructuredGeometry, wall_layer_flags
 
 NITROGEN = {"d_r": 2, "Z_r": 2.667, "omega": 0.74, "A": (0.786, -0.201, -0.059, 0.842)}
 MONATOMIC_A = (2.0 / 3.0, 0.0, 0.0, 1.0)
@@ -111,7 +113,9 @@ class RykovGrid:
         self.d_r = int(d_r)
         self.w = base.w
         self.n0 = base.nv
-        self.idx1 = np.nonzero(base.plane == 0)[0] if base.reduced else np.arange(base.nv)
+        self.idx1 = np.nonzero(base.plane == 0)[0] if isinstance(base, ReducedGrid) else np.arange(base.nv)
+        # quadrature weight of each f1 node relative to w (per node on a hybrid grid, whose w is 1)
+        self.w1 = base.wv[self.idx1] if isinstance(base, HybridGrid) else 1.0
         self.n1 = len(self.idx1)
         self.nv = self.n0 + self.n1
         self.xi = np.concatenate([base.xi, base.xi[self.idx1]])
@@ -122,8 +126,8 @@ class RykovGrid:
             psi0 = np.stack([np.ones(base.nv), x[:, 0], x[:, 1], x[:, 2], 0.5 * np.sum(x * x, axis=1)], axis=1)
         self.psi = np.zeros((self.nv, 6))
         self.psi[:self.n0, :5] = psi0
-        self.psi[self.n0:, 4] = 1.0
-        self.psi[self.n0:, 5] = 1.0
+        self.psi[self.n0:, 4] = self.w1
+        self.psi[self.n0:, 5] = self.w1
 
     def split(self, f):
         return f[:self.n0], f[self.n0:]
@@ -146,10 +150,10 @@ class RykovGrid:
         f0, f1 = self.split(f)
         rho, u, Tt, sigma, qt = self.base.moments(f0)
         if self.d_r > 0:
-            Tr = 2.0 * self.w * np.sum(f1) / (self.d_r * rho)
+            Tr = 2.0 * self.w * np.sum(self.w1 * f1) / (self.d_r * rho)
         else:
             Tr = Tt
-        qr = self.w * (self.c1(u).T @ f1)
+        qr = self.w * (self.c1(u).T @ (self.w1 * f1))
         return rho, u, Tt, Tr, sigma, qt, qr
 
     # ---------------------------------------------------------------- distributions
@@ -475,15 +479,23 @@ def residual_eps6(Wn, Wp, vol):
 
 class RykovSolver:
     """Adaptive GSIS (the steps of oracle.gsis.OracleSolver) for the two-VDF gas.
-    case: a workload descriptor (mesh, velocity grid, initial W0 with 5 columns
-    (T_r = T_t) or 6, Kn, run parameters); gas: d_r, Z_r, A (mu0 and omega come
-    from the case)."""
+    case: a workload descriptor (mesh -- structured, or a polygon or polyhedral
+    mesh of oracle.unstructured --, velocity grid -- uniform, reduced or a
+    HybridGrid --, initial W0 with 5 columns (T_r = T_t) or 6, Kn, run
+    parameters); gas: d_r, Z_r, A (mu0 and omega come from the case)."""
 
     def __init__(self, case, d_r, Zr, A, flags_override=None):
         self.case = case
-        self.topo = Topology(case.mesh)
-        self.geo = MacroGeometry(self.topo)
-        if getattr(case.vgrid, "reduced", False):
+        self.unstructured = isinstance(case.mesh, (PolygonMesh, PolyhedralMesh))
+        if self.unstructured:
+            self.topo = topology_of(case.mesh)
+            self.geo = UnstructuredGeometry(self.topo)
+        else:
+            self.topo = Topology(case.mesh)
+            self.geo = MacroGeometry(self.topo)
+        if isinstance(case.vgrid, HybridGrid):
+            base = case.vgrid
+        elif getattr(case.vgrid, "reduced", False):
             base = ReducedGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
         else:
             base = M.VelocityGrid(case.vgrid.n, case.vgrid.lo, case.vgrid.hi)
@@ -539,6 +551,8 @@ class RykovSolver:
         self.kn_gll = self.kn_gll_field(W)
         flag = self.kn_gll >= self.case.Kn_ref
         mesh = self.case.mesh
+        if self.unstructured:
+            return flag | wall_layer_flags(self.topo, self.case.wall_layers)
         if self.case.wall_layers > 0:
             for d in range(3):
                 for hi in (0, 1):
@@ -600,7 +614,7 @@ class RykovSolver:
             rho, u, Tt, Tr = W[c, 0], W[c, 1:4], W[c, 4], W[c, 5]
             f0, f1 = vg.split(self.f[c])
             qt = vg.base.heat_flux_about(f0, u)
-            qr = vg.w * (vg.c1(u).T @ f1)
+            qr = vg.w * (vg.c1(u).T @ (vg.w1 * f1))
             gt[c] = vg.reference(rho, u, Tt, Tr, qt, qr, gas.Zr, gas.A)
             tau[c] = M.viscosity(Tt, gas.mu0, gas.omega) / (rho * Tt)
         need = set()

@@ -288,15 +288,21 @@ class UnstructuredSolver(OracleSolver):
         if self.flags_override is not None:
             return np.array(self.flags_override, dtype=bool)
         self.kn_gll = self.kn_gll_field(W)
-        flag = self.kn_gll >= self.case.Kn_ref
-        front = [c for c in range(self.N) if any(sd.bc == BC_WALL for sd in self.topo.sides[c])]
-        seen = set(front)
-        for _ in range(self.case.wall_layers):
-            nxt = []
-            for c in front:
-                flag[c] = True
-                for sd in self.topo.sides[c]:
-                    if sd.nbr >= 0 and sd.nbr not in seen:
-                        seen.add(sd.nbr); nxt.append(sd.nbr)
-            front = nxt
-        return flag
+        return (self.kn_gll >= self.case.Kn_ref) | wall_layer_flags(self.topo, self.case.wall_layers)
+
+
+def wall_layer_flags(topo, layers):
+    """Cells within `layers` face-neighbour steps of a wall face (the first
+    layer touches the wall)."""
+    flag = np.zeros(topo.ncell, dtype=bool)
+    front = [c for c in range(topo.ncell) if any(sd.bc == BC_WALL for sd in topo.sides[c])]
+    seen = set(front)
+    for _ in range(layers):
+        nxt = []
+        for c in front:
+            flag[c] = True
+            for sd in topo.sides[c]:
+                if sd.nbr >= 0 and sd.nbr not in seen:
+                    seen.add(sd.nbr); nxt.append(sd.nbr)
+        front = nxt
+    return flag

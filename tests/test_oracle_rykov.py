@@ -357,3 +357,61 @@ def test_reduced_two_vdf_iteration_is_the_xi_z_integral_of_the_3d_one(monkeypatc
         ref = dz * f1.sum(axis=0)
         red = orr.vg.split(orr.f[cell])[1]
         assert np.max(np.abs(red - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+# ----------------------------------------------------------------------------- unstructured meshes, hybrid grids
+def test_collision_term_conserves_on_a_hybrid_grid():
+    """The conservation readings hold with per-node weights too: on a stretched
+    hybrid velocity grid the two-VDF collision term conserves mass, momentum
+    and total energy to rounding and moves internal energy at the exchange
+    rate, exactly as on the uniform grid."""
+    from oracle.hybrid import HybridGrid, stretched_edges
+    vg = RykovGrid(HybridGrid(*[stretched_edges(-9.0, 9.0, n, c, 1.1) for n, c in ((18, 0.4), (16, -0.2),
+                                                                                     (14, 0.0))]), 2)
+    f = _nonequilibrium(vg)
+    rho, u, Tt, Tr, sig, qt, qr = vg.moments(f)
+    g = vg.reference(rho, u, Tt, Tr, qt, qr, NITROGEN["Z_r"], NITROGEN["A"])
+    dU = vg.conserved(g) - vg.conserved(f)
+    scale = np.max(np.abs(vg.conserved(f)))
+    assert np.max(np.abs(dU[:5])) < 1e-13 * scale
+    T = (3.0 * Tt + 2.0 * Tr) / 5.0
+    assert abs(dU[5] - rho * (T - Tr) / NITROGEN["Z_r"]) < 1e-13 * scale and abs(Tt - Tr) > 0.05
+
+
+def test_monatomic_case_on_triangles_with_a_hybrid_grid_is_the_unstructured_oracle():
+    """d_r = 0 on a triangulated, heated channel with a hybrid velocity grid
+    and one wall layer: the two-VDF iteration is the (pinned) unstructured
+    Shakhov iteration."""
+    from oracle.hybrid import HybridGrid, stretched_edges
+    from oracle.unstructured import UnstructuredSolver
+    from test_oracle_unstructured import _channel
+    hg = HybridGrid(*[stretched_edges(-8.0, 9.0, n, c, 1.1) for n, c in ((14, 0.6), (12, 0.0), (8, 0.0))])
+    case = _channel(True, triangles=True, vgrid=hg)
+    case.adaptive, case.Kn_ref, case.wall_layers, case.adapt_every = True, 1e9, 1, 1000
+    o = UnstructuredSolver(case).run(3)
+    r = RykovSolver(case, 0, NITROGEN["Z_r"], MONATOMIC_A).run(3)
+    assert np.array_equal(r.dvm, o.dvm) and 0 < o.dvm.sum() < o.N
+    assert np.max(np.abs(r.W[:, :5] - o.W)) < 1e-12 * np.max(np.abs(o.W))
+    assert np.max(np.abs(r.f[:, :o.vg.nv] - o.f)) < 1e-12 * np.max(np.abs(o.f))
+
+
+def test_nitrogen_on_tetrahedra_with_a_hybrid_grid():
+    """Nitrogen in the heated box split into tetrahedra, hybrid velocity grid:
+    after every GSIS iteration each kinetic cell carries the six new conserved
+    moments (Eq. updatef), the internal mode is out of equilibrium at the
+    heated walls, and the residual falls."""
+    from oracle.hybrid import HybridGrid, stretched_edges
+    from test_oracle_unstructured import _box_case
+    hg = HybridGrid(*[stretched_edges(-7.0, 8.0, n, c, 1.1) for n, c in ((10, 0.6), (10, 0.0), (8, 0.1))])
+    case = _box_case(True, tets=True, vgrid=hg)
+    case.omega = NITROGEN["omega"]
+    s = RykovSolver(case, *N2)
+    s.initialise()
+    for _ in range(3):
+        s.step()
+        for c in np.nonzero(s.dvm)[0]:
+            Uf = s.vg.conserved(s.f[c])
+            Uw = conserved6(s.W[c], N2[0])
+            assert np.max(np.abs(Uf - Uw)) < 1e-12 * np.max(np.abs(Uw))
+    assert np.max(np.abs(s.W[:, 4] - s.W[:, 5])) > 1e-3
+    assert s.eps_history[-1] < s.eps_history[0]
